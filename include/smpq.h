@@ -1,0 +1,161 @@
+/*
+ * smpq.h - C ABI of libsmpq: topological charge density q(x) = 1/2 tr(gamma_5 D_ov)(x,x)
+ * estimated with symmetric multi-probing (SMP) sources on one GB300 GPU.
+ *
+ * Method (arXiv:1901.02211):
+ *   D_ov = 1 + gamma_5 eps(gamma_5 D_W)                                (Sec. 2.1, Eq. 3)
+ *   eps(H) = H (c0 + sum_{i=1}^{n} c_i / (H^2 + q_i)), H = gamma_5 D_W,
+ *            H^2 = D_W^dag D_W, n = 14 Zolotarev poles                  (Sec. 2.1, Eq. 4)
+ *   q(x) = 1/2 sum_{alpha,a} <psi(x,alpha,a)| gamma_5 D_ov |psi(x,alpha,a)>  (Eq. 5)
+ *   the shifted systems (D_W^dag D_W + q_i) v_i = b are solved by CG     (Eqs. 6-8)
+ *   SMP source phi_P(S, alpha, a) = sum_{y in S} psi(y, alpha, a)        (Sec. 2.2, Eq. 15)
+ *   q^SMP(x) = sum_{alpha,a} psi(x,alpha,a) D~_ov phi_P(S(x,P),alpha,a),
+ *              D~_ov = gamma_5 D_ov / 2                                  (Sec. 2.2, Eq. 16)
+ *   colouring schemes P(m_x,m_y,m_z,m_t,mode), r_mu = n_mu/m_mu,
+ *              mode 0 Normal, 1 Split, 2 Combine                          (Sec. 2.2, Eq. 19)
+ *
+ * Conventions:
+ *   lattice dims = {nx, ny, nz, nt}, site index s = x + nx*(y + ny*(z + nz*t));
+ *   D_W psi(x) = psi(x) - kappa sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                       + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)],
+ *   chiral basis gamma_5 = diag(1, 1, -1, -1), bc[mu] = +1 periodic / -1 antiperiodic;
+ *   complex numbers are interleaved (re, im) doubles;
+ *   gauge field (host or device): double[V][4][3][3][2], U[s][mu][row][col];
+ *   FP64 spinor fields at the ABI: double[V][4][3][B][2] (site, spin, colour, rhs).
+ *
+ * Errors: every call returns an smpq_status; nothing throws across the ABI.  On
+ * error smpq_last_error(ctx) gives a message valid until the next call on ctx.
+ * Ownership: caller buffers are only read or written during the call (device
+ * buffers are used in stream order on the context's stream and the call
+ * synchronises that stream before returning); the library never frees caller
+ * memory and owns every device allocation it makes (released by smpq_destroy).
+ * A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SMPQ_H
+#define SMPQ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smpq_ctx smpq_ctx;
+
+typedef enum {
+    SMPQ_OK = 0,
+    SMPQ_EINVAL = -1,     /* bad argument (sizes, scheme that does not tile, NULL) */
+    SMPQ_ENOMEM = -2,     /* device allocation failed */
+    SMPQ_ECUDA = -3,      /* CUDA runtime error (message in smpq_last_error) */
+    SMPQ_ENOCONV = -4,    /* solver reached max_iter before every shift converged */
+    SMPQ_EBREAKDOWN = -5, /* CG breakdown: <p, A p> <= 0 or non-finite */
+    SMPQ_ETIMEOUT = -6,   /* reserved: a bounded device wait gave up */
+    SMPQ_ENOTSU3 = -7,    /* gauge field is not SU(3) to 1e-10 */
+    SMPQ_ESTATE = -8      /* call out of order (e.g. compute before load_gauge) */
+} smpq_status;
+
+typedef enum {
+    SMPQ_FP64 = 0, /* vectors, dslash and updates in FP64 (reference path) */
+    SMPQ_FP32 = 1  /* FP32 vectors and dslash with FP64 reliable updates, FP64 scalars */
+} smpq_precision;
+
+typedef struct {
+    double kappa;          /* Wilson hopping parameter (Sec. 2.1: 0.21) */
+    int npoles;            /* Zolotarev poles (Sec. 2.1: 14); 1..32 */
+    double tol;            /* per-shift relative residual |zeta_i| ||r|| / ||b|| */
+    int max_iter;          /* CG iteration cap */
+    int precision;         /* smpq_precision */
+    double reliable_delta; /* FP32 path: replace the residual when ||r|| < delta * max ||r|| */
+    int bc[4];             /* fermion boundary factors per direction */
+    int rhs_block;         /* right-hand sides per solve batch (multiple of 12; 0 = automatic) */
+    int iters_per_check;   /* CG iterations launched between host convergence checks */
+    int use_graphs;        /* capture those iterations in a CUDA graph */
+} smpq_options;
+
+typedef struct {
+    int n_rhs;              /* right-hand sides solved by the last call */
+    int n_classes;          /* colour classes processed */
+    int n_batches;          /* solve batches */
+    int max_iterations;     /* largest CG iteration count of any right-hand side */
+    long long total_iterations; /* sum over batches of the batch iteration count */
+    int reliable_updates;   /* FP64 residual replacements (FP32 path) */
+    double max_resid;       /* largest final recursive residual |zeta_i| ||r|| / ||b|| */
+    double max_im_q;        /* max |Im q^SMP(x)| over processed sites */
+    double Q;               /* sum_x Re q(x) over the processed sites */
+    double solve_ms;        /* device time of the solves (CUDA events) */
+    double total_ms;        /* device time of the whole call */
+} smpq_stats;
+
+/* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
+ * max_iter 5000, FP64, reliable_delta 0.1, periodic bc, automatic batching,
+ * 10 iterations per check, graphs on. */
+int smpq_options_default(smpq_options *opt);
+
+/* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream; NULL = the legacy default stream).
+ * *out receives the context; options are copied. */
+int smpq_create(smpq_ctx **out, int device, void *stream, const smpq_options *opt);
+int smpq_destroy(smpq_ctx *ctx);
+const char *smpq_last_error(const smpq_ctx *ctx);
+
+/* Change the options of an existing context (kappa/bc changes take effect on
+ * the next call; the gauge field and spectrum stay loaded). */
+int smpq_set_options(smpq_ctx *ctx, const smpq_options *opt);
+
+/* Load the gauge field U_mu(x) (Sec. 2.1: the links of D_W).  dims: {nx,ny,nz,nt},
+ * each >= 2 and V <= 2^28; links: double[V][4][3][3][2], host (on_device=0) or
+ * device memory; copied and packed into the context's FP64 and FP32 link arrays.
+ * SMPQ_ENOTSU3 if any link deviates from unitarity or det = 1 by more than 1e-10. */
+int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int on_device);
+
+/* Set the Zolotarev interval [a, b] = [lmin2, lmax2] of H_W^2 and compute the
+ * coefficients (Eq. 4).  0 < lmin2 < lmax2. */
+int smpq_set_spectrum(smpq_ctx *ctx, double lmin2, double lmax2);
+
+/* Estimate the extreme eigenvalues of H_W^2 by `iters` Lanczos steps (CG
+ * coefficients on a seeded random vector) and set the interval to
+ * [0.98 lmin2, 1.02 lmax2] (the paper does not say how the interval is chosen).
+ * Outputs (nullable) receive the unwidened Ritz values. */
+int smpq_measure_spectrum(smpq_ctx *ctx, int iters, double *lmin2, double *lmax2);
+
+/* Zolotarev coefficients of R(x) = c0 + sum_i c[i]/(x + q[i]) ~ 1/sqrt(x) on
+ * [a, b] (Eq. 4), type (npoles, npoles), q ascending; *delta = max relative
+ * error.  Pure host computation; c and q hold npoles doubles. */
+int smpq_zolotarev(int npoles, double a, double b, double *c0, double *c, double *q, double *delta);
+
+/* Coefficients currently used by the context (after set/measure_spectrum). */
+int smpq_get_zolotarev(const smpq_ctx *ctx, double *c0, double *c, double *q, double *delta);
+
+/* Choose the colouring scheme (Sec. 2.2): same-colour sites every r sites in
+ * each direction (r_mu = r), mode 0 Normal / 1 Split / 2 Combine.  SMPQ_EINVAL
+ * if r does not divide every n_mu, if mode 1 and some n_mu/r is odd, or if
+ * mode 2 and r is odd.  *n_classes (nullable) = N_p; the solve count is 12 N_p. */
+int smpq_build_sources(smpq_ctx *ctx, int r, int mode, int *n_classes);
+
+/* Host-side colouring only (no GPU work): colour of every site, int[V].  Same
+ * validation as smpq_build_sources. */
+int smpq_colour_sites(const int dims[4], int r, int mode, int *colour, int *n_classes);
+
+/* D_W (or gamma_5 D_W gamma_5 = D_W^dag if dagger) applied to B fields,
+ * computed in `precision` (FP64 or FP32 kernel; in/out FP64 at the ABI).
+ * in/out: double[V][4][3][B][2], host or device (on_device). */
+int smpq_dslash(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision, int on_device);
+
+/* out = D_ov in = in + D_W R(H^2) in (Eqs. 3-4 with gamma_5^2 = 1), B fields,
+ * FP64 multi-shift CG over the full lattice.  Layout as smpq_dslash. */
+int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_device);
+
+/* q^SMP(x) for every site with the scheme of smpq_build_sources (Eq. 16):
+ * q_re, q_im: double[V] (host or device), Q (nullable): sum_x Re q(x).
+ * With r = n_mu in every direction every set is one site and the result is
+ * the exact point-source q(x) of Eq. 5. */
+int smpq_compute_qx(smpq_ctx *ctx, double *q_re, double *q_im, int on_device, double *Q, smpq_stats *stats);
+
+/* As smpq_compute_qx for the listed colour classes only (sampled checks,
+ * checkpoint/resume).  Sites of other classes are left untouched in q_re/q_im. */
+int smpq_compute_qx_classes(smpq_ctx *ctx, const int *classes, int n, double *q_re, double *q_im, int on_device,
+                            smpq_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMPQ_H */

@@ -10,19 +10,21 @@ from __future__ import annotations
 import numpy as np
 from scipy.sparse.linalg import LinearOperator, eigsh
 
-from . import dirac
+from . import dirac, native
 
 MARGIN_LO = 0.98
 MARGIN_HI = 1.02
 
 
-def h2_extremes(U, dims, kappa, bc=(1, 1, 1, 1), tol=1e-10):
-    """(lambda_min^2, lambda_max^2) of H_W^2 via eigsh on the matrix-free operator."""
+def h2_extremes(U, dims, kappa, bc=(1, 1, 1, 1), tol=1e-10, backend="c"):
+    """(lambda_min^2, lambda_max^2) of H_W^2 via eigsh on the matrix-free operator
+    (applied by the compiled oracle, or by oracle/dirac.py with backend="numpy")."""
     V = int(np.prod(dims))
     n = 12 * V
+    h2 = native.apply_h2 if backend == "c" else dirac.apply_h2
 
     def mv(v):
-        return dirac.apply_h2(U, v.reshape(V, 4, 3), dims, kappa, bc).reshape(n)
+        return h2(U, v.reshape(V, 4, 3), dims, kappa, bc).reshape(n)
 
     op = LinearOperator((n, n), matvec=mv, dtype=np.complex128)
     lmax = eigsh(op, k=1, which="LA", tol=tol, return_eigenvectors=False)[0]

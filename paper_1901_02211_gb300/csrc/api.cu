@@ -1,0 +1,604 @@
+// C ABI of libsmpq (declared and documented in include/smpq.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "smpq_internal.cuh"
+
+// ------------------------------------------------------------------ helpers
+int set_err(smpq_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_check(smpq_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SMPQ_OK;
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? SMPQ_ENOMEM : SMPQ_ECUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ensure(smpq_ctx *ctx, Buf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return SMPQ_OK;
+    release(b);
+    if (bytes == 0) return SMPQ_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        b.bytes = 0;
+        return set_err(ctx, SMPQ_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    b.bytes = bytes;
+    return SMPQ_OK;
+}
+
+void release(Buf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// make the context stream wait for work already queued on the caller's stream
+struct StreamEntry {
+    StreamEntry(smpq_ctx *ctx, void *user) {
+        if (user) {
+            cudaEventRecord(ctx->ev0, (cudaStream_t)user);
+            cudaStreamWaitEvent(ctx->stream, ctx->ev0, 0);
+        }
+    }
+};
+
+__global__ void k_axpy(double2 *__restrict__ y, const double2 *__restrict__ x, double a, size_t n) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        y[i].x += a * x[i].x;
+        y[i].y += a * x[i].y;
+    }
+}
+
+void launch_axpy(double2 *y, const double2 *x, double a, size_t n, cudaStream_t st) {
+    k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, x, a, n);
+}
+
+int check_ctx(smpq_ctx *ctx, bool gauge, bool spec, bool src) {
+    if (!ctx) return SMPQ_EINVAL;
+    if (gauge && !ctx->have_gauge) return set_err(ctx, SMPQ_ESTATE, "no gauge field loaded");
+    if (spec && !ctx->have_spec) return set_err(ctx, SMPQ_ESTATE, "no spectrum interval set");
+    if (src && !ctx->have_sources) return set_err(ctx, SMPQ_ESTATE, "no colouring scheme built");
+    return SMPQ_OK;
+}
+
+int validate_options(smpq_ctx *ctx, const smpq_options *o) {
+    if (!(o->kappa > 0) || !(o->kappa < 1)) return set_err(ctx, SMPQ_EINVAL, "kappa must be in (0, 1)");
+    if (o->npoles < 1 || o->npoles > SMPQ_MAX_POLES) return set_err(ctx, SMPQ_EINVAL, "npoles must be in 1..32");
+    if (!(o->tol > 0) || !(o->tol < 1)) return set_err(ctx, SMPQ_EINVAL, "tol must be in (0, 1)");
+    if (o->max_iter < 1) return set_err(ctx, SMPQ_EINVAL, "max_iter must be positive");
+    if (o->precision != SMPQ_FP64 && o->precision != SMPQ_FP32) return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    if (!(o->reliable_delta > 0) || !(o->reliable_delta < 1))
+        return set_err(ctx, SMPQ_EINVAL, "reliable_delta must be in (0, 1)");
+    for (int mu = 0; mu < 4; ++mu)
+        if (o->bc[mu] != 1 && o->bc[mu] != -1) return set_err(ctx, SMPQ_EINVAL, "bc must be +1 or -1");
+    if (o->rhs_block < 0 || (o->rhs_block > 1 && o->rhs_block % 12))
+        return set_err(ctx, SMPQ_EINVAL, "rhs_block must be 0, 1 or a multiple of 12");
+    if (o->iters_per_check < 1) return set_err(ctx, SMPQ_EINVAL, "iters_per_check must be positive");
+    return SMPQ_OK;
+}
+
+void set_geom(smpq_ctx *ctx) {
+    Geom &g = ctx->geom;
+    int st = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        g.n[mu] = ctx->dims[mu];
+        g.stride[mu] = st;
+        st *= ctx->dims[mu];
+        g.bcf[mu] = (float)ctx->opt.bc[mu];
+    }
+    g.V = ctx->V;
+}
+
+int pick_bc(int B) {
+    if (B == 1) return 1;
+    if (B % 48 == 0) return 48;
+    if (B % 24 == 0) return 24;
+    if (B % 12 == 0) return 12;
+    return 1;
+}
+
+// device bytes one right-hand side costs in the solver (full-lattice vectors)
+size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
+    size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16) : (3 * 16);
+    size_t full = (size_t)ctx->V * 12 * per;
+    size_t eb = prec == SMPQ_FP32 ? 8 : 16;
+    size_t sup = (size_t)n_sup * 12 * (npoles * eb + 16);
+    return full + sup;
+}
+
+int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re, double *q_im, int on_device,
+                    smpq_stats *stats, bool full) {
+    cudaStream_t st = ctx->stream;
+    cudaEventRecord(ctx->evA, st);
+    int rc;
+    // star support of every class
+    int n_sup = 0;
+    if ((rc = build_star_support(ctx, ctx->ws[W_SUP], &n_sup))) return rc;
+    const int prec = ctx->opt.precision;
+    const int nc = (int)classes.size();
+    const int nrhs_total = 12 * nc;
+    // batch size
+    int B;
+    if (ctx->opt.rhs_block == 1) B = 1;
+    else if (ctx->opt.rhs_block > 1) B = std::min(ctx->opt.rhs_block, nrhs_total);
+    else {
+        size_t freeb = 0, totb = 0;
+        cudaMemGetInfo(&freeb, &totb);
+        size_t per = bytes_per_rhs(ctx, prec, n_sup, ctx->opt.npoles);
+        long cap = (long)((0.6 * (double)freeb) / (double)per);
+        cap = std::max(12L, cap - cap % 48);
+        B = (int)std::min<long>(nrhs_total, cap);
+        if (B > 48) B -= B % 48;
+    }
+    if (B > 1) B -= B % 12;
+    if (B < 1) B = 1;
+    const int BC = pick_bc(B);
+    // qterm + device q
+    if ((rc = ensure(ctx, ctx->ws[W_QTERM], (size_t)ctx->n_classes * 12 * ctx->members * sizeof(double2)))) return rc;
+    if ((rc = ensure(ctx, ctx->ws[W_RHS], (size_t)3 * B * sizeof(int) + (size_t)nc * sizeof(int) +
+                                           (size_t)nc * ctx->members * sizeof(int) + 4 * sizeof(double))))
+        return rc;
+    int *d_rhs_class = (int *)ctx->ws[W_RHS].p, *d_src_comp = d_rhs_class + B, *d_src_class = d_src_comp + B;
+    int *d_classes = d_src_class + B, *d_sites = d_classes + nc;
+    double *d_tot = (double *)(((uintptr_t)(d_sites + (size_t)nc * ctx->members) + 15) & ~(uintptr_t)15);
+    std::vector<int> h_rhs(3 * (size_t)B);
+
+    SolveSpec spec{};
+    spec.B = B;
+    spec.BC = BC;
+    spec.prec = prec;
+    spec.full_support = 0;
+    spec.n_sup = n_sup;
+    spec.d_supsite = (const int *)ctx->ws[W_SUP].p;
+    spec.d_rhs_class = d_rhs_class;
+    spec.d_colour = (const int *)ctx->d_colour.p;
+    spec.d_src_class = d_src_class;
+    spec.d_src_comp = d_src_comp;
+    spec.d_src_field = nullptr;
+
+    int maxit = 0, nrel = 0, nb = 0;
+    long long totit = 0;
+    double worst = 0, solve_ms = 0;
+    for (int j0 = 0; j0 < nrhs_total; j0 += B) {
+        for (int j = 0; j < B; ++j) {
+            int g = j0 + j;
+            int cl = g < nrhs_total ? classes[g / 12] : -1;
+            h_rhs[j] = cl;
+            h_rhs[B + j] = g % 12;
+            h_rhs[2 * B + j] = cl;
+        }
+        cudaMemcpyAsync(d_rhs_class, h_rhs.data(), 3 * (size_t)B * sizeof(int), cudaMemcpyHostToDevice, st);
+        SolveOut out;
+        rc = multishift_solve(ctx, spec, &out);
+        if (rc) return rc;
+        launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y, st);
+        launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class, d_src_comp,
+                        (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa, (double2 *)ctx->ws[W_QTERM].p,
+                        st);
+        maxit = std::max(maxit, out.iterations);
+        totit += out.iterations;
+        nrel += out.reliable_updates;
+        worst = std::max(worst, out.max_resid);
+        solve_ms += out.solve_ms;
+        ++nb;
+    }
+    // q(x) of the processed classes
+    cudaMemcpyAsync(d_classes, classes.data(), nc * sizeof(int), cudaMemcpyHostToDevice, st);
+    double *dq_re, *dq_im;
+    if (on_device) {
+        dq_re = q_re;
+        dq_im = q_im;
+    } else {
+        if ((rc = ensure(ctx, ctx->ws[W_Q], 2 * (size_t)ctx->V * sizeof(double)))) return rc;
+        dq_re = (double *)ctx->ws[W_Q].p;
+        dq_im = dq_re + ctx->V;
+    }
+    launch_qsum((const double2 *)ctx->ws[W_QTERM].p, d_classes, nc, (const int *)ctx->d_members.p, ctx->members,
+                dq_re, dq_im, st);
+    // Q in site order over the processed sites
+    std::vector<int> sites;
+    if (!full) {
+        sites.reserve((size_t)nc * ctx->members);
+        std::vector<char> mark(ctx->n_classes, 0);
+        for (int c : classes) mark[c] = 1;
+        for (int s = 0; s < ctx->V; ++s)
+            if (mark[ctx->colour[s]]) sites.push_back(s);
+        cudaMemcpyAsync(d_sites, sites.data(), sites.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    }
+    launch_qtotal(dq_re, dq_im, full ? nullptr : d_sites, full ? ctx->V : (int)sites.size(), d_tot, st);
+    double tot[2];
+    cudaMemcpyAsync(tot, d_tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (!on_device) {
+        std::vector<double> hq(2 * (size_t)ctx->V);
+        cudaMemcpyAsync(hq.data(), dq_re, hq.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "compute_qx copy-out");
+        if (full) {
+            std::memcpy(q_re, hq.data(), ctx->V * sizeof(double));
+            std::memcpy(q_im, hq.data() + ctx->V, ctx->V * sizeof(double));
+        } else {
+            for (int s : sites) {
+                q_re[s] = hq[s];
+                q_im[s] = hq[ctx->V + s];
+            }
+        }
+    }
+    cudaEventRecord(ctx->evB, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "compute_qx");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(ctx, e, "compute_qx launch");
+    float tms = 0;
+    cudaEventElapsedTime(&tms, ctx->evA, ctx->evB);
+    if (stats) {
+        stats->n_rhs = nrhs_total;
+        stats->n_classes = nc;
+        stats->n_batches = nb;
+        stats->max_iterations = maxit;
+        stats->total_iterations = totit;
+        stats->reliable_updates = nrel;
+        stats->max_resid = worst;
+        stats->max_im_q = tot[1];
+        stats->Q = tot[0];
+        stats->solve_ms = solve_ms;
+        stats->total_ms = tms;
+    }
+    ctx->last_Q = tot[0];
+    return SMPQ_OK;
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+int smpq_options_default(smpq_options *o) {
+    if (!o) return SMPQ_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->kappa = 0.21;
+    o->npoles = 14;
+    o->tol = 1e-10;
+    o->max_iter = 5000;
+    o->precision = SMPQ_FP64;
+    o->reliable_delta = 0.1;
+    for (int mu = 0; mu < 4; ++mu) o->bc[mu] = 1;
+    o->rhs_block = 0;
+    o->iters_per_check = 10;
+    o->use_graphs = 1;
+    return SMPQ_OK;
+}
+
+int smpq_create(smpq_ctx **out, int device, void *stream, const smpq_options *opt) {
+    if (!out) return SMPQ_EINVAL;
+    *out = nullptr;
+    smpq_ctx *ctx = new (std::nothrow) smpq_ctx();
+    if (!ctx) return SMPQ_ENOMEM;
+    if (opt) ctx->opt = *opt;
+    else smpq_options_default(&ctx->opt);
+    int rc = validate_options(ctx, &ctx->opt);
+    if (rc) { delete ctx; return rc; }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        delete ctx;
+        return SMPQ_ECUDA;
+    }
+    ctx->device = device;
+    DeviceGuard dg(device);
+    ctx->user_stream = stream;
+    e = cudaStreamCreate(&ctx->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev2);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->evA);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->evB);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return SMPQ_ECUDA;
+    }
+    ctx->ws.resize(W_COUNT);
+    *out = ctx;
+    return SMPQ_OK;
+}
+
+int smpq_destroy(smpq_ctx *ctx) {
+    if (!ctx) return SMPQ_EINVAL;
+    {
+        DeviceGuard dg(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &b : ctx->ws) release(b);
+        release(ctx->U64);
+        release(ctx->U32);
+        release(ctx->d_colour);
+        release(ctx->d_members);
+        cudaEventDestroy(ctx->ev0);
+        cudaEventDestroy(ctx->ev1);
+        cudaEventDestroy(ctx->ev2);
+        cudaEventDestroy(ctx->evA);
+        cudaEventDestroy(ctx->evB);
+        cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+    return SMPQ_OK;
+}
+
+const char *smpq_last_error(const smpq_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int smpq_set_options(smpq_ctx *ctx, const smpq_options *opt) {
+    if (!ctx || !opt) return SMPQ_EINVAL;
+    int rc = validate_options(ctx, opt);
+    if (rc) return rc;
+    bool respec = opt->npoles != ctx->opt.npoles;
+    ctx->opt = *opt;
+    if (ctx->have_gauge) set_geom(ctx);
+    if (respec && ctx->have_spec) return smpq_set_spectrum(ctx, ctx->lmin2, ctx->lmax2);
+    return SMPQ_OK;
+}
+
+int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int on_device) {
+    if (!ctx || !dims || !links) return SMPQ_EINVAL;
+    long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2) return set_err(ctx, SMPQ_EINVAL, "every lattice extent must be >= 2");
+        V *= dims[mu];
+    }
+    if (V > (1L << 28)) return set_err(ctx, SMPQ_EINVAL, "lattice volume above 2^28 sites");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    int rc;
+    if ((rc = ensure(ctx, ctx->U64, (size_t)V * 36 * sizeof(double2)))) return rc;
+    if ((rc = ensure(ctx, ctx->U32, (size_t)V * 36 * sizeof(float2)))) return rc;
+    const double *src = links;
+    if (!on_device) {
+        if ((rc = ensure(ctx, ctx->ws[W_MISC], (size_t)V * 36 * sizeof(double2)))) return rc;
+        cudaMemcpyAsync(ctx->ws[W_MISC].p, links, (size_t)V * 36 * sizeof(double2), cudaMemcpyHostToDevice,
+                        ctx->stream);
+        src = (const double *)ctx->ws[W_MISC].p;
+    }
+    for (int mu = 0; mu < 4; ++mu) ctx->dims[mu] = dims[mu];
+    ctx->V = (int)V;
+    set_geom(ctx);
+    launch_pack_links(src, (double *)ctx->U64.p, (float *)ctx->U32.p, (int)V, ctx->stream);
+    if ((rc = ensure(ctx, ctx->ws[W_PART], 64))) return rc;
+    double *derr = (double *)ctx->ws[W_PART].p;
+    launch_su3_check((const double *)ctx->U64.p, (int)V, derr, ctx->stream);
+    double err = 0;
+    cudaMemcpyAsync(&err, derr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "load_gauge");
+    if (!(err <= 1e-10)) {
+        ctx->have_gauge = false;
+        return set_err(ctx, SMPQ_ENOTSU3, "gauge field is not SU(3): max deviation " + std::to_string(err));
+    }
+    ctx->have_gauge = true;
+    ctx->have_sources = false; // colouring depends on the lattice
+    return SMPQ_OK;
+}
+
+int smpq_zolotarev(int npoles, double a, double b, double *c0, double *c, double *q, double *delta) {
+    if (!c0 || !c || !q) return SMPQ_EINVAL;
+    return zolotarev_coeffs(npoles, a, b, c0, c, q, delta);
+}
+
+int smpq_set_spectrum(smpq_ctx *ctx, double lmin2, double lmax2) {
+    if (!ctx) return SMPQ_EINVAL;
+    if (!(lmin2 > 0) || !(lmax2 > lmin2)) return set_err(ctx, SMPQ_EINVAL, "need 0 < lmin2 < lmax2");
+    int n = ctx->opt.npoles;
+    std::vector<double> c(n), q(n);
+    double c0, d;
+    int rc = zolotarev_coeffs(n, lmin2, lmax2, &c0, c.data(), q.data(), &d);
+    if (rc) return set_err(ctx, rc, "zolotarev coefficients");
+    ctx->lmin2 = lmin2;
+    ctx->lmax2 = lmax2;
+    ctx->c0 = c0;
+    ctx->delta = d;
+    ctx->zc = c;
+    ctx->zq = q;
+    ctx->have_spec = true;
+    return SMPQ_OK;
+}
+
+int smpq_get_zolotarev(const smpq_ctx *ctx, double *c0, double *c, double *q, double *delta) {
+    if (!ctx || !ctx->have_spec) return SMPQ_ESTATE;
+    if (c0) *c0 = ctx->c0;
+    if (c) std::copy(ctx->zc.begin(), ctx->zc.end(), c);
+    if (q) std::copy(ctx->zq.begin(), ctx->zq.end(), q);
+    if (delta) *delta = ctx->delta;
+    return SMPQ_OK;
+}
+
+int smpq_measure_spectrum(smpq_ctx *ctx, int iters, double *lmin2, double *lmax2) {
+    int rc = check_ctx(ctx, true, false, false);
+    if (rc) return rc;
+    if (iters < 4) return set_err(ctx, SMPQ_EINVAL, "need at least 4 Lanczos steps");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    double lo, hi;
+    if ((rc = lanczos_extremes(ctx, iters, &lo, &hi))) return rc;
+    if (lmin2) *lmin2 = lo;
+    if (lmax2) *lmax2 = hi;
+    return smpq_set_spectrum(ctx, 0.98 * lo, 1.02 * hi);
+}
+
+int smpq_colour_sites(const int dims[4], int r, int mode, int *colour, int *n_classes) {
+    if (!dims || !colour) return SMPQ_EINVAL;
+    std::vector<int> col;
+    int n = 0;
+    int rc = colour_sites_host(dims, r, mode, col, &n, nullptr);
+    if (rc) return rc;
+    std::copy(col.begin(), col.end(), colour);
+    if (n_classes) *n_classes = n;
+    return SMPQ_OK;
+}
+
+int smpq_build_sources(smpq_ctx *ctx, int r, int mode, int *n_classes) {
+    int rc = check_ctx(ctx, true, false, false);
+    if (rc) return rc;
+    std::string why;
+    std::vector<int> col;
+    int n = 0;
+    if ((rc = colour_sites_host(ctx->dims, r, mode, col, &n, &why))) return set_err(ctx, rc, why);
+    std::vector<int> count(n, 0);
+    for (int c : col) ++count[c];
+    int members = count[0];
+    for (int c = 0; c < n; ++c)
+        if (count[c] != members) return set_err(ctx, SMPQ_EINVAL, "colour classes of unequal size");
+    std::vector<int> mem((size_t)n * members), fill(n, 0);
+    for (int s = 0; s < ctx->V; ++s) mem[(size_t)col[s] * members + fill[col[s]]++] = s;
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    if ((rc = ensure(ctx, ctx->d_colour, (size_t)ctx->V * sizeof(int)))) return rc;
+    if ((rc = ensure(ctx, ctx->d_members, mem.size() * sizeof(int)))) return rc;
+    cudaMemcpyAsync(ctx->d_colour.p, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_members.p, mem.data(), mem.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "build_sources");
+    ctx->colour.swap(col);
+    ctx->r = r;
+    ctx->mode = mode;
+    ctx->n_classes = n;
+    ctx->members = members;
+    ctx->have_sources = true;
+    if (n_classes) *n_classes = n;
+    return SMPQ_OK;
+}
+
+int smpq_dslash(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision, int on_device) {
+    int rc = check_ctx(ctx, true, false, false);
+    if (rc) return rc;
+    if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad dslash arguments");
+    if (precision != SMPQ_FP64 && precision != SMPQ_FP32) return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    cudaStream_t st = ctx->stream;
+    const size_t n = (size_t)ctx->V * 12 * B;
+    const size_t esz = precision == SMPQ_FP64 ? 16 : 8;
+    if ((rc = ensure(ctx, ctx->ws[W_SRC], n * 16 + 2 * n * esz))) return rc;
+    double *abi = (double *)ctx->ws[W_SRC].p;
+    char *tin = (char *)ctx->ws[W_SRC].p + n * 16, *tout = tin + n * esz;
+    const double *din = in;
+    if (!on_device) {
+        cudaMemcpyAsync(abi, in, n * 16, cudaMemcpyHostToDevice, st);
+        din = abi;
+    }
+    const int BC = 1;
+    const void *U = precision == SMPQ_FP64 ? ctx->U64.p : ctx->U32.p;
+    double *dout = on_device ? out : abi;
+    if (precision == SMPQ_FP64) {
+        launch_to_tiled<double>(din, tin, ctx->V, B, BC, st);
+        launch_dslash<double>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+        launch_from_tiled<double>(tout, dout, ctx->V, B, BC, st);
+    } else {
+        launch_to_tiled<float>(din, tin, ctx->V, B, BC, st);
+        launch_dslash<float>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+        launch_from_tiled<float>(tout, dout, ctx->V, B, BC, st);
+    }
+    if (!on_device) cudaMemcpyAsync(out, abi, n * 16, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "dslash");
+    return cuda_check(ctx, cudaGetLastError(), "dslash launch");
+}
+
+int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_device) {
+    int rc = check_ctx(ctx, true, true, false);
+    if (rc) return rc;
+    if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad apply_dov arguments");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    cudaStream_t st = ctx->stream;
+    const size_t n = (size_t)ctx->V * 12 * B;
+    if ((rc = ensure(ctx, ctx->ws[W_SRC], 3 * n * 16))) return rc;
+    if ((rc = ensure(ctx, ctx->ws[W_RHS], 2 * (size_t)B * sizeof(int)))) return rc;
+    double *abi = (double *)ctx->ws[W_SRC].p;
+    double2 *b64 = (double2 *)(abi + 2 * n), *z = b64 + n;
+    const double *din = in;
+    if (!on_device) {
+        cudaMemcpyAsync(abi, in, n * 16, cudaMemcpyHostToDevice, st);
+        din = abi;
+    }
+    const int BC = 1;
+    launch_to_tiled<double>(din, b64, ctx->V, B, BC, st);
+    cudaMemsetAsync(ctx->ws[W_RHS].p, 0, 2 * (size_t)B * sizeof(int), st); // every rhs in support class 0
+    SolveSpec spec{};
+    spec.B = B;
+    spec.BC = BC;
+    spec.prec = SMPQ_FP64;
+    spec.full_support = 1;
+    spec.n_sup = ctx->V;
+    spec.d_supsite = nullptr;
+    spec.d_rhs_class = (const int *)ctx->ws[W_RHS].p;
+    spec.d_src_class = (const int *)ctx->ws[W_RHS].p;
+    spec.d_src_comp = (const int *)ctx->ws[W_RHS].p + B;
+    spec.d_colour = nullptr;
+    spec.d_src_field = (const double *)b64;
+    SolveOut o;
+    if ((rc = multishift_solve(ctx, spec, &o))) return rc;
+    // y = c0 b + sum c_i x_i ; out = b + D_W y
+    launch_axpy(o.y, b64, ctx->c0, n, st);
+    launch_dslash<double>(ctx->geom, ctx->U64.p, o.y, z, B, BC, 0, ctx->opt.kappa, st);
+    launch_axpy(z, b64, 1.0, n, st);
+    double *dout = on_device ? out : abi;
+    launch_from_tiled<double>(z, dout, ctx->V, B, BC, st);
+    if (!on_device) cudaMemcpyAsync(out, abi, n * 16, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "apply_dov");
+    return cuda_check(ctx, cudaGetLastError(), "apply_dov launch");
+}
+
+int smpq_compute_qx(smpq_ctx *ctx, double *q_re, double *q_im, int on_device, double *Q, smpq_stats *stats) {
+    int rc = check_ctx(ctx, true, true, true);
+    if (rc) return rc;
+    if (!q_re || !q_im) return set_err(ctx, SMPQ_EINVAL, "null output");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    std::vector<int> cls(ctx->n_classes);
+    for (int c = 0; c < ctx->n_classes; ++c) cls[c] = c;
+    rc = compute_classes(ctx, cls, q_re, q_im, on_device, stats, true);
+    if (!rc && Q) *Q = ctx->last_Q;
+    return rc;
+}
+
+int smpq_compute_qx_classes(smpq_ctx *ctx, const int *classes, int n, double *q_re, double *q_im, int on_device,
+                            smpq_stats *stats) {
+    int rc = check_ctx(ctx, true, true, true);
+    if (rc) return rc;
+    if (!classes || n < 1 || !q_re || !q_im) return set_err(ctx, SMPQ_EINVAL, "bad class list");
+    std::vector<int> cls(classes, classes + n);
+    std::vector<char> seen(ctx->n_classes, 0);
+    for (int c : cls) {
+        if (c < 0 || c >= ctx->n_classes || seen[c]) return set_err(ctx, SMPQ_EINVAL, "class id out of range or repeated");
+        seen[c] = 1;
+    }
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    return compute_classes(ctx, cls, q_re, q_im, on_device, stats, false);
+}
+
+} // extern "C"

@@ -1,0 +1,161 @@
+// Link packing, SU(3) check, layout conversion and the stand-alone Wilson
+// dslash D_W / D_W^dag (Sec. 2.1, around Eq. 3) used by smpq_dslash.
+#include "wilson.cuh"
+
+// ------------------------------------------------------------------ links
+// U_aos: double[V][4][3][3][2] -> U64/U32: [(mu*9 + e) * V + s] complex
+__global__ void pack_links_kernel(const double2 *__restrict__ Uaos, double2 *__restrict__ U64,
+                                  float2 *__restrict__ U32, int V) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * 36) return;
+    int s = (int)(i / 36), k = (int)(i % 36); // k = mu*9 + e
+    double2 u = Uaos[i];
+    U64[(size_t)k * V + s] = u;
+    U32[(size_t)k * V + s] = make_float2((float)u.x, (float)u.y);
+}
+
+void launch_pack_links(const double *U_aos, double *U64, float *U32, int V, cudaStream_t st) {
+    long n = (long)V * 36;
+    pack_links_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)U_aos, (double2 *)U64,
+                                                                     (float2 *)U32, V);
+}
+
+// max over links of max(|U U^dag - 1|, |det U - 1|), as the bit pattern of a
+// non-negative double (ordered like unsigned integers) for atomicMax.
+__global__ void su3_check_kernel(const double2 *__restrict__ U, int V, unsigned long long *out) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    double err = 0;
+    if (i < (long)V * 4) {
+        int s = (int)(i / 4), mu = (int)(i % 4);
+        double2 u[9];
+        for (int e = 0; e < 9; ++e) u[e] = U[(size_t)(mu * 9 + e) * V + s];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double2 t = make_double2(0, 0);
+                for (int k = 0; k < 3; ++k) t = cfmac(u[b * 3 + k], u[a * 3 + k], t); // (U U^dag)_ab
+                double d = sqrt((t.x - (a == b)) * (t.x - (a == b)) + t.y * t.y);
+                err = fmax(err, d);
+            }
+        // det by cofactor expansion along row 0
+        double2 m0 = csub(cmul(u[4], u[8]), cmul(u[5], u[7]));
+        double2 m1 = csub(cmul(u[3], u[8]), cmul(u[5], u[6]));
+        double2 m2 = csub(cmul(u[3], u[7]), cmul(u[4], u[6]));
+        double2 det = cadd(csub(cmul(u[0], m0), cmul(u[1], m1)), cmul(u[2], m2));
+        err = fmax(err, sqrt((det.x - 1) * (det.x - 1) + det.y * det.y));
+        if (!(err == err)) err = 1e300; // NaN
+    }
+    // block max then one atomic
+    __shared__ double sm[256];
+    sm[threadIdx.x] = err;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sm[0]));
+}
+
+void launch_su3_check(const double *U64, int V, double *dev_maxerr, cudaStream_t st) {
+    cudaMemsetAsync(dev_maxerr, 0, sizeof(double), st);
+    long n = (long)V * 4;
+    su3_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)U64, V,
+                                                                   (unsigned long long *)dev_maxerr);
+}
+
+// ------------------------------------------------------------------ layout conversion
+// ABI [V][12][B] double2  <->  tiled [(j/BC)*12 + c][V][BC] of complex T
+template <typename T>
+__global__ void to_tiled_kernel(const double2 *__restrict__ in, typename cplx_t<T>::type *__restrict__ out, int V,
+                                int B, int BC) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * 12 * B) return;
+    int j = (int)(i % B);
+    long r = i / B;
+    int c = (int)(r % 12);
+    int s = (int)(r / 12);
+    double2 v = in[i];
+    size_t o = ((size_t)((j / BC) * 12 + c) * V + s) * BC + (j % BC);
+    out[o] = mkc<typename cplx_t<T>::type>(v.x, v.y);
+}
+
+template <typename T>
+__global__ void from_tiled_kernel(const typename cplx_t<T>::type *__restrict__ in, double2 *__restrict__ out, int V,
+                                  int B, int BC) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * 12 * B) return;
+    int j = (int)(i % B);
+    long r = i / B;
+    int c = (int)(r % 12);
+    int s = (int)(r / 12);
+    size_t o = ((size_t)((j / BC) * 12 + c) * V + s) * BC + (j % BC);
+    typename cplx_t<T>::type v = in[o];
+    out[i] = make_double2((double)v.x, (double)v.y);
+}
+
+template <typename T> void launch_to_tiled(const double *in, void *out, int V, int B, int BC, cudaStream_t st) {
+    long n = (long)V * 12 * B;
+    to_tiled_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)in,
+                                                                     (typename cplx_t<T>::type *)out, V, B, BC);
+}
+template <typename T> void launch_from_tiled(const void *in, double *out, int V, int B, int BC, cudaStream_t st) {
+    long n = (long)V * 12 * B;
+    from_tiled_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const typename cplx_t<T>::type *)in,
+                                                                       (double2 *)out, V, B, BC);
+}
+template void launch_to_tiled<double>(const double *, void *, int, int, int, cudaStream_t);
+template void launch_to_tiled<float>(const double *, void *, int, int, int, cudaStream_t);
+template void launch_from_tiled<double>(const void *, double *, int, int, int, cudaStream_t);
+template void launch_from_tiled<float>(const void *, double *, int, int, int, cudaStream_t);
+
+// ------------------------------------------------------------------ stand-alone dslash
+template <typename T, bool DAG, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+    dslash_kernel(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ in,
+                  typename cplx_t<T>::type *__restrict__ out, T kappa) {
+    typedef typename cplx_t<T>::type C;
+    int s = blockIdx.x * TileMap<BC>::SPB + threadIdx.x / BC;
+    int jj = threadIdx.x % BC;
+    if (s >= g.V) return;
+    size_t base = (size_t)blockIdx.y * 12 * g.V * BC + jj;
+    const C *pin = in + base;
+    C acc[12];
+    wilson_hop<T, DAG, BC>(g, U, pin, s, acc);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        size_t o = (size_t)(c * g.V + s) * BC;
+        C v = pin[o];
+        v.x -= kappa * acc[c].x;
+        v.y -= kappa * acc[c].y;
+        out[base + o] = v;
+    }
+}
+
+template <typename T, int BC>
+static void dslash_bc(const Geom &g, const void *U, const void *in, void *out, int B, int dagger, double kappa,
+                      cudaStream_t st) {
+    typedef typename cplx_t<T>::type C;
+    dim3 grid((g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB, B / BC);
+    if (dagger)
+        dslash_kernel<T, true, BC><<<grid, TileMap<BC>::THREADS, 0, st>>>(g, (const C *)U, (const C *)in, (C *)out,
+                                                                           (T)kappa);
+    else
+        dslash_kernel<T, false, BC><<<grid, TileMap<BC>::THREADS, 0, st>>>(g, (const C *)U, (const C *)in, (C *)out,
+                                                                            (T)kappa);
+}
+
+template <typename T>
+void launch_dslash(const Geom &g, const void *U, const void *in, void *out, int B, int BC, int dagger, double kappa,
+                   cudaStream_t st) {
+    switch (BC) {
+    case 1: dslash_bc<T, 1>(g, U, in, out, B, dagger, kappa, st); break;
+    case 4: dslash_bc<T, 4>(g, U, in, out, B, dagger, kappa, st); break;
+    case 12: dslash_bc<T, 12>(g, U, in, out, B, dagger, kappa, st); break;
+    case 24: dslash_bc<T, 24>(g, U, in, out, B, dagger, kappa, st); break;
+    case 48: dslash_bc<T, 48>(g, U, in, out, B, dagger, kappa, st); break;
+    default: break;
+    }
+}
+template void launch_dslash<double>(const Geom &, const void *, const void *, void *, int, int, int, double,
+                                    cudaStream_t);
+template void launch_dslash<float>(const Geom &, const void *, const void *, void *, int, int, int, double,
+                                   cudaStream_t);

@@ -1,0 +1,254 @@
+"""Python binding of libsmpq (include/smpq.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the CUDA library; all compute
+runs in the library's kernels.  Arrays may be numpy (host, on_device=0) or
+torch CUDA tensors (device, on_device=1); complex128 arrays are passed as the
+interleaved doubles the ABI expects.  If the compiled library is missing, the
+import fails: there is no other implementation behind these names.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+SMPQ_OK = 0
+SMPQ_EINVAL = -1
+SMPQ_ENOMEM = -2
+SMPQ_ECUDA = -3
+SMPQ_ENOCONV = -4
+SMPQ_EBREAKDOWN = -5
+SMPQ_ETIMEOUT = -6
+SMPQ_ENOTSU3 = -7
+SMPQ_ESTATE = -8
+SMPQ_FP64 = 0
+SMPQ_FP32 = 1
+
+_NAMES = {v: k for k, v in globals().items() if k.startswith("SMPQ_E") or k == "SMPQ_OK"}
+
+
+class SmpqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class smpq_options(ctypes.Structure):
+    _fields_ = [
+        ("kappa", ctypes.c_double),
+        ("npoles", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("reliable_delta", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("rhs_block", ctypes.c_int),
+        ("iters_per_check", ctypes.c_int),
+        ("use_graphs", ctypes.c_int),
+    ]
+
+
+class smpq_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_rhs", ctypes.c_int),
+        ("n_classes", ctypes.c_int),
+        ("n_batches", ctypes.c_int),
+        ("max_iterations", ctypes.c_int),
+        ("total_iterations", ctypes.c_longlong),
+        ("reliable_updates", ctypes.c_int),
+        ("max_resid", ctypes.c_double),
+        ("max_im_q", ctypes.c_double),
+        ("Q", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+        ("total_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = [
+    "smpq_options_default", "smpq_create", "smpq_destroy", "smpq_last_error", "smpq_set_options",
+    "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
+    "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
+    "smpq_compute_qx_classes",
+]
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libsmpq.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libsmpq.so not built; run paper_1901_02211_gb300._build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    PI, PD = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "smpq_options_default": [ctypes.POINTER(smpq_options)],
+        "smpq_create": [ctypes.POINTER(P), I, P, ctypes.POINTER(smpq_options)],
+        "smpq_destroy": [P],
+        "smpq_set_options": [P, ctypes.POINTER(smpq_options)],
+        "smpq_load_gauge": [P, PI, P, I],
+        "smpq_set_spectrum": [P, D, D],
+        "smpq_measure_spectrum": [P, I, PD, PD],
+        "smpq_zolotarev": [I, D, D, PD, P, P, PD],
+        "smpq_get_zolotarev": [P, PD, P, P, PD],
+        "smpq_build_sources": [P, I, I, PI],
+        "smpq_colour_sites": [PI, I, I, P, PI],
+        "smpq_dslash": [P, P, P, I, I, I, I],
+        "smpq_apply_dov": [P, P, P, I, I],
+        "smpq_compute_qx": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
+        "smpq_compute_qx_classes": [P, PI, I, P, P, I, ctypes.POINTER(smpq_stats)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = I
+    L.smpq_last_error.argtypes = [P]
+    L.smpq_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc, ctx=None):
+    if rc != SMPQ_OK:
+        msg = load().smpq_last_error(ctx).decode() if ctx else ""
+        raise SmpqError(rc, msg)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+# ----------------------------------------------------------------------------- thin wrappers (same names)
+
+
+def smpq_options_default():
+    o = smpq_options()
+    _check(load().smpq_options_default(ctypes.byref(o)))
+    return o
+
+
+def smpq_create(device=0, stream=None, options=None):
+    ctx = ctypes.c_void_p()
+    o = options if options is not None else smpq_options_default()
+    _check(load().smpq_create(ctypes.byref(ctx), device, stream, ctypes.byref(o)))
+    return ctx
+
+
+def smpq_destroy(ctx):
+    _check(load().smpq_destroy(ctx))
+
+
+def smpq_last_error(ctx):
+    return load().smpq_last_error(ctx).decode()
+
+
+def smpq_set_options(ctx, options):
+    _check(load().smpq_set_options(ctx, ctypes.byref(options)), ctx)
+
+
+def smpq_load_gauge(ctx, dims, links):
+    d = (ctypes.c_int * 4)(*dims)
+    p, dev = _ptr(links)
+    _check(load().smpq_load_gauge(ctx, d, p, dev), ctx)
+
+
+def smpq_set_spectrum(ctx, lmin2, lmax2):
+    _check(load().smpq_set_spectrum(ctx, lmin2, lmax2), ctx)
+
+
+def smpq_measure_spectrum(ctx, iters=200):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(load().smpq_measure_spectrum(ctx, iters, ctypes.byref(lo), ctypes.byref(hi)), ctx)
+    return lo.value, hi.value
+
+
+def smpq_zolotarev(npoles, a, b):
+    c0, delta = ctypes.c_double(), ctypes.c_double()
+    c = np.zeros(npoles)
+    q = np.zeros(npoles)
+    _check(load().smpq_zolotarev(npoles, a, b, ctypes.byref(c0), c.ctypes.data, q.ctypes.data, ctypes.byref(delta)))
+    return c0.value, c, q, delta.value
+
+
+def smpq_get_zolotarev(ctx, npoles):
+    c0, delta = ctypes.c_double(), ctypes.c_double()
+    c = np.zeros(npoles)
+    q = np.zeros(npoles)
+    _check(load().smpq_get_zolotarev(ctx, ctypes.byref(c0), c.ctypes.data, q.ctypes.data, ctypes.byref(delta)), ctx)
+    return c0.value, c, q, delta.value
+
+
+def smpq_build_sources(ctx, r, mode):
+    n = ctypes.c_int()
+    _check(load().smpq_build_sources(ctx, r, mode, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def smpq_colour_sites(dims, r, mode):
+    d = (ctypes.c_int * 4)(*dims)
+    V = int(np.prod(dims))
+    col = np.zeros(V, dtype=np.int32)
+    n = ctypes.c_int()
+    _check(load().smpq_colour_sites(d, r, mode, col.ctypes.data, ctypes.byref(n)))
+    return col, n.value
+
+
+def smpq_dslash(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
+    pi, di = _ptr(inp)
+    po, do = _ptr(out)
+    if di != do:
+        raise ValueError("in and out must both be host or both be device buffers")
+    _check(load().smpq_dslash(ctx, pi, po, B, int(dagger), precision, di), ctx)
+
+
+def smpq_apply_dov(ctx, inp, out, B):
+    pi, di = _ptr(inp)
+    po, do = _ptr(out)
+    if di != do:
+        raise ValueError("in and out must both be host or both be device buffers")
+    _check(load().smpq_apply_dov(ctx, pi, po, B, di), ctx)
+
+
+def smpq_compute_qx(ctx, q_re, q_im):
+    pr, dr = _ptr(q_re)
+    pm, dm = _ptr(q_im)
+    if dr != dm:
+        raise ValueError("q_re and q_im must both be host or both be device buffers")
+    Q = ctypes.c_double()
+    st = smpq_stats()
+    _check(load().smpq_compute_qx(ctx, pr, pm, dr, ctypes.byref(Q), ctypes.byref(st)), ctx)
+    return Q.value, st.as_dict()
+
+
+def smpq_compute_qx_classes(ctx, classes, q_re, q_im):
+    cl = np.ascontiguousarray(classes, dtype=np.int32)
+    pr, dr = _ptr(q_re)
+    pm, dm = _ptr(q_im)
+    st = smpq_stats()
+    _check(load().smpq_compute_qx_classes(ctx, cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cl.size, pr, pm, dr,
+                                          ctypes.byref(st)), ctx)
+    return st.as_dict()

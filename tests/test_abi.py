@@ -1,0 +1,76 @@
+"""The C ABI library builds, loads without a GPU, exports every declared symbol,
+and its host-side logic (Zolotarev coefficients, colouring, validation) agrees
+with the oracle.  No GPU compute is called here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import probing, zolotarev
+from paper_1901_02211_gb300 import smpq as S
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "smpq.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(smpq_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = S.load()
+    decl = _declared()
+    assert len(decl) >= 16
+    for name in decl:
+        assert hasattr(L, name), name
+    assert set(decl) == set(S.EXPORTS)
+
+
+def test_options_default_are_the_papers():
+    o = S.smpq_options_default()
+    assert o.kappa == 0.21 and o.npoles == 14  # Sec. 2.1
+    assert o.tol == 1e-10 and list(o.bc) == [1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("n,a,b", [(14, 0.0193, 7.0), (14, 1e-3, 8.0), (6, 0.1, 7.0), (20, 1e-4, 10.0)])
+def test_zolotarev_matches_oracle(n, a, b):
+    c0, c, q, d = S.smpq_zolotarev(n, a, b)
+    r0, rc, rq, rd = zolotarev.zolotarev(n, a, b)
+    assert abs(c0 - r0) <= 1e-12 * r0
+    assert np.allclose(c, rc, rtol=1e-11, atol=0)
+    assert np.allclose(q, rq, rtol=1e-11, atol=0)
+    assert abs(d - rd) <= 1e-13  # delta is a difference of two O(1) numbers
+
+
+def test_zolotarev_rejects_bad_interval():
+    with pytest.raises(S.SmpqError):
+        S.smpq_zolotarev(14, 0.0, 1.0)
+    with pytest.raises(S.SmpqError):
+        S.smpq_zolotarev(14, 2.0, 1.0)
+    with pytest.raises(S.SmpqError):
+        S.smpq_zolotarev(33, 0.1, 1.0)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 16), (12, 12, 12, 24)])
+@pytest.mark.parametrize("r,mode", [(2, 0), (4, 0), (2, 1), (2, 2), (4, 2), (4, 1), (3, 0)])
+def test_colouring_matches_oracle(dims, r, mode):
+    try:
+        ref, nref = probing.color_sites(dims, r, mode)
+    except ValueError:
+        with pytest.raises(S.SmpqError) as e:
+            S.smpq_colour_sites(dims, r, mode)
+        assert e.value.code == S.SMPQ_EINVAL
+        return
+    col, n = S.smpq_colour_sites(dims, r, mode)
+    assert n == nref
+    assert np.array_equal(col, ref)
+
+
+def test_colouring_point_sources():
+    dims = (4, 4, 4, 8)
+    col, n = S.smpq_colour_sites(dims, 4, 0)
+    assert n == 256
+    with pytest.raises(S.SmpqError):
+        S.smpq_colour_sites(dims, 8, 0)  # 8 does not divide 4

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: q(x) within 1e-8 absolute per site and Q within 1e-9 for the FP64
+path (the solver stops at relative residual 1e-10; the oracle at 1e-13);
+D_W within 1e-13 (FP64) / 2e-6 relative (FP32 kernel).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from conftest import KAPPA, NPOLES
+from oracle import dirac, native, probing, qx, zolotarev
+from synth import make_config, random_spinor
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "spectra.json")
+
+
+def _spectra():
+    with open(GOLD) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def S():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_02211_gb300 import smpq
+    smpq.load()
+    return smpq
+
+
+def _session(S, **kw):
+    from paper_1901_02211_gb300 import Session
+    return Session(**kw)
+
+
+def _interval(name):
+    sp = _spectra()[name]
+    return 0.98 * sp["lmin2"], 1.02 * sp["lmax2"]
+
+
+def _zolo(a, b):
+    c0, c, q, d = zolotarev.zolotarev(NPOLES, a, b)
+    return (c0, c, q), d
+
+
+# ----------------------------------------------------------------------------- D_W
+
+
+@pytest.mark.parametrize("name", ["flux4", "flux4x8", "flux8x16"])
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1)])
+def test_dslash_fp64(S, name, bc):
+    cfg = make_config(name)
+    V = int(np.prod(cfg["dims"]))
+    psi = random_spinor(np.random.default_rng(1), V, 3)
+    with _session(S, bc=bc) as s:
+        s.load_gauge(cfg["dims"], cfg["U"])
+        for dag in (False, True):
+            got = s.dslash(psi, dagger=dag)
+            ref = native.apply_dw(cfg["U"], dirac.apply_g5(psi) if dag else psi, cfg["dims"], KAPPA, bc)
+            if dag:
+                ref = dirac.apply_g5(ref)
+            assert np.abs(got - ref).max() <= 1e-13
+
+
+def test_dslash_fp32(S):
+    cfg = make_config("flux8x16")
+    V = int(np.prod(cfg["dims"]))
+    psi = random_spinor(np.random.default_rng(2), V, 2)
+    with _session(S) as s:
+        s.load_gauge(cfg["dims"], cfg["U"])
+        got = s.dslash(psi, precision=S.SMPQ_FP32)
+    ref = native.apply_dw(cfg["U"], psi, cfg["dims"], KAPPA)
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------- D_ov, spectrum
+
+
+def test_apply_dov_vs_dense(S, flux4, dense4, zolo4, g5dov4):
+    U, dims = flux4["U"], flux4["dims"]
+    v = random_spinor(np.random.default_rng(3), 256, 2)
+    with _session(S) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(zolo4["a"], zolo4["b"])
+        got = s.apply_dov(v)
+    Dov = dense4["g5"] @ g5dov4
+    ref = (Dov @ v.reshape(3072, 2)).reshape(256, 4, 3, 2)
+    assert np.abs(got - ref).max() <= 1e-9
+
+
+def test_measure_spectrum(S, flux4, dense4):
+    with _session(S) as s:
+        s.load_gauge(flux4["dims"], flux4["U"])
+        lo, hi = s.measure_spectrum(300)
+    l2 = dense4["lam"] ** 2
+    assert l2.min() * (1 - 1e-9) <= lo <= l2.min() * (1 + 1e-4)
+    assert l2.max() * (1 - 1e-4) <= hi <= l2.max() * (1 + 1e-9)
+
+
+def test_zolotarev_of_context_matches_oracle(S, flux4, zolo4):
+    with _session(S) as s:
+        s.load_gauge(flux4["dims"], flux4["U"])
+        s.set_spectrum(zolo4["a"], zolo4["b"])
+        c0, c, q, d = s.zolotarev()
+    assert np.allclose(c, zolo4["c"], rtol=1e-11) and np.allclose(q, zolo4["q"], rtol=1e-11)
+
+
+# ----------------------------------------------------------------------------- q(x) on 4^4 against dense
+
+
+@pytest.mark.parametrize("rhs_block", [1, 0])
+@pytest.mark.parametrize("r,mode", [(2, 0), (2, 1), (2, 2), (4, 2)])
+def test_qx_4x4_fp64_vs_dense(S, flux4, zolo4, g5dov4, r, mode, rhs_block):
+    if rhs_block == 1 and (r, mode) != (2, 0):
+        pytest.skip("one-rhs path checked on one scheme")
+    U, dims = flux4["U"], flux4["dims"]
+    colour, n = probing.color_sites(dims, r, mode)
+    ref = qx.dense_smp_qx(g5dov4, colour)
+    with _session(S, rhs_block=rhs_block) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(zolo4["a"], zolo4["b"])
+        assert s.build_sources(r, mode) == n
+        q, Q, st = s.compute_qx()
+    assert np.abs(q - ref).max() <= 1e-8
+    assert abs(Q - ref.real.sum()) <= 1e-9
+    assert st["max_resid"] <= 1e-10
+    assert abs(st["max_im_q"] - np.abs(ref.imag).max()) <= 1e-8
+
+
+def test_exact_trace_point_sources_4x4(S, flux4, zolo4, g5dov4):
+    """r = n_mu: every set is one site, 3072 point sources (Eq. 5); Q = 1."""
+    U, dims = flux4["U"], flux4["dims"]
+    ref = qx.dense_smp_qx(g5dov4, np.arange(256))
+    with _session(S) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(zolo4["a"], zolo4["b"])
+        assert s.build_sources(4, 0) == 256
+        q, Q, st = s.compute_qx()
+    assert st["n_rhs"] == 3072
+    assert np.abs(q - ref).max() <= 1e-8
+    assert abs(Q - 1.0) <= 1e-8 + 6 * 256 * zolo4["delta"]
+    assert st["max_im_q"] <= 1e-10
+
+
+def test_unit_links_give_zero(S):
+    dims = (4, 4, 4, 4)
+    U = np.zeros((256, 4, 3, 3), dtype=np.complex128)
+    U[:] = np.eye(3)
+    with _session(S) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(0.2, 7.5)
+        for mode in (0, 1, 2):
+            s.build_sources(2, mode)
+            q, Q, st = s.compute_qx()
+            assert np.abs(q).max() <= 1e-11
+
+
+# ----------------------------------------------------------------------------- 8^3 x 16 against the oracle (sampled classes)
+
+
+@pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_qx_8x16_sampled(S, r, classes, prec):
+    cfg = make_config("flux8x16")
+    U, dims = cfg["U"], cfg["dims"]
+    a, b = _interval("flux8x16")
+    zolo, delta = _zolo(a, b)
+    colour, n = probing.color_sites(dims, r, 0)
+    ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=classes, batch_colours=len(classes))
+    precision = S.SMPQ_FP64 if prec == "fp64" else S.SMPQ_FP32
+    with _session(S, precision=precision) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(a, b)
+        s.build_sources(r, 0)
+        q, Q, st = s.compute_qx(classes=classes)
+    mask = np.isin(colour, classes)
+    err = np.abs(q[mask] - ref[mask]).max()
+    print("8^3x16 r=%d %s: max |dq| = %.3e, iterations %d, reliable updates %d" % (
+        r, prec, err, st["max_iterations"], st["reliable_updates"]))
+    tol = 1e-8 if prec == "fp64" else 1e-5
+    assert err <= tol
+    assert abs(Q - ref.real[mask].sum()) <= (1e-9 if prec == "fp64" else 1e-4)
+
+
+# ----------------------------------------------------------------------------- host/device buffers, determinism, errors
+
+
+def test_device_buffers_and_determinism(S, flux4, zolo4):
+    with _session(S) as s:
+        s.load_gauge(flux4["dims"], flux4["U"])
+        s.set_spectrum(zolo4["a"], zolo4["b"])
+        s.build_sources(2, 0)
+        q1, Q1, _ = s.compute_qx()
+        q2, Q2, _ = s.compute_qx()
+        qd, Qd, _ = s.compute_qx(device=True)
+    assert np.array_equal(q1, q2) and Q1 == Q2
+    assert np.array_equal(qd.cpu().numpy(), q1) and Qd == Q1
+
+
+def test_error_codes(S, flux4):
+    from paper_1901_02211_gb300 import smpq
+    with _session(S) as s:
+        with pytest.raises(smpq.SmpqError) as e:
+            s.build_sources(2, 0)
+        assert e.value.code == smpq.SMPQ_ESTATE
+        bad = flux4["U"].copy()
+        bad[3, 1] *= 1.01
+        with pytest.raises(smpq.SmpqError) as e:
+            s.load_gauge(flux4["dims"], bad)
+        assert e.value.code == smpq.SMPQ_ENOTSU3
+        s.load_gauge(flux4["dims"], flux4["U"])
+        with pytest.raises(smpq.SmpqError) as e:
+            s.build_sources(3, 0)
+        assert e.value.code == smpq.SMPQ_EINVAL
+        s.build_sources(2, 0)
+        with pytest.raises(smpq.SmpqError) as e:
+            s.compute_qx()
+        assert e.value.code == smpq.SMPQ_ESTATE  # no spectrum yet
+        s.set_spectrum(0.02, 7.0)
+        s.set_options(max_iter=5, iters_per_check=5)
+        with pytest.raises(smpq.SmpqError) as e:
+            s.compute_qx()
+        assert e.value.code == smpq.SMPQ_ENOCONV
