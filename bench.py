@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the SMP topological-charge-density path on one GB300.
+
+Workload (a "step"): q(x) and Q for every site of the 8^3 x 16 quantised-flux
+configuration (Q = 2, noise 0.1, random gauge transform), symmetric
+multi-probing r_min = 4, Normal mode: 256 colour classes x 12 = 3072 sources,
+each a 14-shift multi-shift CG to relative residual 1e-10 (kappa = 0.21,
+14-pole Zolotarev), then the gamma_5 contraction and Q.
+
+Metric: q(x) sites/s = sites of the lattice / step time.
+  value : mixed-precision batched path (FP32 dslash and vectors, FP64 reliable
+          updates, all 3072 sources in one batch), inputs resident on the GPU;
+  e2e   : the same call with host buffers: gauge field uploaded from pinned
+          host memory and q(x) read back every step;
+  fp64_plain / fp64_batched : the FP64 path one source at a time / batched,
+          timed on a sample of classes and scaled to all classes;
+  roofline : the dominant solver kernel's algorithmic bytes / CUDA-event time;
+  cpu_baseline : the FP64 oracle on the host cores on one class (12 sources).
+
+Multi-GPU (torchrun, N ranks): every rank evaluates its own configuration
+(independent problems, no collective on the data path) -> weak scaling.
+`--impl reference` times the CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = "flux8x16"
+R_MIN, MODE = 4, 0
+KAPPA = 0.21
+
+
+def _spectrum(name):
+    with open(os.path.join(ROOT, "tests", "golden", "spectra.json")) as f:
+        sp = json.load(f)[name]
+    return 0.98 * sp["lmin2"], 1.02 * sp["lmax2"]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        hbm = d.get("hbm_gbs") or d.get("hbm_GBs")
+        if hbm:
+            return float(hbm), "measured"
+    return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1901_02211_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, B):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("src_hash") != _src_hash():
+        return None
+    # scale a smaller capture to this launch by the sources processed
+    return float(e["dram_bytes_per_launch"]) * B / float(e["B"])
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = "/tmp/smpq_clocks_%d.csv" % os.getpid()
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(U, dims, a, b, n_classes=1, tol=1e-10):
+    """FP64 oracle on `n_classes` colour classes (12 sources each); returns (sites/s, sites, sec, threads)."""
+    from oracle import native, probing, qx, zolotarev
+    c0, c, q, _ = zolotarev.zolotarev(14, a, b)
+    colour, n = probing.color_sites(dims, R_MIN, MODE)
+    classes = list(range(n_classes))
+    t0 = time.perf_counter()
+    qv, st = qx.smp_qx(U, dims, KAPPA, (c0, c, q), colour, n, tol=tol, colours=classes, batch_colours=n_classes)
+    dt = time.perf_counter() - t0
+    sites = int(np.isin(colour, classes).sum())
+    return sites / dt, sites, dt, native.threads()
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from oracle import native
+    from synth import make_config
+    native.build()
+    cfg = make_config(CONFIG)
+    U, dims = cfg["U"], cfg["dims"]
+    a, b = _spectrum(CONFIG)
+    V = int(np.prod(dims))
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; bounded steps only
+    vals = []
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1)
+        vals.append(v)
+        t_all += dt
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * V / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "8^3x16 flux Q=2 noise 0.1, SMP r_min=4 mode 0, 3072 sources x 14 shifts, tol 1e-10",
+                   "sample": "1 colour class (12 sources, 32 sites) per step"},
+        "cpu_baseline": {"value": value, "unit": "sites/s", "cores": thr, "kind": "oracle",
+                         "sample": "1 of 256 colour classes per step (12 sources, 32 sites), FP64, tol 1e-10"},
+        "e2e": {"value": value, "unit": "sites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1901_02211_gb300 import Session, smpq
+    from synth import CONFIGS, make_config
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream().cuda_stream
+
+    name = CONFIG
+    cfg = make_config(name)
+    if rank > 0:  # an independent configuration per rank (same shape and recipe, other seeds)
+        p = dict(CONFIGS[name])
+        p["seed_noise"] += 100 * rank
+        p["seed_gauge"] += 100 * rank
+        CONFIGS[name + "_r%d" % rank] = p
+        cfg = make_config(name + "_r%d" % rank)
+    U, dims = cfg["U"], cfg["dims"]
+    V = int(np.prod(dims))
+    a, b = _spectrum(CONFIG)
+    prec = smpq.SMPQ_FP32 if args.precision == "fp32" else smpq.SMPQ_FP64
+
+    s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
+                use_graphs=1, profile=1)
+    s.load_gauge(dims, U)
+    s.set_spectrum(a, b)
+    n_classes = s.build_sources(R_MIN, MODE)
+    q_re = torch.zeros(V, dtype=torch.float64, device="cuda")
+    q_im = torch.zeros(V, dtype=torch.float64, device="cuda")
+
+    def step():
+        return smpq.smpq_compute_qx(s.ctx, q_re, q_im)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    stats = []
+    with Clocks(dev) as clk:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            Q, st = step()
+            stats.append(st)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    value = ws * V / (ms / 1000.0)
+    clocks = clk.summary()
+
+    # dominant kernel: average CUDA-event duration per launch over the timed steps
+    a_ms = sum(x["dslash_ms"] for x in stats)
+    a_n = sum(x["dslash_launches"] for x in stats)
+    b_ms = sum(x["update_ms"] for x in stats)
+    b_n = sum(x["update_launches"] for x in stats)
+    B = stats[-1]["n_rhs"] // max(1, stats[-1]["n_batches"])
+    esz = 8 if prec == smpq.SMPQ_FP32 else 16
+    link = 4 * 9 * esz
+    kern = {
+        "k_apply_a": dict(ms=a_ms / max(a_n, 1), n=a_n, share_ms=a_ms, bytes=V * B * 24 * esz + V * link),
+        "k_apply_b": dict(ms=b_ms / max(b_n, 1), n=b_n, share_ms=b_ms,
+                          bytes=V * B * (6 if prec == smpq.SMPQ_FP32 else 4) * 12 * esz + V * link),
+    }
+    dom = max(kern, key=lambda k: kern[k]["share_ms"])
+    peak, peak_kind = _peaks()
+    ach = kern[dom]["bytes"] / (kern[dom]["ms"] / 1000.0) / 1e9
+    traffic = _traffic(dom, B)
+    launches = sum(x["kernel_launches"] for x in stats)
+
+    # e2e: host buffers, gauge upload + read-back every step
+    Upin = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
+    hq_re = torch.zeros(V, dtype=torch.float64).pin_memory()
+    hq_im = torch.zeros(V, dtype=torch.float64).pin_memory()
+    s2 = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
+                 use_graphs=1)
+    s2.load_gauge(dims, Upin.numpy())
+    s2.set_spectrum(a, b)
+    s2.build_sources(R_MIN, MODE)
+
+    def e2e_step():
+        smpq.smpq_load_gauge(s2.ctx, dims, Upin)
+        s2.set_spectrum(a, b)
+        s2.build_sources(R_MIN, MODE)
+        return smpq.smpq_compute_qx(s2.ctx, hq_re, hq_im)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0.record()
+    t0 = time.perf_counter()
+    n_e2e = max(1, args.steps)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max(e0.elapsed_time(e1), 1000 * (time.perf_counter() - t0)) / n_e2e
+    e2e_val = ws * V / (e2e_ms / 1000.0)
+    s2.close()
+
+    out = {}
+    if rank == 0 and not args.no_baselines:
+        # FP64 one-source-at-a-time path and FP64 batched path on a sample of classes
+        sample = list(range(0, n_classes, n_classes // 2))[:2]
+        for key, blk in (("fp64_plain", 1), ("fp64_batched", 0)):
+            s3 = Session(device=dev, stream=stream, precision=smpq.SMPQ_FP64, tol=1e-10, rhs_block=blk,
+                         iters_per_check=10, use_graphs=1)
+            s3.load_gauge(dims, U)
+            s3.set_spectrum(a, b)
+            s3.build_sources(R_MIN, MODE)
+            cls = sample if blk == 1 else list(range(0, n_classes, 8))
+            s3.compute_qx(classes=cls[:1])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q, Qs, st3 = s3.compute_qx(classes=cls)
+            dt = time.perf_counter() - t0
+            s3.close()
+            per_class = dt / len(cls)
+            out[key] = {"value": V / (per_class * n_classes), "unit": "sites/s", "extrapolated": True,
+                        "sample": "%d of %d classes (%d sources), %.3f s" % (len(cls), n_classes, 12 * len(cls), dt),
+                        "max_iterations": st3["max_iterations"]}
+        if not args.no_cpu:
+            v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1)
+            out["cpu_baseline"] = {"value": v, "unit": "sites/s", "cores": thr, "kind": "oracle",
+                                   "sample": "1 of %d colour classes (12 sources, %d sites), FP64 tol 1e-10, %.1f s"
+                                             % (n_classes, sites, dt)}
+    if rank == 0:
+        st = stats[-1]
+        line = {
+            "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == smpq.SMPQ_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": "8^3x16 flux Q=2 noise 0.1 + gauge transform, SMP r_min=4 mode 0, "
+                                   "256 classes x 12 = 3072 sources x 14 shifts, tol 1e-10",
+                       "precision": "FP32 dslash/vectors + FP64 reliable updates" if prec == smpq.SMPQ_FP32
+                       else "FP64", "batch": B, "l2": "inputs larger than L2 (each solver vector %.1f GB)"
+                       % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": "sites/s", "h2d_bytes_per_step": int(U.nbytes),
+                    "d2h_bytes_per_step": int(2 * V * 8 + 16)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": kern[dom]["bytes"],
+                         "avg_launch_ms": kern[dom]["ms"], "launches": kern[dom]["n"]},
+            "solver": {"iterations": st["max_iterations"], "reliable_updates": st["reliable_updates"],
+                       "max_resid": st["max_resid"], "Q": st["Q"], "max_im_q": st["max_im_q"],
+                       "kernel_ms": {k: v["share_ms"] / args.steps for k, v in kern.items()}},
+        }
+        line.update(out)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="smpq", choices=["smpq", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -68,6 +68,7 @@ typedef struct {
     int rhs_block;         /* right-hand sides per solve batch (multiple of 12; 0 = automatic) */
     int iters_per_check;   /* CG iterations launched between host convergence checks */
     int use_graphs;        /* capture those iterations in a CUDA graph */
+    int profile;           /* time every D_W / D_W^dag launch of the solver with CUDA events */
 } smpq_options;
 
 typedef struct {
@@ -82,11 +83,16 @@ typedef struct {
     double Q;               /* sum_x Re q(x) over the processed sites */
     double solve_ms;        /* device time of the solves (CUDA events) */
     double total_ms;        /* device time of the whole call */
+    long long kernel_launches; /* CUDA kernels launched by the call (graph nodes included) */
+    double dslash_ms;       /* profile: summed time of the t = D_W p launches */
+    long long dslash_launches;
+    double update_ms;       /* profile: summed time of the r -= alpha (D_W^dag t + s0 p) launches */
+    long long update_launches;
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 0.1, periodic bc, automatic batching,
- * 10 iterations per check, graphs on. */
+ * 10 iterations per check, graphs on, profiling off. */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.

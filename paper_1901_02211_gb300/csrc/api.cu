@@ -134,6 +134,9 @@ size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
 int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re, double *q_im, int on_device,
                     smpq_stats *stats, bool full) {
     cudaStream_t st = ctx->stream;
+    ctx->launches = 0;
+    ctx->prof_a_ms = ctx->prof_b_ms = 0;
+    ctx->prof_a_n = ctx->prof_b_n = 0;
     cudaEventRecord(ctx->evA, st);
     int rc;
     // star support of every class
@@ -197,6 +200,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         rc = multishift_solve(ctx, spec, &out);
         if (rc) return rc;
         launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y, st);
+        ctx->launches += 2;
         launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class, d_src_comp,
                         (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa, (double2 *)ctx->ws[W_QTERM].p,
                         st);
@@ -231,6 +235,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         cudaMemcpyAsync(d_sites, sites.data(), sites.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     }
     launch_qtotal(dq_re, dq_im, full ? nullptr : d_sites, full ? ctx->V : (int)sites.size(), d_tot, st);
+    ctx->launches += 3 + 1; // qsum, qtotal, star support (+1)
     double tot[2];
     cudaMemcpyAsync(tot, d_tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (!on_device) {
@@ -267,6 +272,11 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->Q = tot[0];
         stats->solve_ms = solve_ms;
         stats->total_ms = tms;
+        stats->kernel_launches = ctx->launches;
+        stats->dslash_ms = ctx->prof_a_ms;
+        stats->dslash_launches = ctx->prof_a_n;
+        stats->update_ms = ctx->prof_b_ms;
+        stats->update_launches = ctx->prof_b_n;
     }
     ctx->last_Q = tot[0];
     return SMPQ_OK;
@@ -290,6 +300,7 @@ int smpq_options_default(smpq_options *o) {
     o->rhs_block = 0;
     o->iters_per_check = 10;
     o->use_graphs = 1;
+    o->profile = 0;
     return SMPQ_OK;
 }
 
@@ -343,6 +354,7 @@ int smpq_destroy(smpq_ctx *ctx) {
         cudaEventDestroy(ctx->ev2);
         cudaEventDestroy(ctx->evA);
         cudaEventDestroy(ctx->evB);
+        for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
         cudaStreamDestroy(ctx->stream);
     }
     delete ctx;

@@ -555,20 +555,48 @@ template <typename T, int BC> struct Solver {
             k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps, y,
                                                 sc, sp, Gs, 1);
 
-        auto iteration = [&]() {
+        const bool prof = ctx->opt.profile != 0;
+        const int chk = std::max(1, ctx->opt.iters_per_check);
+        if (prof) {
+            while ((int)ctx->prof_ev.size() < 4 * chk) {
+                cudaEvent_t ev;
+                if (cudaEventCreate(&ev) != cudaSuccess) return cuda_check(ctx, cudaGetLastError(), "event");
+                ctx->prof_ev.push_back(ev);
+            }
+        }
+        const int per_iter = 5 + (spec.n_sup > 0 ? 1 : 0);
+        auto iteration = [&](int k) {
+            if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
             k_apply_a<T, BC><<<grid, TH, 0, st>>>(g, U, p, t, kappa, part0, part1, G);
+            if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
             s1_kernel<<<sblocks, 128, 0, st>>>(B, BC, G, part0, part1, sc, sp);
+            if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
             if (rel)
                 k_apply_b<T, BC, true><<<grid, TH, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2, G);
             else
                 k_apply_b<T, BC, false><<<grid, TH, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2, G);
+            if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
             s2_kernel<<<sblocks, 128, 0, st>>>(B, BC, G, part2, sc, sp, tol2, delta2);
             if (spec.n_sup > 0)
                 k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps,
                                                     y, sc, sp, Gs, 0);
             k_update_p<T, BC><<<grid, TH, 0, st>>>(V, r, p, sc.beta, sc.upd_rhs, G);
         };
+        // after the stream is synchronised: add the event timings of the last `n` iterations
+        auto collect = [&](int n) {
+            if (!prof) return;
+            for (int k = 0; k < n; ++k) {
+                float a = 0, b = 0;
+                cudaEventElapsedTime(&a, ctx->prof_ev[4 * k], ctx->prof_ev[4 * k + 1]);
+                cudaEventElapsedTime(&b, ctx->prof_ev[4 * k + 2], ctx->prof_ev[4 * k + 3]);
+                ctx->prof_a_ms += a;
+                ctx->prof_b_ms += b;
+            }
+            ctx->prof_a_n += n;
+            ctx->prof_b_n += n;
+        };
         auto reliable = [&]() {
+            ctx->launches += 4;
             k_rel_accum<T, BC><<<grid, TH, 0, st>>>(V, xhi, xlo, G);
             launch_dslash<double>(g, ctx->U64.p, xhi, t64, B, BC, 0, ctx->opt.kappa, st);
             k_rel_resid<T, BC><<<grid, TH, 0, st>>>(g, (const double2 *)ctx->U64.p, t64, xhi, src, r, sp.s0,
@@ -577,13 +605,12 @@ template <typename T, int BC> struct Solver {
             s_rel<<<sblocks, 128, 0, st>>>(B, BC, G, part2, sc, sp, tol2, base_shift);
         };
 
-        const int chk = std::max(1, ctx->opt.iters_per_check);
         cudaGraphExec_t gexec = nullptr;
         bool graph_ok = false;
         if (ctx->opt.use_graphs && fixed_iters == 0) {
             cudaGraph_t graph;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                for (int k = 0; k < chk; ++k) iteration();
+                for (int k = 0; k < chk; ++k) iteration(k);
                 if (cudaStreamEndCapture(st, &graph) == cudaSuccess) {
                     if (cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess) graph_ok = true;
                     cudaGraphDestroy(graph);
@@ -594,18 +621,25 @@ template <typename T, int BC> struct Solver {
         int *hflags = nullptr;
         cudaMallocHost(&hflags, 4 * sizeof(int));
         int iters = 0, nrel = 0, status = SMPQ_OK;
+        ctx->launches += 2 + (spec.n_sup > 0 ? 1 : 0);
         if (fixed_iters > 0) {
-            for (int k = 0; k < fixed_iters; ++k) iteration();
+            for (int k = 0; k < fixed_iters; ++k) {
+                iteration(prof ? k % chk : 0);
+                if (prof && k % chk == chk - 1) { cudaStreamSynchronize(st); collect(chk); }
+            }
+            ctx->launches += (long long)fixed_iters * per_iter;
             iters = fixed_iters;
         } else {
             for (;;) {
                 if (graph_ok) cudaGraphLaunch(gexec, st);
                 else
-                    for (int k = 0; k < chk; ++k) iteration();
+                    for (int k = 0; k < chk; ++k) iteration(k);
+                ctx->launches += (long long)chk * per_iter;
                 iters += chk;
                 cudaMemcpyAsync(hflags, sc.flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
                 cudaError_t e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
+                collect(chk);
                 if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
                 bool done = hflags[0] == 0;
                 if (rel && (hflags[1] || done)) {

@@ -140,6 +140,11 @@ struct smpq_ctx {
     // workspace (grown on demand)
     std::vector<Buf> ws;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evA = nullptr, evB = nullptr;
+    // launch accounting and optional per-launch timing of the solver's D_W kernels
+    long long launches = 0;
+    std::vector<cudaEvent_t> prof_ev; // 4 per iteration of one check interval
+    double prof_a_ms = 0, prof_b_ms = 0;
+    long long prof_a_n = 0, prof_b_n = 0;
 };
 
 // workspace slots of smpq_ctx::ws

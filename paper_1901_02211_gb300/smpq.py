@@ -48,6 +48,7 @@ class smpq_options(ctypes.Structure):
         ("rhs_block", ctypes.c_int),
         ("iters_per_check", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -64,6 +65,11 @@ class smpq_stats(ctypes.Structure):
         ("Q", ctypes.c_double),
         ("solve_ms", ctypes.c_double),
         ("total_ms", ctypes.c_double),
+        ("kernel_launches", ctypes.c_longlong),
+        ("dslash_ms", ctypes.c_double),
+        ("dslash_launches", ctypes.c_longlong),
+        ("update_ms", ctypes.c_double),
+        ("update_launches", ctypes.c_longlong),
     ]
 
     def as_dict(self):
