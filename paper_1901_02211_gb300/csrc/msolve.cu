@@ -587,8 +587,11 @@ template <typename T, int BC> struct Solver {
             if (!prof) return;
             for (int k = 0; k < n; ++k) {
                 float a = 0, b = 0;
-                cudaEventElapsedTime(&a, ctx->prof_ev[4 * k], ctx->prof_ev[4 * k + 1]);
-                cudaEventElapsedTime(&b, ctx->prof_ev[4 * k + 2], ctx->prof_ev[4 * k + 3]);
+                if (cudaEventElapsedTime(&a, ctx->prof_ev[4 * k], ctx->prof_ev[4 * k + 1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&b, ctx->prof_ev[4 * k + 2], ctx->prof_ev[4 * k + 3]) != cudaSuccess) {
+                    cudaGetLastError();
+                    a = b = 0;
+                }
                 ctx->prof_a_ms += a;
                 ctx->prof_b_ms += b;
             }
@@ -607,7 +610,8 @@ template <typename T, int BC> struct Solver {
 
         cudaGraphExec_t gexec = nullptr;
         bool graph_ok = false;
-        if (ctx->opt.use_graphs && fixed_iters == 0) {
+        // (profiling records CUDA events between launches, so it runs without a graph)
+        if (ctx->opt.use_graphs && fixed_iters == 0 && !prof) {
             cudaGraph_t graph;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 for (int k = 0; k < chk; ++k) iteration(k);
