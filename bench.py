@@ -222,8 +222,14 @@ def run_gpu(args):
     q_re = torch.zeros(V, dtype=torch.float64, device="cuda")
     q_im = torch.zeros(V, dtype=torch.float64, device="cuda")
 
+    sub = list(range(args.classes)) if args.classes else None
+    V_step = V if sub is None else V * len(sub) // n_classes  # sites whose q(x) one step produces
+
     def step():
-        return smpq.smpq_compute_qx(s.ctx, q_re, q_im)
+        if sub is None:
+            return smpq.smpq_compute_qx(s.ctx, q_re, q_im)
+        st = smpq.smpq_compute_qx_classes(s.ctx, sub, q_re, q_im)
+        return st["Q"], st
 
     for _ in range(args.warmup):
         step()
@@ -247,7 +253,7 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
         ms = float(t.item())
-    value = ws * V / (ms / 1000.0)
+    value = ws * V_step / (ms / 1000.0)
     clocks = clk.summary()
 
     # dominant kernel: average CUDA-event duration per launch over the timed steps
@@ -269,7 +275,25 @@ def run_gpu(args):
     traffic = _traffic(dom, B)
     launches = sum(x["kernel_launches"] for x in stats)
 
-    # e2e: host buffers, gauge upload + read-back every step
+    e2e_val = None
+    if args.no_e2e:
+        pass
+    else:
+        e2e_val = _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws)
+    out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream) if rank == 0 else {}
+    if rank == 0:
+        _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak,
+                peak_kind, traffic, stats, out, sub)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws):
+    """Same metric through host buffers: pinned gauge upload + q(x) read-back each step."""
+    import torch
+
+    from paper_1901_02211_gb300 import Session, smpq
     Upin = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
     hq_re = torch.zeros(V, dtype=torch.float64).pin_memory()
     hq_im = torch.zeros(V, dtype=torch.float64).pin_memory()
@@ -287,6 +311,8 @@ def run_gpu(args):
 
     e2e_step()
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     t0 = time.perf_counter()
     n_e2e = max(1, args.steps)
@@ -295,11 +321,16 @@ def run_gpu(args):
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = max(e0.elapsed_time(e1), 1000 * (time.perf_counter() - t0)) / n_e2e
-    e2e_val = ws * V / (e2e_ms / 1000.0)
     s2.close()
+    return ws * V / (e2e_ms / 1000.0)
 
+
+def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
+    import torch
+
+    from paper_1901_02211_gb300 import Session, smpq
     out = {}
-    if rank == 0 and not args.no_baselines:
+    if not args.no_baselines:
         # FP64 one-source-at-a-time path and FP64 batched path on a sample of classes
         sample = list(range(0, n_classes, n_classes // 2))[:2]
         for key, blk in (("fp64_plain", 1), ("fp64_batched", 0)):
@@ -324,7 +355,13 @@ def run_gpu(args):
             out["cpu_baseline"] = {"value": v, "unit": "sites/s", "cores": thr, "kind": "oracle",
                                    "sample": "1 of %d colour classes (12 sources, %d sites), FP64 tol 1e-10, %.1f s"
                                              % (n_classes, sites, dt)}
-    if rank == 0:
+    return out
+
+
+def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak, peak_kind,
+            traffic, stats, out, sub):
+    from paper_1901_02211_gb300 import smpq
+    if True:
         st = stats[-1]
         line = {
             "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": ws, "steps": args.steps,
@@ -336,8 +373,9 @@ def run_gpu(args):
                        else "FP64", "batch": B, "l2": "inputs larger than L2 (each solver vector %.1f GB)"
                        % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
             "clocks": clocks,
-            "e2e": {"value": e2e_val, "unit": "sites/s", "h2d_bytes_per_step": int(U.nbytes),
-                    "d2h_bytes_per_step": int(2 * V * 8 + 16)},
+            "e2e": None if e2e_val is None else {
+                "value": e2e_val, "unit": "sites/s", "h2d_bytes_per_step": int(U.nbytes),
+                "d2h_bytes_per_step": int(2 * V * 8 + 16)},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
@@ -347,11 +385,10 @@ def run_gpu(args):
                        "max_resid": st["max_resid"], "Q": st["Q"], "max_im_q": st["max_im_q"],
                        "kernel_ms": {k: v["share_ms"] / args.steps for k, v in kern.items()}},
         }
+        if sub is not None:
+            line["config"]["workload"] += " (profiling subset: first %d classes)" % len(sub)
         line.update(out)
         print(json.dumps(line), flush=True)
-    s.close()
-    if ws > 1:
-        dist.destroy_process_group()
 
 
 def main():
@@ -363,6 +400,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--classes", type=int, default=0, help="profiling: only the first N colour classes")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

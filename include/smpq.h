@@ -91,7 +91,7 @@ typedef struct {
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
- * max_iter 5000, FP64, reliable_delta 0.1, periodic bc, automatic batching,
+ * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
  * 10 iterations per check, graphs on, profiling off. */
 int smpq_options_default(smpq_options *opt);
 

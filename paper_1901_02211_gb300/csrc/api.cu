@@ -295,7 +295,7 @@ int smpq_options_default(smpq_options *o) {
     o->tol = 1e-10;
     o->max_iter = 5000;
     o->precision = SMPQ_FP64;
-    o->reliable_delta = 0.1;
+    o->reliable_delta = 1e-3;
     for (int mu = 0; mu < 4; ++mu) o->bc[mu] = 1;
     o->rhs_block = 0;
     o->iters_per_check = 10;

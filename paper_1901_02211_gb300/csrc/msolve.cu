@@ -27,7 +27,11 @@
 
 namespace {
 
-constexpr int TARGET_BLOCKS = 152 * 8;
+// Each block of a lattice kernel handles TPB consecutive tiles of one RHS
+// tile, and blocks are numbered site-major inside an RHS tile, so the blocks
+// resident at any moment cover a narrow band of the lattice for few RHS tiles:
+// the +-t neighbours (V/n_t sites away) are still in L2 when they are read.
+constexpr int TPB = 4;
 
 template <typename T> struct Prec;
 template <> struct Prec<double> { static constexpr int id = SMPQ_FP64; };
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     double acc = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
 #pragma unroll
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     double at = 0, ap = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
         C acc[12];
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const T a = (T)alpha[j];
     const T sh = (T)s0;
     double ar = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
         C acc[12];
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const size_t base = (size_t)chunk * 12 * V * BC + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     const T b = (T)beta[j];
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= V) continue;
 #pragma unroll
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const size_t sbase = (size_t)chunk * 12 * n_sup * BC + jj;
     const size_t sstride = (size_t)B * 12 * n_sup; // one shift
     const int ntiles = (n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int k = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (k >= n_sup) continue;
         int site = supsite ? supsite[(size_t)cls * n_sup + k] : k;
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const int jj = threadIdx.x % BC, chunk = blockIdx.y;
     const size_t base = (size_t)chunk * 12 * V * BC + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= V) continue;
 #pragma unroll
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     double ar = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
         double2 acc[12];
@@ -330,18 +334,32 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
 }
 
-// ------------------------------------------------------------------ scalar kernels (one thread per rhs)
-__device__ __forceinline__ double sum_part(const double *part, int j, int BC, int G) {
-    int chunk = j / BC, jj = j % BC;
+// ------------------------------------------------------------------ scalar kernels (one block per rhs)
+constexpr int SCAL_THREADS = 128;
+
+// sum over blocks of the partials of rhs j: strided per-thread sums, then a
+// fixed tree (deterministic)
+__device__ __forceinline__ double part_sum(const double *part, int j, int BC, int G, double *sm) {
+    const int chunk = j / BC, jj = j % BC;
     double s = 0;
-    for (int b = 0; b < G; ++b) s += part[((size_t)chunk * G + b) * BC + jj];
-    return s;
+    for (int b = threadIdx.x; b < G; b += SCAL_THREADS) s += part[((size_t)chunk * G + b) * BC + jj];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = SCAL_THREADS / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+        __syncthreads();
+    }
+    double r = sm[0];
+    __syncthreads();
+    return r;
 }
 
-__global__ void s_init(int B, int BC, int G, const double *part_b, Scal sc, ShiftParams sp, double tol) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= B) return;
-    double bb = sum_part(part_b, j, BC, G);
+__global__ void __launch_bounds__(SCAL_THREADS)
+    s_init(int B, int BC, int G, const double *part_b, Scal sc, ShiftParams sp, double tol) {
+    __shared__ double sm[SCAL_THREADS];
+    const int j = blockIdx.x;
+    double bb = part_sum(part_b, j, BC, G, sm);
+    if (threadIdx.x) return;
     sc.bb[j] = bb;
     sc.rr[j] = bb;
     sc.rr_ref[j] = bb;
@@ -367,23 +385,25 @@ __global__ void s_init(int B, int BC, int G, const double *part_b, Scal sc, Shif
     if (any) atomicAdd(&sc.flags[0], 1);
 }
 
-__global__ void s1_kernel(int B, int BC, int G, const double *part_t, const double *part_p, Scal sc, ShiftParams sp) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(SCAL_THREADS)
+    s1_kernel(int B, int BC, int G, const double *part_t, const double *part_p, Scal sc, ShiftParams sp) {
+    __shared__ double sm[SCAL_THREADS];
+    const int j = blockIdx.x;
+    double tt = part_sum(part_t, j, BC, G, sm), pp = part_sum(part_p, j, BC, G, sm);
+    if (threadIdx.x) return;
     if (j == 0) {
         sc.flags[0] = 0;
         if (sc.hist) {
             int it = sc.iter_counter[0];
-            if (it < sc.hist_len) sc.hist[it] = 0; // filled below by rhs 0
+            if (it < sc.hist_len) sc.hist[it] = 0; // filled below when rhs 0 is active
         }
     }
-    if (j >= B) return;
     if (!sc.act_rhs[j]) {
         sc.alpha[j] = 0;
         sc.upd_rhs[j] = 0;
         for (int i = 0; i < sp.n; ++i) { sc.upd[i * B + j] = 0; sc.alpha_s[i * B + j] = 0; }
         return;
     }
-    double tt = sum_part(part_t, j, BC, G), pp = sum_part(part_p, j, BC, G);
     double pAp = tt + sp.s0 * pp;
     if (!(pAp > 0) || !isfinite(pAp)) {
         atomicOr(&sc.flags[2], 1);
@@ -413,21 +433,20 @@ __global__ void s1_kernel(int B, int BC, int G, const double *part_t, const doub
     }
 }
 
-__global__ void s2_kernel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2,
-                          double delta2) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(SCAL_THREADS)
+    s2_kernel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2, double delta2) {
+    __shared__ double sm[SCAL_THREADS];
+    const int j = blockIdx.x;
+    double rrn = part_sum(part_r, j, BC, G, sm);
+    if (threadIdx.x) return;
     if (j == 0) {
         if (sc.hist) {
             int it = sc.iter_counter[0];
-            if (it < sc.hist_len) {
-                double rrn = sum_part(part_r, 0, BC, G);
-                sc.hist[sc.hist_len + it] = sc.upd_rhs[0] ? rrn / sc.rr[0] : 0.0;
-            }
+            if (it < sc.hist_len) sc.hist[sc.hist_len + it] = sc.upd_rhs[0] ? rrn / sc.rr[0] : 0.0;
         }
         sc.iter_counter[0] += 1;
     }
-    if (j >= B || !sc.upd_rhs[j]) return;
-    double rrn = sum_part(part_r, j, BC, G);
+    if (!sc.upd_rhs[j]) return;
     double b = rrn / sc.rr[j];
     sc.beta[j] = b;
     int any = 0;
@@ -454,12 +473,14 @@ __global__ void s2_kernel(int B, int BC, int G, const double *part_r, Scal sc, S
 }
 
 // after a residual replacement: rr = |r_hi|^2, the base shift re-activates if
-// its true residual is above tolerance
-// (flags[0] and flags[1] are cleared by the host before the launch)
-__global__ void s_rel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2, int base) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= B || !(sc.bb[j] > 0)) return;
-    double rr = sum_part(part_r, j, BC, G);
+// its true residual is above tolerance (flags[0] and flags[1] are cleared by
+// the host before the launch)
+__global__ void __launch_bounds__(SCAL_THREADS)
+    s_rel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2, int base) {
+    __shared__ double sm[SCAL_THREADS];
+    const int j = blockIdx.x;
+    double rr = part_sum(part_r, j, BC, G, sm);
+    if (threadIdx.x || !(sc.bb[j] > 0)) return;
     sc.rr[j] = rr;
     sc.rr_ref[j] = rr;
     int any = 0;
@@ -482,9 +503,9 @@ template <typename T, int BC> struct Solver {
         const bool rel = (Prec<T>::id == SMPQ_FP32);
         cudaStream_t st = ctx->stream;
         const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-        const int G = std::max(1, std::min(ntiles, (TARGET_BLOCKS + nchunk - 1) / nchunk));
+        const int G = (ntiles + TPB - 1) / TPB;
         const int nsup_tiles = (spec.n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-        const int Gs = std::max(1, std::min(std::max(nsup_tiles, 1), (TARGET_BLOCKS + nchunk - 1) / nchunk));
+        const int Gs = std::max(1, (nsup_tiles + TPB - 1) / TPB);
         const size_t nfield = (size_t)B * 12 * V;
         const size_t nsupf = (size_t)B * 12 * spec.n_sup;
         std::vector<Buf> &ws = ctx->ws;
@@ -537,7 +558,7 @@ template <typename T, int BC> struct Solver {
 
         const dim3 grid(G, nchunk), gsup(Gs, nchunk);
         const int TH = TileMap<BC>::THREADS;
-        const int sblocks = (B + 127) / 128;
+        const int sblocks = B; // scalar kernels: one block per right-hand side
         const double tol2 = tol * tol;
         const double delta2 = rel ? ctx->opt.reliable_delta * ctx->opt.reliable_delta : 0.0;
         const Geom g = ctx->geom;
@@ -550,7 +571,7 @@ template <typename T, int BC> struct Solver {
         cudaMemsetAsync(sc.flags, 0, 5 * sizeof(int), st);
         cudaEventRecord(ctx->ev1, st);
         k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
-        s_init<<<sblocks, 128, 0, st>>>(B, BC, G, part0, sc, sp, tol);
+        s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, tol);
         if (spec.n_sup > 0)
             k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps, y,
                                                 sc, sp, Gs, 1);
@@ -569,14 +590,14 @@ template <typename T, int BC> struct Solver {
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
             k_apply_a<T, BC><<<grid, TH, 0, st>>>(g, U, p, t, kappa, part0, part1, G);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-            s1_kernel<<<sblocks, 128, 0, st>>>(B, BC, G, part0, part1, sc, sp);
+            s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, part1, sc, sp);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
             if (rel)
                 k_apply_b<T, BC, true><<<grid, TH, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2, G);
             else
                 k_apply_b<T, BC, false><<<grid, TH, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2, G);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-            s2_kernel<<<sblocks, 128, 0, st>>>(B, BC, G, part2, sc, sp, tol2, delta2);
+            s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, delta2);
             if (spec.n_sup > 0)
                 k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps,
                                                     y, sc, sp, Gs, 0);
@@ -605,7 +626,7 @@ template <typename T, int BC> struct Solver {
             k_rel_resid<T, BC><<<grid, TH, 0, st>>>(g, (const double2 *)ctx->U64.p, t64, xhi, src, r, sp.s0,
                                                      ctx->opt.kappa, part2, G);
             cudaMemsetAsync(sc.flags, 0, 2 * sizeof(int), st);
-            s_rel<<<sblocks, 128, 0, st>>>(B, BC, G, part2, sc, sp, tol2, base_shift);
+            s_rel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, base_shift);
         };
 
         cudaGraphExec_t gexec = nullptr;
