@@ -19,6 +19,8 @@ LIB = os.path.join(HERE, "libsmpq.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# extra nvcc flags for tuning sweeps, e.g. SMPQ_NVCC_EXTRA="-DSMPQ_FP32_MIN_BLOCKS=3"
+FLAGS += os.environ.get("SMPQ_NVCC_EXTRA", "").split()
 
 
 def _nvcc():
@@ -37,7 +39,7 @@ def _deps():
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("SMPQ_NVCC_EXTRA"):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _deps())

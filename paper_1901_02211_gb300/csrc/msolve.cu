@@ -33,6 +33,14 @@ namespace {
 // the +-t neighbours (V/n_t sites away) are still in L2 when they are read.
 constexpr int TPB = 4;
 
+// minimum resident blocks per SM requested from the register allocator for
+// the FP32 lattice kernels (240-thread blocks: 2 -> <= 136 registers, 3 -> <= 91)
+#ifndef SMPQ_FP32_MIN_BLOCKS
+#define SMPQ_FP32_MIN_BLOCKS 2
+#endif
+template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
+template <> struct MinBlocks<double> { static constexpr int value = 1; };
+
 template <typename T> struct Prec;
 template <> struct Prec<double> { static constexpr int id = SMPQ_FP64; };
 template <> struct Prec<float> { static constexpr int id = SMPQ_FP32; };
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 
 // t = D_W p ; partials |t|^2 -> part[0], |p|^2 -> part[1]
 template <typename T, int BC>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<T>::value)
     k_apply_a(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ p,
               typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G) {
     typedef typename cplx_t<T>::type C;
@@ -133,16 +141,19 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         if (s >= g.V) continue;
         C acc[12];
         wilson_hop<T, false, BC>(g, U, p + base, s, acc);
+        T st = 0, sp = 0; // per-site sums in the iteration precision, one FP64 add per site
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             size_t o = base + (size_t)(c * g.V + s) * BC;
             C v = p[o];
-            ap += norm2(v);
+            sp += v.x * v.x + v.y * v.y;
             v.x -= kappa * acc[c].x;
             v.y -= kappa * acc[c].y;
             t[o] = v;
-            at += norm2(v);
+            st += v.x * v.x + v.y * v.y;
         }
+        at += (double)st;
+        ap += (double)sp;
     }
     double s1 = block_sum<BC>(at, sm);
     double s2 = block_sum<BC>(ap, sm);
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 
 // r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2
 template <typename T, int BC, bool REL>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<T>::value)
     k_apply_b(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ t,
               const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ r,
               typename cplx_t<T>::type *__restrict__ xlo, const double *__restrict__ alpha, double s0, T kappa,
@@ -172,6 +183,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         if (s >= g.V) continue;
         C acc[12];
         wilson_hop<T, true, BC>(g, U, t + base, s, acc);
+        T sr = 0;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             size_t o = base + (size_t)(c * g.V + s) * BC;
@@ -182,7 +194,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             rv.x -= a * ap.x;
             rv.y -= a * ap.y;
             r[o] = rv;
-            ar += norm2(rv);
+            sr += rv.x * rv.x + rv.y * rv.y;
             if (REL) {
                 C xv = xlo[o];
                 xv.x += a * pv.x;
@@ -190,6 +202,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
                 xlo[o] = xv;
             }
         }
+        ar += (double)sr;
     }
     double s1 = block_sum<BC>(ar, sm);
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;

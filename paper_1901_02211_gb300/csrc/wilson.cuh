@@ -77,15 +77,25 @@ __device__ __forceinline__ void hop_one(const typename cplx_t<T>::type *__restri
     }
 }
 
+// SMPQ_HOP_FENCE: keep the compiler from hoisting the loads of later hops
+// above earlier ones (bounds the live registers to about one neighbour).
+#ifdef SMPQ_HOP_FENCE
+#define SMPQ_FENCE() asm volatile("" ::: "memory")
+#else
+#define SMPQ_FENCE()
+#endif
+
 template <typename T, int MU, bool DAG, int BC>
 __device__ __forceinline__ void hop_dir(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
                                         const typename cplx_t<T>::type *__restrict__ in, int s,
                                         typename cplx_t<T>::type acc[12]) {
     float f;
+    SMPQ_FENCE();
     int nf = neighbour(g, s, MU, +1, &f);
     // forward: (1 - g) U(x) psi(x+mu)   [DAG: (1 + g)]
     hop_one<T, MU, DAG ? +1 : -1, false, BC>(U, in, g.V, g.V, nf, s, (T)f, acc);
     int nbk = neighbour(g, s, MU, -1, &f);
+    SMPQ_FENCE();
     // backward: (1 + g) U(x-mu)^dag psi(x-mu)   [DAG: (1 - g)]
     hop_one<T, MU, DAG ? -1 : +1, true, BC>(U, in, g.V, g.V, nbk, nbk, (T)f, acc);
 }
