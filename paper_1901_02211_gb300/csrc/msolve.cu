@@ -36,7 +36,7 @@ constexpr int TPB = 4;
 // minimum resident blocks per SM requested from the register allocator for
 // the FP32 lattice kernels (240-thread blocks: 2 -> <= 136 registers, 3 -> <= 91)
 #ifndef SMPQ_FP32_MIN_BLOCKS
-#define SMPQ_FP32_MIN_BLOCKS 2
+#define SMPQ_FP32_MIN_BLOCKS 3
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
