@@ -145,6 +145,27 @@ int smpq_colour_sites(const int dims[4], int r, int mode, int *colour, int *n_cl
  * in/out: double[V][4][3][B][2], host or device (on_device). */
 int smpq_dslash(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision, int on_device);
 
+/* Allocation-free variant of smpq_dslash (the paper has no counterpart; this
+ * is a service for callers of this library).  Some callers cannot call
+ * cudaMalloc: code whose device memory is owned by another allocator that must
+ * see every allocation (a framework's caching allocator), or latency-critical
+ * loops where cudaMalloc/cudaFree would synchronise the device.  This call
+ * allocates nothing: in and out are caller-owned DEVICE buffers in the layout
+ * of smpq_dslash, and the kernel's scratch (tiled copies of in and out) lives
+ * in a file-scope device array of 32 MiB that every GPU which loads the
+ * library holds until the process exits.
+ *   - Limit: 2 * V * 12 * B * e bytes <= 32 MiB, e = 16 (FP64) or 8 (FP32);
+ *     larger requests return SMPQ_EINVAL with the sizes in smpq_last_error.
+ *   - The first call on a device looks up the device address of the scratch
+ *     array (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture on the device.
+ *   - Every call on a device shares the same scratch.  Each call overwrites all
+ *     of the scratch it uses (nothing has to start at zero) and synchronises
+ *     the context's stream before returning, but calls from different
+ *     contexts or host threads that overlap on the GPU race on the scratch.
+ * Requires a loaded gauge field (SMPQ_ESTATE otherwise). */
+int smpq_dslash_noalloc(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision);
+
 /* out = D_ov in = in + D_W R(H^2) in (Eqs. 3-4 with gamma_5^2 = 1), B fields,
  * FP64 multi-shift CG over the full lattice.  Layout as smpq_dslash. */
 int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_device);

@@ -1,5 +1,7 @@
 // Link packing, SU(3) check, layout conversion and the stand-alone Wilson
 // dslash D_W / D_W^dag (Sec. 2.1, around Eq. 3) used by smpq_dslash.
+#include <string>
+
 #include "wilson.cuh"
 
 // ------------------------------------------------------------------ links
@@ -159,3 +161,78 @@ template void launch_dslash<double>(const Geom &, const void *, const void *, vo
                                     cudaStream_t);
 template void launch_dslash<float>(const Geom &, const void *, const void *, void *, int, int, int, double,
                                    cudaStream_t);
+
+// ------------------------------------------------------------------ allocation-free dslash
+// smpq_dslash_noalloc keeps its scratch (the tiled copies of the input and the
+// output field that the kernel reads and writes) in this file-scope device
+// array instead of asking for device memory.  The array is created when the
+// library's device code is loaded on a GPU and stays reserved on every GPU that
+// loads the library until the process exits.
+#define SMPQ_NOALLOC_SCRATCH_BYTES (32u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SMPQ_NOALLOC_SCRATCH_BYTES];
+
+#include <mutex>
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side handle, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(smpq_ctx *ctx, int dev, void **out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return set_err(ctx, SMPQ_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_check(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "scratch address");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SMPQ_OK;
+}
+} // namespace
+
+extern "C" int smpq_dslash_noalloc(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision) {
+    if (!ctx) return SMPQ_EINVAL;
+    if (!ctx->have_gauge) return set_err(ctx, SMPQ_ESTATE, "no gauge field loaded");
+    if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad dslash_noalloc arguments");
+    if (precision != SMPQ_FP64 && precision != SMPQ_FP32) return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    const size_t n = (size_t)ctx->V * 12 * B;
+    const size_t esz = precision == SMPQ_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t half = ((n * esz + 255) / 256) * 256; // input tile, then output tile
+    if (2 * half > SMPQ_NOALLOC_SCRATCH_BYTES)
+        return set_err(ctx, SMPQ_EINVAL,
+                       "field too large for smpq_dslash_noalloc: needs " + std::to_string(2 * half) +
+                           " bytes of scratch, the limit is " + std::to_string(SMPQ_NOALLOC_SCRATCH_BYTES) +
+                           " (2 * V * 12 * B * " + std::to_string(esz) + " bytes)");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(ctx, ctx->device, &scratch);
+    if (rc == SMPQ_OK) {
+        cudaStream_t st = ctx->stream;
+        if (ctx->user_stream) {
+            cudaEventRecord(ctx->ev0, (cudaStream_t)ctx->user_stream);
+            cudaStreamWaitEvent(st, ctx->ev0, 0);
+        }
+        char *tin = (char *)scratch, *tout = (char *)scratch + half;
+        const int BC = 1;
+        if (precision == SMPQ_FP64) {
+            launch_to_tiled<double>(in, tin, ctx->V, B, BC, st);
+            launch_dslash<double>(ctx->geom, ctx->U64.p, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+            launch_from_tiled<double>(tout, out, ctx->V, B, BC, st);
+        } else {
+            launch_to_tiled<float>(in, tin, ctx->V, B, BC, st);
+            launch_dslash<float>(ctx->geom, ctx->U32.p, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+            launch_from_tiled<float>(tout, out, ctx->V, B, BC, st);
+        }
+        cudaError_t e = cudaStreamSynchronize(st);
+        rc = e != cudaSuccess ? cuda_check(ctx, e, "dslash_noalloc") : cuda_check(ctx, cudaGetLastError(), "dslash_noalloc launch");
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}

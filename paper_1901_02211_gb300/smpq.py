@@ -80,7 +80,7 @@ EXPORTS = [
     "smpq_options_default", "smpq_create", "smpq_destroy", "smpq_last_error", "smpq_set_options",
     "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
-    "smpq_compute_qx_classes",
+    "smpq_compute_qx_classes", "smpq_dslash_noalloc",
 ]
 
 _lib = None
@@ -115,6 +115,7 @@ def load(build_if_missing=True):
         "smpq_build_sources": [P, I, I, PI],
         "smpq_colour_sites": [PI, I, I, P, PI],
         "smpq_dslash": [P, P, P, I, I, I, I],
+        "smpq_dslash_noalloc": [P, P, P, I, I, I],
         "smpq_apply_dov": [P, P, P, I, I],
         "smpq_compute_qx": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
         "smpq_compute_qx_classes": [P, PI, I, P, P, I, ctypes.POINTER(smpq_stats)],
@@ -229,6 +230,16 @@ def smpq_dslash(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
     if di != do:
         raise ValueError("in and out must both be host or both be device buffers")
     _check(load().smpq_dslash(ctx, pi, po, B, int(dagger), precision, di), ctx)
+
+
+def smpq_dslash_noalloc(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
+    """Allocation-free D_W for callers that cannot allocate device memory:
+    `inp` and `out` must be device buffers (torch CUDA tensors)."""
+    pi, di = _ptr(inp)
+    po, do = _ptr(out)
+    if not (di and do):
+        raise ValueError("smpq_dslash_noalloc takes device buffers only")
+    _check(load().smpq_dslash_noalloc(ctx, pi, po, B, int(dagger), precision), ctx)
 
 
 def smpq_apply_dov(ctx, inp, out, B):
