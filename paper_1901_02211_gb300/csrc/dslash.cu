@@ -5,15 +5,16 @@
 #include "wilson.cuh"
 
 // ------------------------------------------------------------------ links
-// U_aos: double[V][4][3][3][2] -> U64/U32: [(mu*9 + e) * V + s] complex
+// U_aos: double[V][4][3][3][2] -> U64/U32: [(mu * V + s) * 9 + e] complex
 __global__ void pack_links_kernel(const double2 *__restrict__ Uaos, double2 *__restrict__ U64,
                                   float2 *__restrict__ U32, int V) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= (long)V * 36) return;
     int s = (int)(i / 36), k = (int)(i % 36); // k = mu*9 + e
     double2 u = Uaos[i];
-    U64[(size_t)k * V + s] = u;
-    U32[(size_t)k * V + s] = make_float2((float)u.x, (float)u.y);
+    size_t o = ((size_t)(k / 9) * V + s) * 9 + (k % 9);
+    U64[o] = u;
+    U32[o] = make_float2((float)u.x, (float)u.y);
 }
 
 void launch_pack_links(const double *U_aos, double *U64, float *U32, int V, cudaStream_t st) {
@@ -30,7 +31,7 @@ __global__ void su3_check_kernel(const double2 *__restrict__ U, int V, unsigned 
     if (i < (long)V * 4) {
         int s = (int)(i / 4), mu = (int)(i % 4);
         double2 u[9];
-        for (int e = 0; e < 9; ++e) u[e] = U[(size_t)(mu * 9 + e) * V + s];
+        for (int e = 0; e < 9; ++e) u[e] = U[((size_t)mu * V + s) * 9 + e];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
                 double2 t = make_double2(0, 0);
@@ -65,7 +66,7 @@ void launch_su3_check(const double *U64, int V, double *dev_maxerr, cudaStream_t
 }
 
 // ------------------------------------------------------------------ layout conversion
-// ABI [V][12][B] double2  <->  tiled [(j/BC)*12 + c][V][BC] of complex T
+// ABI [V][12][B] double2  <->  tiled [j/BC][V][12][BC] of complex T
 template <typename T>
 __global__ void to_tiled_kernel(const double2 *__restrict__ in, typename cplx_t<T>::type *__restrict__ out, int V,
                                 int B, int BC) {
@@ -76,7 +77,7 @@ __global__ void to_tiled_kernel(const double2 *__restrict__ in, typename cplx_t<
     int c = (int)(r % 12);
     int s = (int)(r / 12);
     double2 v = in[i];
-    size_t o = ((size_t)((j / BC) * 12 + c) * V + s) * BC + (j % BC);
+    size_t o = (((size_t)(j / BC) * V + s) * 12 + c) * BC + (j % BC);
     out[o] = mkc<typename cplx_t<T>::type>(v.x, v.y);
 }
 
@@ -89,7 +90,7 @@ __global__ void from_tiled_kernel(const typename cplx_t<T>::type *__restrict__ i
     long r = i / B;
     int c = (int)(r % 12);
     int s = (int)(r / 12);
-    size_t o = ((size_t)((j / BC) * 12 + c) * V + s) * BC + (j % BC);
+    size_t o = (((size_t)(j / BC) * V + s) * 12 + c) * BC + (j % BC);
     typename cplx_t<T>::type v = in[o];
     out[i] = make_double2((double)v.x, (double)v.y);
 }
@@ -120,14 +121,14 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     if (s >= g.V) return;
     size_t base = (size_t)blockIdx.y * 12 * g.V * BC + jj;
     const C *pin = in + base;
-    C acc[12];
+    C acc[12][1];
     wilson_hop<T, DAG, BC>(g, U, pin, s, acc);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
-        size_t o = (size_t)(c * g.V + s) * BC;
+        size_t o = ((size_t)s * 12 + c) * BC;
         C v = pin[o];
-        v.x -= kappa * acc[c].x;
-        v.y -= kappa * acc[c].y;
+        v.x -= kappa * acc[c][0].x;
+        v.y -= kappa * acc[c][0].y;
         out[base + o] = v;
     }
 }

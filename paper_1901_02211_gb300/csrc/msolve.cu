@@ -36,7 +36,7 @@ constexpr int TPB = 4;
 // minimum resident blocks per SM requested from the register allocator for
 // the FP32 lattice kernels (240-thread blocks: 2 -> <= 136 registers, 3 -> <= 91)
 #ifndef SMPQ_FP32_MIN_BLOCKS
-#define SMPQ_FP32_MIN_BLOCKS 3
+#define SMPQ_FP32_MIN_BLOCKS 2
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         if (s >= g.V) continue;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            size_t o = base + (size_t)(c * g.V + s) * BC;
+            size_t o = base + ((size_t)s * 12 + c) * BC;
             double2 b = source_at<BC>(src, g.V, s, c, j, o);
             C v = mkc<C>(b.x, b.y);
             r[o] = v;
@@ -125,86 +125,144 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     if (threadIdx.x < BC) part[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s;
 }
 
-// t = D_W p ; partials |t|^2 -> part[0], |p|^2 -> part[1]
-template <typename T, int BC>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<T>::value)
+// per-column sums over a block of the NR-column kernels (sites x columns in
+// shared memory, then a fixed-order sum down each column); threads < BC return
+// the total of column threadIdx.x
+template <int BC, int NR>
+__device__ __forceinline__ double block_sum_cols(const double v[NR], double *sm) {
+    constexpr int TPS = TileMap<BC, NR>::TPS, SPB = TileMap<BC, NR>::SPB;
+    const int row = threadIdx.x / TPS, col0 = (threadIdx.x % TPS) * NR;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sm[row * BC + col0 + r] = v[r];
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x < BC)
+        for (int k = 0; k < SPB; ++k) s += sm[k * BC + threadIdx.x];
+    __syncthreads();
+    return s;
+}
+
+template <int BC, int NR>
+__device__ __forceinline__ double block_total(const double v[NR], double *sm) {
+    if constexpr (NR == 1) return block_sum<BC>(v[0], sm);
+    else return block_sum_cols<BC, NR>(v, sm);
+}
+
+template <int BC, int NR> struct SmemCols {
+    static constexpr int N = TileMap<BC, NR>::THREADS > TileMap<BC, NR>::SPB * BC ? TileMap<BC, NR>::THREADS
+                                                                                   : TileMap<BC, NR>::SPB * BC;
+};
+
+// t = D_W p ; partials |t|^2 -> part_t, |p|^2 -> part_p (NR columns per thread)
+template <typename T, int BC, int NR>
+__global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_a(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ p,
               typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G) {
     typedef typename cplx_t<T>::type C;
-    __shared__ double sm[TileMap<BC>::THREADS];
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y;
+    typedef TileMap<BC, NR> TM;
+    __shared__ double sm[SmemCols<BC, NR>::N];
+    const int jj = (threadIdx.x % TM::TPS) * NR, chunk = blockIdx.y;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
-    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    double at = 0, ap = 0;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    double at[NR], ap[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) at[r] = ap[r] = 0;
     for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
-        int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
-        C acc[12];
-        wilson_hop<T, false, BC>(g, U, p + base, s, acc);
-        T st = 0, sp = 0; // per-site sums in the iteration precision, one FP64 add per site
+        C acc[12][NR];
+        wilson_hop<T, false, BC, NR>(g, U, p + base, s, acc);
+        T st[NR], sp[NR]; // per-site sums in the iteration precision, one FP64 add per site
+#pragma unroll
+        for (int r = 0; r < NR; ++r) st[r] = sp[r] = 0;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            size_t o = base + (size_t)(c * g.V + s) * BC;
-            C v = p[o];
-            sp += v.x * v.x + v.y * v.y;
-            v.x -= kappa * acc[c].x;
-            v.y -= kappa * acc[c].y;
-            t[o] = v;
-            st += v.x * v.x + v.y * v.y;
+            size_t o = base + ((size_t)s * 12 + c) * BC;
+            C v[NR];
+            Cols<C, NR>::load(p + o, v);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                sp[r] += v[r].x * v[r].x + v[r].y * v[r].y;
+                v[r].x -= kappa * acc[c][r].x;
+                v[r].y -= kappa * acc[c][r].y;
+                st[r] += v[r].x * v[r].x + v[r].y * v[r].y;
+            }
+            Cols<C, NR>::store(t + o, v);
         }
-        at += (double)st;
-        ap += (double)sp;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            at[r] += (double)st[r];
+            ap[r] += (double)sp[r];
+        }
     }
-    double s1 = block_sum<BC>(at, sm);
-    double s2 = block_sum<BC>(ap, sm);
+    double s1 = block_total<BC, NR>(at, sm);
+    double s2 = block_total<BC, NR>(ap, sm);
     if (threadIdx.x < BC) {
         part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
         part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
     }
 }
 
-// r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2
-template <typename T, int BC, bool REL>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<T>::value)
+// r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2 (NR columns per thread)
+template <typename T, int BC, int NR, bool REL>
+__global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_b(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ t,
               const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ r,
               typename cplx_t<T>::type *__restrict__ xlo, const double *__restrict__ alpha, double s0, T kappa,
               double *part_r, int G) {
     typedef typename cplx_t<T>::type C;
-    __shared__ double sm[TileMap<BC>::THREADS];
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    typedef TileMap<BC, NR> TM;
+    __shared__ double sm[SmemCols<BC, NR>::N];
+    const int jj = (threadIdx.x % TM::TPS) * NR, chunk = blockIdx.y, j = chunk * BC + jj;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
-    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    const T a = (T)alpha[j];
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    T a[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) a[q] = (T)alpha[j + q];
     const T sh = (T)s0;
-    double ar = 0;
+    double ar[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) ar[q] = 0;
     for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
-        int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
-        C acc[12];
-        wilson_hop<T, true, BC>(g, U, t + base, s, acc);
-        T sr = 0;
+        C acc[12][NR];
+        wilson_hop<T, true, BC, NR>(g, U, t + base, s, acc);
+        T sr[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) sr[q] = 0;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            size_t o = base + (size_t)(c * g.V + s) * BC;
-            C tv = t[o], pv = p[o], rv = r[o];
-            C ap;
-            ap.x = tv.x - kappa * acc[c].x + sh * pv.x;
-            ap.y = tv.y - kappa * acc[c].y + sh * pv.y;
-            rv.x -= a * ap.x;
-            rv.y -= a * ap.y;
-            r[o] = rv;
-            sr += rv.x * rv.x + rv.y * rv.y;
+            size_t o = base + ((size_t)s * 12 + c) * BC;
+            C tv[NR], pv[NR], rv[NR];
+            Cols<C, NR>::load(t + o, tv);
+            Cols<C, NR>::load(p + o, pv);
+            Cols<C, NR>::load(r + o, rv);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                C ap;
+                ap.x = tv[q].x - kappa * acc[c][q].x + sh * pv[q].x;
+                ap.y = tv[q].y - kappa * acc[c][q].y + sh * pv[q].y;
+                rv[q].x -= a[q] * ap.x;
+                rv[q].y -= a[q] * ap.y;
+                sr[q] += rv[q].x * rv[q].x + rv[q].y * rv[q].y;
+            }
+            Cols<C, NR>::store(r + o, rv);
             if (REL) {
-                C xv = xlo[o];
-                xv.x += a * pv.x;
-                xv.y += a * pv.y;
-                xlo[o] = xv;
+                C xv[NR];
+                Cols<C, NR>::load(xlo + o, xv);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    xv[q].x += a[q] * pv[q].x;
+                    xv[q].y += a[q] * pv[q].y;
+                }
+                Cols<C, NR>::store(xlo + o, xv);
             }
         }
-        ar += (double)sr;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) ar[q] += (double)sr[q];
     }
-    double s1 = block_sum<BC>(ar, sm);
+    double s1 = block_total<BC, NR>(ar, sm);
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
 }
 
@@ -224,7 +282,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         if (s >= V) continue;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            size_t o = base + (size_t)(c * V + s) * BC;
+            size_t o = base + ((size_t)s * 12 + c) * BC;
             C rv = r[o], pv = p[o];
             pv.x = rv.x + b * pv.x;
             pv.y = rv.y + b * pv.y;
@@ -256,18 +314,18 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         int site = supsite ? supsite[(size_t)cls * n_sup + k] : k;
         C rv[12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) rv[c] = r[rbase + (size_t)(c * V + site) * BC];
+        for (int c = 0; c < 12; ++c) rv[c] = r[rbase + ((size_t)site * 12 + c) * BC];
         if (init) { // p_i = b (= r at the start), y = 0
             for (int i = 0; i < nshift; ++i)
 #pragma unroll
-                for (int c = 0; c < 12; ++c) ps[i * sstride + sbase + (size_t)(c * n_sup + k) * BC] = rv[c];
+                for (int c = 0; c < 12; ++c) ps[i * sstride + sbase + ((size_t)k * 12 + c) * BC] = rv[c];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) y[sbase + (size_t)(c * n_sup + k) * BC] = make_double2(0, 0);
+            for (int c = 0; c < 12; ++c) y[sbase + ((size_t)k * 12 + c) * BC] = make_double2(0, 0);
             continue;
         }
         double2 yv[12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) yv[c] = y[sbase + (size_t)(c * n_sup + k) * BC];
+        for (int c = 0; c < 12; ++c) yv[c] = y[sbase + ((size_t)k * 12 + c) * BC];
         for (int i = 0; i < nshift; ++i) {
             if (!sc.upd[i * B + j]) continue;
             double ca = sp.c[i] * sc.alpha_s[i * B + j];
@@ -276,7 +334,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             C *pi = ps + i * sstride + sbase;
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                size_t o = (size_t)(c * n_sup + k) * BC;
+                size_t o = ((size_t)k * 12 + c) * BC;
                 C pv = pi[o];
                 yv[c].x += ca * (double)pv.x;
                 yv[c].y += ca * (double)pv.y;
@@ -286,7 +344,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             }
         }
 #pragma unroll
-        for (int c = 0; c < 12; ++c) y[sbase + (size_t)(c * n_sup + k) * BC] = yv[c];
+        for (int c = 0; c < 12; ++c) y[sbase + ((size_t)k * 12 + c) * BC] = yv[c];
     }
 }
 
@@ -303,7 +361,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         if (s >= V) continue;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            size_t o = base + (size_t)(c * V + s) * BC;
+            size_t o = base + ((size_t)s * 12 + c) * BC;
             C xl = xlo[o];
             double2 xh = xhi[o];
             xh.x += (double)xl.x;
@@ -329,16 +387,16 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
-        double2 acc[12];
+        double2 acc[12][1];
         wilson_hop<double, true, BC>(g, U64, t64 + base, s, acc);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            size_t o = base + (size_t)(c * g.V + s) * BC;
+            size_t o = base + ((size_t)s * 12 + c) * BC;
             double2 tv = t64[o], xv = xhi[o];
             double2 b = source_at<BC>(src, g.V, s, c, j, o);
             double2 rv;
-            rv.x = b.x - (tv.x - kappa * acc[c].x + s0 * xv.x);
-            rv.y = b.y - (tv.y - kappa * acc[c].y + s0 * xv.y);
+            rv.x = b.x - (tv.x - kappa * acc[c][0].x + s0 * xv.x);
+            rv.y = b.y - (tv.y - kappa * acc[c][0].y + s0 * xv.y);
             r[o] = mkc<C>(rv.x, rv.y);
             ar += rv.x * rv.x + rv.y * rv.y;
         }
@@ -508,8 +566,18 @@ __global__ void __launch_bounds__(SCAL_THREADS)
 
 // ------------------------------------------------------------------ driver
 
+// columns per thread of the D_W kernels: two FP32 columns share one 16-byte
+// access and one link fetch
+#ifndef SMPQ_FP32_NR
+#define SMPQ_FP32_NR 2
+#endif
+template <typename T, int BC> struct NRSel {
+    static constexpr int value = (sizeof(T) == 4 && BC % SMPQ_FP32_NR == 0) ? SMPQ_FP32_NR : 1;
+};
+
 template <typename T, int BC> struct Solver {
     typedef typename cplx_t<T>::type C;
+    static constexpr int NR = NRSel<T, BC>::value;
     static int run(smpq_ctx *ctx, const SolveSpec &spec, const ShiftParams &sp, double tol, int max_iter,
                    SolveOut *out, double *hist, int hist_len, int fixed_iters) {
         const int B = spec.B, V = ctx->V, nchunk = B / BC;
@@ -517,6 +585,8 @@ template <typename T, int BC> struct Solver {
         cudaStream_t st = ctx->stream;
         const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
         const int G = (ntiles + TPB - 1) / TPB;
+        const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
+        const int GN = (ntiles_n + TPB - 1) / TPB; // blocks per RHS tile of the NR-column kernels
         const int nsup_tiles = (spec.n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
         const int Gs = std::max(1, (nsup_tiles + TPB - 1) / TPB);
         const size_t nfield = (size_t)B * 12 * V;
@@ -536,7 +606,7 @@ template <typename T, int BC> struct Solver {
             if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * nsupf * sizeof(C)))) return rc;
             if ((rc = ensure(ctx, ws[W_Y], nsupf * sizeof(double2)))) return rc;
         }
-        const size_t npart = (size_t)nchunk * std::max(G, Gs) * BC;
+        const size_t npart = (size_t)nchunk * std::max(std::max(G, Gs), GN) * BC;
         if ((rc = ensure(ctx, ws[W_PART], 3 * npart * sizeof(double)))) return rc;
         const size_t nscal = (size_t)B * 7 + (size_t)sp.n * B * 5;
         const size_t nint = (size_t)B * 3 + (size_t)sp.n * B * 2 + 8;
@@ -569,7 +639,8 @@ template <typename T, int BC> struct Solver {
         src.src_comp = spec.d_src_comp;
         src.b64 = (const double2 *)spec.d_src_field;
 
-        const dim3 grid(G, nchunk), gsup(Gs, nchunk);
+        const dim3 grid(G, nchunk), gsup(Gs, nchunk), gridn(GN, nchunk);
+        const int THN = TileMap<BC, NR>::THREADS;
         const int TH = TileMap<BC>::THREADS;
         const int sblocks = B; // scalar kernels: one block per right-hand side
         const double tol2 = tol * tol;
@@ -601,16 +672,18 @@ template <typename T, int BC> struct Solver {
         const int per_iter = 5 + (spec.n_sup > 0 ? 1 : 0);
         auto iteration = [&](int k) {
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-            k_apply_a<T, BC><<<grid, TH, 0, st>>>(g, U, p, t, kappa, part0, part1, G);
+            k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(g, U, p, t, kappa, part0, part1, GN);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-            s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, part1, sc, sp);
+            s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GN, part0, part1, sc, sp);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
             if (rel)
-                k_apply_b<T, BC, true><<<grid, TH, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2, G);
+                k_apply_b<T, BC, NR, true><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
+                                                                   GN);
             else
-                k_apply_b<T, BC, false><<<grid, TH, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2, G);
+                k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
+                                                                    GN);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-            s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, delta2);
+            s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GN, part2, sc, sp, tol2, delta2);
             if (spec.n_sup > 0)
                 k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps,
                                                     y, sc, sp, Gs, 0);

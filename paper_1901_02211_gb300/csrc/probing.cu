@@ -101,7 +101,7 @@ __global__ void add_c0b_kernel(int n_sup, int B, int BC, const int *__restrict__
     int site = supsite[(size_t)cl * n_sup + k];
     if (colour[site] != cl) return;
     int c = src_comp[j];
-    size_t o = ((size_t)((j / BC) * 12 + c) * n_sup + k) * BC + (j % BC);
+    size_t o = (((size_t)(j / BC) * n_sup + k) * 12 + c) * BC + (j % BC);
     y[o].x += c0;
 }
 
@@ -125,9 +125,9 @@ __global__ void contract_kernel(Geom g, const double2 *__restrict__ U, const dou
     if (cl < 0) return;
     int x = members[(size_t)cl * nmem + m];
     const double2 *yb = y + (size_t)(j / BC) * 12 * n_sup * BC + (j % BC);
-    double2 acc[12];
+    double2 acc[12][1];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = make_double2(0, 0);
+    for (int c = 0; c < 12; ++c) acc[c][0] = make_double2(0, 0);
     const int k0 = 9 * m;
     float f;
 #define SMPQ_HOP(MU)                                                                                                   \
@@ -143,8 +143,8 @@ __global__ void contract_kernel(Geom g, const double2 *__restrict__ U, const dou
     SMPQ_HOP(3)
 #undef SMPQ_HOP
     int c = src_comp[j];
-    double2 yc = yb[(size_t)(c * n_sup + k0) * BC];
-    double2 z = make_double2(yc.x - kappa * acc[c].x, yc.y - kappa * acc[c].y);
+    double2 yc = yb[((size_t)k0 * 12 + c) * BC];
+    double2 z = make_double2(yc.x - kappa * acc[c][0].x, yc.y - kappa * acc[c][0].y);
     double g5 = (c / 3) < 2 ? 1.0 : -1.0;
     qterm[((size_t)cl * 12 + c) * nmem + m] = make_double2(g5 * z.x, g5 * z.y);
 }

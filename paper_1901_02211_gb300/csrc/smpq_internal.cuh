@@ -94,8 +94,11 @@ __device__ __forceinline__ int neighbour(const Geom &g, int s, int mu, int dir, 
 // ---------------------------------------------------------------- field layout
 // A batch of B right-hand sides is stored in RHS tiles of BC columns:
 //   element (component c in 0..11 = spin*3 + colour, site s, rhs j)
-//   at ((j / BC) * 12 + c) * V + s) * BC + (j % BC).
-// Links: U[(mu * 9 + row * 3 + col) * V + s] (structure of arrays).
+//   at (((j / BC) * V + s) * 12 + c) * BC + (j % BC),
+// i.e. one tile is [site][component][column]: a warp reads consecutive columns
+// of one site component, and the 12 components of a site sit at fixed
+// offsets (immediates in the load instructions).
+// Links: U[(mu * V + s) * 9 + row * 3 + col] (the 9 elements of one link contiguous).
 
 // ---------------------------------------------------------------- solver state
 struct ShiftParams {

@@ -1,5 +1,5 @@
-// Wilson hopping term of D_W (Sec. 2.1, around Eq. 3) for one site and one
-// right-hand side, with half-spinor projection.
+// Wilson hopping term of D_W (Sec. 2.1, around Eq. 3) for one site and NR
+// right-hand sides, with half-spinor projection.
 //
 //   hop(x) = sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
 //   D_W psi(x) = psi(x) - kappa hop(x)
@@ -10,6 +10,10 @@
 // and S_t = 1.  (1 + s g_mu) psi has upper half h = psi_up + s S_mu psi_lo and
 // lower half s S_mu^dag h, so only h (2 spins x 3 colours) is multiplied by the
 // link: 2 colour mat-vecs per hop instead of 4.
+//
+// A thread handles NR adjacent right-hand-side columns of one site: the link
+// and the neighbour index are fetched once for all NR columns, and two FP32
+// columns move as one 16-byte access.
 #pragma once
 #include "smpq_internal.cuh"
 
@@ -28,96 +32,153 @@ template <int MU, typename C> __device__ __forceinline__ void sdag_apply(C u0, C
     else { o0 = u0; o1 = u1; }
 }
 
-// One hop: acc += (1 + SG g_mu) W psi(nb) * f, with W = U (BACK = false) or
-// U^dag (BACK = true) read from link site ls.
-// `in` has component stride Vf * BC (field sites), links have site stride Vl.
-template <typename T, int MU, int SG, bool BACK, int BC>
+// NR adjacent complex values, with one access where the width allows it
+template <typename C, int NR> struct Cols {
+    static __device__ __forceinline__ void load(const C *p, C v[NR]) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = p[r];
+    }
+    static __device__ __forceinline__ void store(C *p, const C v[NR]) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) p[r] = v[r];
+    }
+};
+template <> struct Cols<float2, 2> {
+    static __device__ __forceinline__ void load(const float2 *p, float2 v[2]) {
+        float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = make_float2(q.x, q.y);
+        v[1] = make_float2(q.z, q.w);
+    }
+    static __device__ __forceinline__ void store(float2 *p, const float2 v[2]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+};
+
+// One hop: acc += (1 + SG g_mu) W psi(nb) * f for NR columns, with W = U
+// (BACK = false) or U^dag (BACK = true) read from link site ls.
+// `in` points at the tile (plus first column): site nb starts at nb * 12 * BC;
+// links U[(MU * Vl + ls) * 9 + e].  (Vf, the field site count, is not needed.)
+template <typename T, int MU, int SG, bool BACK, int BC, int NR = 1>
 __device__ __forceinline__ void hop_one(const typename cplx_t<T>::type *__restrict__ U,
                                         const typename cplx_t<T>::type *__restrict__ in, int Vf, int Vl, int nb,
-                                        int ls, T f, typename cplx_t<T>::type acc[12]) {
+                                        int ls, T f, typename cplx_t<T>::type acc[12][NR]) {
     typedef typename cplx_t<T>::type C;
-    C p[12];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) p[c] = in[(size_t)(c * Vf + nb) * BC];
-    // project
-    C h[2][3];
+    const C *q = in + (size_t)nb * (12 * BC); // the 12 components of a site are BC apart
+    // project colour by colour: only the 4 spin components of one colour are live
+    C h[2][3][NR];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        C s0, s1;
-        s_apply<MU>(p[6 + a], p[9 + a], s0, s1);
-        if (SG > 0) { h[0][a] = cadd(p[a], s0); h[1][a] = cadd(p[3 + a], s1); }
-        else { h[0][a] = csub(p[a], s0); h[1][a] = csub(p[3 + a], s1); }
+        C p0[NR], p1[NR], p2[NR], p3[NR];
+        Cols<C, NR>::load(q + a * BC, p0);
+        Cols<C, NR>::load(q + (3 + a) * BC, p1);
+        Cols<C, NR>::load(q + (6 + a) * BC, p2);
+        Cols<C, NR>::load(q + (9 + a) * BC, p3);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            C s0, s1;
+            s_apply<MU>(p2[r], p3[r], s0, s1);
+            if (SG > 0) { h[0][a][r] = cadd(p0[r], s0); h[1][a][r] = cadd(p1[r], s1); }
+            else { h[0][a][r] = csub(p0[r], s0); h[1][a][r] = csub(p1[r], s1); }
+        }
     }
-    // colour multiply
     C u[9];
+    const C *ul = U + ((size_t)MU * Vl + ls) * 9; // the 9 elements of a link are contiguous
 #pragma unroll
-    for (int e = 0; e < 9; ++e) u[e] = U[(size_t)(MU * 9 + e) * Vl + ls];
-    C w[2][3];
+    for (int e = 0; e < 9; ++e) u[e] = ul[e];
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
+    for (int r = 0; r < NR; ++r) {
+        // colour multiply
+        C w[2][3];
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                C t = mkc<C>(0, 0);
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (BACK) t = cfmac(u[b * 3 + a], h[sp][b][r], t);
+                    else t = cfma(u[a * 3 + b], h[sp][b][r], t);
+                }
+                w[sp][a] = cscale(f, t);
+            }
+        // reconstruct
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            C t = mkc<C>(0, 0);
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (BACK) t = cfmac(u[b * 3 + a], h[sp][b], t);
-                else t = cfma(u[a * 3 + b], h[sp][b], t);
-            }
-            w[sp][a] = cscale(f, t);
+            acc[a][r] = cadd(acc[a][r], w[0][a]);
+            acc[3 + a][r] = cadd(acc[3 + a][r], w[1][a]);
+            C l0, l1;
+            sdag_apply<MU>(w[0][a], w[1][a], l0, l1);
+            if (SG > 0) { acc[6 + a][r] = cadd(acc[6 + a][r], l0); acc[9 + a][r] = cadd(acc[9 + a][r], l1); }
+            else { acc[6 + a][r] = csub(acc[6 + a][r], l0); acc[9 + a][r] = csub(acc[9 + a][r], l1); }
         }
-    // reconstruct
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        acc[a] = cadd(acc[a], w[0][a]);
-        acc[3 + a] = cadd(acc[3 + a], w[1][a]);
-        C l0, l1;
-        sdag_apply<MU>(w[0][a], w[1][a], l0, l1);
-        if (SG > 0) { acc[6 + a] = cadd(acc[6 + a], l0); acc[9 + a] = cadd(acc[9 + a], l1); }
-        else { acc[6 + a] = csub(acc[6 + a], l0); acc[9 + a] = csub(acc[9 + a], l1); }
     }
 }
 
-// SMPQ_HOP_FENCE: keep the compiler from hoisting the loads of later hops
-// above earlier ones (bounds the live registers to about one neighbour).
+// SMPQ_HOP_FENCE: a compiler-only memory fence between hops, so the loads of
+// later hops are not hoisted above earlier ones (bounds the live registers).
+// It emits no instruction and never waits.
 #ifdef SMPQ_HOP_FENCE
-#define SMPQ_FENCE() asm volatile("" ::: "memory")
+#define SMPQ_HOP_BARRIER() asm volatile("" ::: "memory")
 #else
-#define SMPQ_FENCE()
+#define SMPQ_HOP_BARRIER()
 #endif
 
-template <typename T, int MU, bool DAG, int BC>
-__device__ __forceinline__ void hop_dir(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
+// Lattice coordinates of site s (three integer divisions, once per site).
+struct SiteCoords {
+    int x[4];
+    __device__ __forceinline__ SiteCoords(const Geom &g, int s) {
+        int r = s;
+        x[0] = r % g.n[0];
+        r /= g.n[0];
+        x[1] = r % g.n[1];
+        r /= g.n[1];
+        x[2] = r % g.n[2];
+        x[3] = r / g.n[2];
+    }
+};
+
+template <typename T, int MU, bool DAG, int BC, int NR>
+__device__ __forceinline__ void hop_dir(const Geom &g, const SiteCoords &xc,
+                                        const typename cplx_t<T>::type *__restrict__ U,
                                         const typename cplx_t<T>::type *__restrict__ in, int s,
-                                        typename cplx_t<T>::type acc[12]) {
-    float f;
-    SMPQ_FENCE();
-    int nf = neighbour(g, s, MU, +1, &f);
+                                        typename cplx_t<T>::type acc[12][NR]) {
+    const int n = g.n[MU], st = g.stride[MU], c = xc.x[MU];
+    const bool top = c == n - 1, bot = c == 0;
+    const int nf = top ? s - (n - 1) * st : s + st;
+    const int nbk = bot ? s + (n - 1) * st : s - st;
+    const T ff = top ? (T)g.bcf[MU] : (T)1;
+    const T fb = bot ? (T)g.bcf[MU] : (T)1;
     // forward: (1 - g) U(x) psi(x+mu)   [DAG: (1 + g)]
-    hop_one<T, MU, DAG ? +1 : -1, false, BC>(U, in, g.V, g.V, nf, s, (T)f, acc);
-    int nbk = neighbour(g, s, MU, -1, &f);
-    SMPQ_FENCE();
+    hop_one<T, MU, DAG ? +1 : -1, false, BC, NR>(U, in, g.V, g.V, nf, s, ff, acc);
+    SMPQ_HOP_BARRIER();
     // backward: (1 + g) U(x-mu)^dag psi(x-mu)   [DAG: (1 - g)]
-    hop_one<T, MU, DAG ? -1 : +1, true, BC>(U, in, g.V, g.V, nbk, nbk, (T)f, acc);
+    hop_one<T, MU, DAG ? -1 : +1, true, BC, NR>(U, in, g.V, g.V, nbk, nbk, fb, acc);
+    SMPQ_HOP_BARRIER();
 }
 
-// acc = hop(s) for the right-hand side whose tile base pointer is `in`
-// (already offset by tile and column).
-template <typename T, bool DAG, int BC>
+// acc = hop(s) for the NR columns whose tile base pointer is `in`
+// (already offset by tile and first column).
+template <typename T, bool DAG, int BC, int NR = 1>
 __device__ __forceinline__ void wilson_hop(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
                                            const typename cplx_t<T>::type *__restrict__ in, int s,
-                                           typename cplx_t<T>::type acc[12]) {
+                                           typename cplx_t<T>::type acc[12][NR]) {
     typedef typename cplx_t<T>::type C;
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = mkc<C>(0, 0);
-    hop_dir<T, 0, DAG, BC>(g, U, in, s, acc);
-    hop_dir<T, 1, DAG, BC>(g, U, in, s, acc);
-    hop_dir<T, 2, DAG, BC>(g, U, in, s, acc);
-    hop_dir<T, 3, DAG, BC>(g, U, in, s, acc);
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[c][r] = mkc<C>(0, 0);
+    const SiteCoords xc(g, s);
+    hop_dir<T, 0, DAG, BC, NR>(g, xc, U, in, s, acc);
+    hop_dir<T, 1, DAG, BC, NR>(g, xc, U, in, s, acc);
+    hop_dir<T, 2, DAG, BC, NR>(g, xc, U, in, s, acc);
+    hop_dir<T, 3, DAG, BC, NR>(g, xc, U, in, s, acc);
 }
 
 // Thread -> (tile, site, column) mapping shared by the lattice kernels:
-// blockDim.x = BC * spb threads, site = tile_site0 + threadIdx.x / BC, jj = threadIdx.x % BC.
-template <int BC> struct TileMap {
-    static constexpr int SPB = (256 / BC) > 0 ? (256 / BC) : 1; // sites per block
-    static constexpr int THREADS = BC * SPB;
+// TPS = BC/NR threads per site and SPB sites per block;
+// site = tile * SPB + tid / TPS, first column jj = (tid % TPS) * NR.
+template <int BC, int NR = 1> struct TileMap {
+    static constexpr int TPS = BC / NR;
+    static constexpr int SPB = (256 / TPS) > 0 ? (256 / TPS) : 1;
+    static constexpr int THREADS = TPS * SPB;
 };
