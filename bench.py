@@ -212,7 +212,7 @@ def run_gpu(args):
     U, dims = cfg["U"], cfg["dims"]
     V = int(np.prod(dims))
     a, b = _spectrum(CONFIG)
-    prec = smpq.SMPQ_FP32 if args.precision == "fp32" else smpq.SMPQ_FP64
+    prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
                 use_graphs=1, profile=1)
@@ -366,11 +366,14 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
         line = {
             "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == smpq.SMPQ_FP32 else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {smpq.SMPQ_FP32: "f32", smpq.SMPQ_FP64: "f64", smpq.SMPQ_MIXED: "f64+f32"}[prec],
+            "data": "synthetic",
             "config": {"workload": "8^3x16 flux Q=2 noise 0.1 + gauge transform, SMP r_min=4 mode 0, "
                                    "256 classes x 12 = 3072 sources x 14 shifts, tol 1e-10",
-                       "precision": "FP32 dslash/vectors + FP64 reliable updates" if prec == smpq.SMPQ_FP32
-                       else "FP64", "batch": B, "l2": "inputs larger than L2 (each solver vector %.1f GB)"
+                       "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
+                                     smpq.SMPQ_FP64: "FP64",
+                                     smpq.SMPQ_MIXED: "FP64 until ||r|| < 1e-4 ||b||, then FP32; FP64 shifted vectors"}[prec],
+                       "batch": B, "l2": "inputs larger than L2 (each solver vector %.1f GB)"
                        % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
             "clocks": clocks,
             "e2e": None if e2e_val is None else {
@@ -397,7 +400,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="smpq", choices=["smpq", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

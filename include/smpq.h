@@ -53,8 +53,10 @@ typedef enum {
 } smpq_status;
 
 typedef enum {
-    SMPQ_FP64 = 0, /* vectors, dslash and updates in FP64 (reference path) */
-    SMPQ_FP32 = 1  /* FP32 vectors and dslash with FP64 reliable updates, FP64 scalars */
+    SMPQ_FP64 = 0,  /* vectors, dslash and updates in FP64 (reference path) */
+    SMPQ_FP32 = 1,  /* FP32 vectors and dslash with FP64 reliable updates, FP64 scalars */
+    SMPQ_MIXED = 2  /* FP64 iterations until ||r|| <= switch_residual ||b||, then FP32;
+                       shifted directions and y in FP64 throughout */
 } smpq_precision;
 
 typedef struct {
@@ -69,6 +71,7 @@ typedef struct {
     int iters_per_check;   /* CG iterations launched between host convergence checks */
     int use_graphs;        /* capture those iterations in a CUDA graph */
     int profile;           /* time every D_W / D_W^dag launch of the solver with CUDA events */
+    double switch_residual; /* SMPQ_MIXED: relative residual at which FP64 iterations hand over to FP32 */
 } smpq_options;
 
 typedef struct {
@@ -92,7 +95,7 @@ typedef struct {
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
- * 10 iterations per check, graphs on, profiling off. */
+ * 10 iterations per check, graphs on, profiling off, switch_residual 1e-4. */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.

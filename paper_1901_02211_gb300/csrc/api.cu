@@ -91,7 +91,10 @@ int validate_options(smpq_ctx *ctx, const smpq_options *o) {
     if (o->npoles < 1 || o->npoles > SMPQ_MAX_POLES) return set_err(ctx, SMPQ_EINVAL, "npoles must be in 1..32");
     if (!(o->tol > 0) || !(o->tol < 1)) return set_err(ctx, SMPQ_EINVAL, "tol must be in (0, 1)");
     if (o->max_iter < 1) return set_err(ctx, SMPQ_EINVAL, "max_iter must be positive");
-    if (o->precision != SMPQ_FP64 && o->precision != SMPQ_FP32) return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    if (o->precision != SMPQ_FP64 && o->precision != SMPQ_FP32 && o->precision != SMPQ_MIXED)
+        return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    if (o->precision == SMPQ_MIXED && (!(o->switch_residual > 0) || !(o->switch_residual < 1)))
+        return set_err(ctx, SMPQ_EINVAL, "switch_residual must be in (0, 1)");
     if (!(o->reliable_delta > 0) || !(o->reliable_delta < 1))
         return set_err(ctx, SMPQ_EINVAL, "reliable_delta must be in (0, 1)");
     for (int mu = 0; mu < 4; ++mu)
@@ -124,7 +127,7 @@ int pick_bc(int B) {
 
 // device bytes one right-hand side costs in the solver (full-lattice vectors)
 size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
-    size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16) : (3 * 16);
+    size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16) : (prec == SMPQ_MIXED ? 3 * 16 + 3 * 8 : 3 * 16);
     size_t full = (size_t)ctx->V * 12 * per;
     size_t eb = prec == SMPQ_FP32 ? 8 : 16;
     size_t sup = (size_t)n_sup * 12 * (npoles * eb + 16);
@@ -301,6 +304,7 @@ int smpq_options_default(smpq_options *o) {
     o->iters_per_check = 10;
     o->use_graphs = 1;
     o->profile = 0;
+    o->switch_residual = 1e-4;
     return SMPQ_OK;
 }
 

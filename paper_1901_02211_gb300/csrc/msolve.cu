@@ -41,9 +41,6 @@ constexpr int TPB = 4;
 template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
 
-template <typename T> struct Prec;
-template <> struct Prec<double> { static constexpr int id = SMPQ_FP64; };
-template <> struct Prec<float> { static constexpr int id = SMPQ_FP32; };
 
 // ------------------------------------------------------------------ block reduction per column
 template <int BC>
@@ -74,7 +71,8 @@ struct Scal {
     int *act_rhs, *upd_rhs, *iters;                                  // [B]
     double *zeta, *zeta_prev, *zeta_new, *alpha_s, *beta_s;          // [n][B]
     int *act, *upd;                                                  // [n][B]
-    int *flags; // [0] active rhs count, [1] residual replacement requested, [2] breakdown
+    int *flags; // [0] active rhs count, [1] residual replacement requested, [2] breakdown,
+                // [3] active rhs still above the precision-switch residual
     double *hist; // Lanczos: [2][hist_len] alpha_k, beta_k of rhs 0 (nullable)
     int hist_len;
     int *iter_counter; // [1] global iteration count (for the history index)
@@ -293,14 +291,15 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 
 // Shifted updates on the support: y += c_i alpha_i p_i ; p_i = zeta_new_i r + beta_i p_i.
 // Support entry k of rhs j sits on lattice site supsite[rhs_class[j] * n_sup + k]
-// (identity when supsite == nullptr).  ps: [n][chunk][12][n_sup][BC] of T,
-// y: [chunk][12][n_sup][BC] of double2.
-template <typename T, int BC>
+// (identity when supsite == nullptr).  r is read in the iteration precision T,
+// ps ([shift][chunk][n_sup][12][BC]) is kept in TS, y ([chunk][n_sup][12][BC]) in FP64.
+template <typename T, typename TS, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     k_shift(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
-            const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<T>::type *__restrict__ ps,
+            const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<TS>::type *__restrict__ ps,
             double2 *__restrict__ y, Scal sc, ShiftParams sp, int G, int init) {
-    typedef typename cplx_t<T>::type C;
+    typedef typename cplx_t<T>::type CR;
+    typedef typename cplx_t<TS>::type C;
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
     const int cls = rhs_class[j];
     if (cls < 0) return;
@@ -314,7 +313,10 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         int site = supsite ? supsite[(size_t)cls * n_sup + k] : k;
         C rv[12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) rv[c] = r[rbase + ((size_t)site * 12 + c) * BC];
+        for (int c = 0; c < 12; ++c) {
+            CR v = r[rbase + ((size_t)site * 12 + c) * BC];
+            rv[c] = mkc<C>(v.x, v.y);
+        }
         if (init) { // p_i = b (= r at the start), y = 0
             for (int i = 0; i < nshift; ++i)
 #pragma unroll
@@ -329,8 +331,8 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         for (int i = 0; i < nshift; ++i) {
             if (!sc.upd[i * B + j]) continue;
             double ca = sp.c[i] * sc.alpha_s[i * B + j];
-            T zn = (T)sc.zeta_new[i * B + j];
-            T bs = (T)sc.beta_s[i * B + j];
+            TS zn = (TS)sc.zeta_new[i * B + j];
+            TS bs = (TS)sc.beta_s[i * B + j];
             C *pi = ps + i * sstride + sbase;
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
@@ -464,6 +466,7 @@ __global__ void __launch_bounds__(SCAL_THREADS)
     if (threadIdx.x) return;
     if (j == 0) {
         sc.flags[0] = 0;
+        sc.flags[3] = 0;
         if (sc.hist) {
             int it = sc.iter_counter[0];
             if (it < sc.hist_len) sc.hist[it] = 0; // filled below when rhs 0 is active
@@ -505,7 +508,8 @@ __global__ void __launch_bounds__(SCAL_THREADS)
 }
 
 __global__ void __launch_bounds__(SCAL_THREADS)
-    s2_kernel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2, double delta2) {
+    s2_kernel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2, double delta2,
+              double theta2) {
     __shared__ double sm[SCAL_THREADS];
     const int j = blockIdx.x;
     double rrn = part_sum(part_r, j, BC, G, sm);
@@ -541,6 +545,7 @@ __global__ void __launch_bounds__(SCAL_THREADS)
     sc.act_rhs[j] = any;
     if (any) atomicAdd(&sc.flags[0], 1);
     if (delta2 > 0 && rrn < delta2 * sc.rr_ref[j]) atomicOr(&sc.flags[1], 1);
+    if (any && rrn > theta2 * bb) atomicAdd(&sc.flags[3], 1); // still above the precision switch
 }
 
 // after a residual replacement: rr = |r_hi|^2, the base shift re-activates if
@@ -575,52 +580,63 @@ template <typename T, int BC> struct NRSel {
     static constexpr int value = (sizeof(T) == 4 && BC % SMPQ_FP32_NR == 0) ? SMPQ_FP32_NR : 1;
 };
 
-template <typename T, int BC> struct Solver {
-    typedef typename cplx_t<T>::type C;
-    static constexpr int NR = NRSel<T, BC>::value;
-    static int run(smpq_ctx *ctx, const SolveSpec &spec, const ShiftParams &sp, double tol, int max_iter,
-                   SolveOut *out, double *hist, int hist_len, int fixed_iters) {
-        const int B = spec.B, V = ctx->V, nchunk = B / BC;
-        const bool rel = (Prec<T>::id == SMPQ_FP32);
-        cudaStream_t st = ctx->stream;
+// elementwise FP64 -> FP32 copy of a field (same tiled layout)
+__global__ void k_to_fp32(const double2 *__restrict__ in, float2 *__restrict__ out, size_t n) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// One multi-shift solve of B right-hand sides in tiles of BC columns.  The
+// solve runs in one or two phases:
+//   SMPQ_FP64  : FP64 iterations (vectors, D_W, shifted directions);
+//   SMPQ_FP32  : FP32 iterations with FP64 reliable updates of the base system;
+//   SMPQ_MIXED : FP64 iterations until every right-hand side has
+//                ||r|| <= theta ||b||, then FP32 iterations without residual
+//                replacement; the shifted directions and y stay FP64 throughout.
+// Scalars, reductions and y are FP64 in every mode.
+template <int BC> struct Solve {
+    smpq_ctx *ctx;
+    const SolveSpec &spec;
+    ShiftParams sp;
+    int B, V, nchunk, G, Gs;
+    size_t nfield, nsupf, npart;
+    cudaStream_t st;
+    Scal sc;
+    Source src;
+    double *part0, *part1, *part2;
+    double2 *y;
+    double tol2;
+    int base_shift;
+    int *hflags = nullptr;
+    int iters = 0, nrel = 0;
+    bool prof;
+    int chk;
+
+    Solve(smpq_ctx *c, const SolveSpec &s, const ShiftParams &p) : ctx(c), spec(s), sp(p) {}
+
+    int setup(double tol, double *hist, int hist_len) {
+        B = spec.B;
+        V = ctx->V;
+        nchunk = B / BC;
+        st = ctx->stream;
         const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-        const int G = (ntiles + TPB - 1) / TPB;
-        const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
-        const int GN = (ntiles_n + TPB - 1) / TPB; // blocks per RHS tile of the NR-column kernels
+        G = (ntiles + TPB - 1) / TPB;
         const int nsup_tiles = (spec.n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-        const int Gs = std::max(1, (nsup_tiles + TPB - 1) / TPB);
-        const size_t nfield = (size_t)B * 12 * V;
-        const size_t nsupf = (size_t)B * 12 * spec.n_sup;
+        Gs = std::max(1, (nsup_tiles + TPB - 1) / TPB);
+        nfield = (size_t)B * 12 * V;
+        nsupf = (size_t)B * 12 * spec.n_sup;
+        // the NR-column kernels have at most as many blocks per tile as the 1-column ones
+        npart = (size_t)nchunk * std::max(G, Gs) * BC;
         std::vector<Buf> &ws = ctx->ws;
         if (ws.size() < W_COUNT) ws.resize(W_COUNT);
         int rc;
-        if ((rc = ensure(ctx, ws[W_P], nfield * sizeof(C)))) return rc;
-        if ((rc = ensure(ctx, ws[W_T], nfield * sizeof(C)))) return rc;
-        if ((rc = ensure(ctx, ws[W_R], nfield * sizeof(C)))) return rc;
-        if (rel) {
-            if ((rc = ensure(ctx, ws[W_XLO], nfield * sizeof(C)))) return rc;
-            if ((rc = ensure(ctx, ws[W_XHI], nfield * sizeof(double2)))) return rc;
-            if ((rc = ensure(ctx, ws[W_T64], nfield * sizeof(double2)))) return rc;
-        }
-        if (spec.n_sup > 0) {
-            if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * nsupf * sizeof(C)))) return rc;
-            if ((rc = ensure(ctx, ws[W_Y], nsupf * sizeof(double2)))) return rc;
-        }
-        const size_t npart = (size_t)nchunk * std::max(std::max(G, Gs), GN) * BC;
         if ((rc = ensure(ctx, ws[W_PART], 3 * npart * sizeof(double)))) return rc;
         const size_t nscal = (size_t)B * 7 + (size_t)sp.n * B * 5;
         const size_t nint = (size_t)B * 3 + (size_t)sp.n * B * 2 + 8;
         if ((rc = ensure(ctx, ws[W_SCAL], nscal * sizeof(double) + nint * sizeof(int)))) return rc;
-
-        C *p = (C *)ws[W_P].p, *t = (C *)ws[W_T].p, *r = (C *)ws[W_R].p;
-        C *xlo = rel ? (C *)ws[W_XLO].p : nullptr;
-        double2 *xhi = rel ? (double2 *)ws[W_XHI].p : nullptr;
-        double2 *t64 = rel ? (double2 *)ws[W_T64].p : nullptr;
-        C *ps = spec.n_sup > 0 ? (C *)ws[W_PS].p : nullptr;
-        double2 *y = spec.n_sup > 0 ? (double2 *)ws[W_Y].p : nullptr;
-        double *part0 = (double *)ws[W_PART].p, *part1 = part0 + npart, *part2 = part1 + npart;
-
-        Scal sc;
+        part0 = (double *)ws[W_PART].p;
+        part1 = part0 + npart;
+        part2 = part1 + npart;
         double *d = (double *)ws[W_SCAL].p;
         sc.rr = d; d += B; sc.bb = d; d += B; sc.alpha = d; d += B; sc.beta = d; d += B;
         sc.alpha_prev = d; d += B; sc.beta_prev = d; d += B; sc.rr_ref = d; d += B;
@@ -632,36 +648,16 @@ template <typename T, int BC> struct Solver {
         sc.flags = ip; ip += 4; sc.iter_counter = ip;
         sc.hist = hist;
         sc.hist_len = hist_len;
-
-        Source src;
         src.colour = spec.d_colour;
         src.src_class = spec.d_src_class;
         src.src_comp = spec.d_src_comp;
         src.b64 = (const double2 *)spec.d_src_field;
-
-        const dim3 grid(G, nchunk), gsup(Gs, nchunk), gridn(GN, nchunk);
-        const int THN = TileMap<BC, NR>::THREADS;
-        const int TH = TileMap<BC>::THREADS;
-        const int sblocks = B; // scalar kernels: one block per right-hand side
-        const double tol2 = tol * tol;
-        const double delta2 = rel ? ctx->opt.reliable_delta * ctx->opt.reliable_delta : 0.0;
-        const Geom g = ctx->geom;
-        const T kappa = (T)ctx->opt.kappa;
-        const C *U = (const C *)(rel ? ctx->U32.p : ctx->U64.p);
-        int base_shift = 0;
+        tol2 = tol * tol;
+        base_shift = 0;
         for (int i = 1; i < sp.n; ++i)
             if (sp.sig[i] < sp.sig[base_shift]) base_shift = i;
-
-        cudaMemsetAsync(sc.flags, 0, 5 * sizeof(int), st);
-        cudaEventRecord(ctx->ev1, st);
-        k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
-        s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, tol);
-        if (spec.n_sup > 0)
-            k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps, y,
-                                                sc, sp, Gs, 1);
-
-        const bool prof = ctx->opt.profile != 0;
-        const int chk = std::max(1, ctx->opt.iters_per_check);
+        prof = ctx->opt.profile != 0;
+        chk = std::max(1, ctx->opt.iters_per_check);
         if (prof) {
             while ((int)ctx->prof_ev.size() < 4 * chk) {
                 cudaEvent_t ev;
@@ -669,7 +665,64 @@ template <typename T, int BC> struct Solver {
                 ctx->prof_ev.push_back(ev);
             }
         }
-        const int per_iter = 5 + (spec.n_sup > 0 ? 1 : 0);
+        if (cudaMallocHost(&hflags, 4 * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, SMPQ_ENOMEM, "pinned host flags");
+        }
+        cudaMemsetAsync(sc.flags, 0, 5 * sizeof(int), st);
+        return SMPQ_OK;
+    }
+
+    ~Solve() {
+        if (hflags) cudaFreeHost(hflags);
+    }
+
+    void collect(int n) {
+        if (!prof) return;
+        for (int k = 0; k < n; ++k) {
+            float a = 0, b = 0;
+            if (cudaEventElapsedTime(&a, ctx->prof_ev[4 * k], ctx->prof_ev[4 * k + 1]) != cudaSuccess ||
+                cudaEventElapsedTime(&b, ctx->prof_ev[4 * k + 2], ctx->prof_ev[4 * k + 3]) != cudaSuccess) {
+                cudaGetLastError();
+                a = b = 0;
+            }
+            ctx->prof_a_ms += a;
+            ctx->prof_b_ms += b;
+        }
+        ctx->prof_a_n += n;
+        ctx->prof_b_n += n;
+    }
+
+    // Iterate with vectors of precision T and shifted directions of precision TS.
+    // init: start from x = 0 (sources); otherwise continue from the current state.
+    // rel: FP64 reliable updates (needs xlo, xhi, t64).  theta2 > 0: return once
+    // every active right-hand side has ||r||^2 <= theta2 ||b||^2.
+    // fixed > 0: exactly `fixed` iterations, no checks (Lanczos).
+    template <typename T, typename TS>
+    int phase(typename cplx_t<T>::type *p, typename cplx_t<T>::type *t, typename cplx_t<T>::type *r,
+              typename cplx_t<T>::type *xlo, double2 *xhi, double2 *t64, typename cplx_t<TS>::type *ps, bool init,
+              bool rel, double theta2, int fixed, int max_iter) {
+        typedef typename cplx_t<T>::type C;
+        constexpr int NR = NRSel<T, BC>::value;
+        const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
+        const int GN = (ntiles_n + TPB - 1) / TPB;
+        const dim3 grid(G, nchunk), gsup(Gs, nchunk), gridn(GN, nchunk);
+        const int TH = TileMap<BC>::THREADS, THN = TileMap<BC, NR>::THREADS;
+        const int sblocks = B;
+        const double delta2 = rel ? ctx->opt.reliable_delta * ctx->opt.reliable_delta : 0.0;
+        const Geom g = ctx->geom;
+        const T kappa = (T)ctx->opt.kappa;
+        const C *U = (const C *)(sizeof(T) == 4 ? ctx->U32.p : ctx->U64.p);
+        const bool shifts = spec.n_sup > 0;
+        const int per_iter = 5 + (shifts ? 1 : 0);
+        if (init) {
+            k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
+            s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, sqrt(tol2));
+            if (shifts)
+                k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r,
+                                                        ps, y, sc, sp, Gs, 1);
+            ctx->launches += 2 + (shifts ? 1 : 0);
+        }
         auto iteration = [&](int k) {
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
             k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(g, U, p, t, kappa, part0, part1, GN);
@@ -683,27 +736,11 @@ template <typename T, int BC> struct Solver {
                 k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
                                                                     GN);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-            s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GN, part2, sc, sp, tol2, delta2);
-            if (spec.n_sup > 0)
-                k_shift<T, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps,
-                                                    y, sc, sp, Gs, 0);
+            s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GN, part2, sc, sp, tol2, delta2, theta2);
+            if (shifts)
+                k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r,
+                                                        ps, y, sc, sp, Gs, 0);
             k_update_p<T, BC><<<grid, TH, 0, st>>>(V, r, p, sc.beta, sc.upd_rhs, G);
-        };
-        // after the stream is synchronised: add the event timings of the last `n` iterations
-        auto collect = [&](int n) {
-            if (!prof) return;
-            for (int k = 0; k < n; ++k) {
-                float a = 0, b = 0;
-                if (cudaEventElapsedTime(&a, ctx->prof_ev[4 * k], ctx->prof_ev[4 * k + 1]) != cudaSuccess ||
-                    cudaEventElapsedTime(&b, ctx->prof_ev[4 * k + 2], ctx->prof_ev[4 * k + 3]) != cudaSuccess) {
-                    cudaGetLastError();
-                    a = b = 0;
-                }
-                ctx->prof_a_ms += a;
-                ctx->prof_b_ms += b;
-            }
-            ctx->prof_a_n += n;
-            ctx->prof_b_n += n;
         };
         auto reliable = [&]() {
             ctx->launches += 4;
@@ -714,11 +751,22 @@ template <typename T, int BC> struct Solver {
             cudaMemsetAsync(sc.flags, 0, 2 * sizeof(int), st);
             s_rel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, base_shift);
         };
-
+        if (fixed > 0) {
+            for (int k = 0; k < fixed; ++k) {
+                iteration(prof ? k % chk : 0);
+                if (prof && k % chk == chk - 1) {
+                    cudaStreamSynchronize(st);
+                    collect(chk);
+                }
+            }
+            ctx->launches += (long long)fixed * per_iter;
+            iters += fixed;
+            return SMPQ_OK;
+        }
+        // (profiling records CUDA events between launches, so it runs without a graph)
         cudaGraphExec_t gexec = nullptr;
         bool graph_ok = false;
-        // (profiling records CUDA events between launches, so it runs without a graph)
-        if (ctx->opt.use_graphs && fixed_iters == 0 && !prof) {
+        if (ctx->opt.use_graphs && !prof) {
             cudaGraph_t graph;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 for (int k = 0; k < chk; ++k) iteration(k);
@@ -729,48 +777,40 @@ template <typename T, int BC> struct Solver {
             }
             cudaGetLastError();
         }
-        int *hflags = nullptr;
-        cudaMallocHost(&hflags, 4 * sizeof(int));
-        int iters = 0, nrel = 0, status = SMPQ_OK;
-        ctx->launches += 2 + (spec.n_sup > 0 ? 1 : 0);
-        if (fixed_iters > 0) {
-            for (int k = 0; k < fixed_iters; ++k) {
-                iteration(prof ? k % chk : 0);
-                if (prof && k % chk == chk - 1) { cudaStreamSynchronize(st); collect(chk); }
+        int status = SMPQ_OK;
+        for (;;) {
+            if (graph_ok) cudaGraphLaunch(gexec, st);
+            else
+                for (int k = 0; k < chk; ++k) iteration(k);
+            ctx->launches += (long long)chk * per_iter;
+            iters += chk;
+            cudaMemcpyAsync(hflags, sc.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
+            collect(chk);
+            if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
+            bool done = hflags[0] == 0;
+            if (rel && (hflags[1] || done)) {
+                reliable();
+                ++nrel;
+                cudaMemcpyAsync(hflags, sc.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+                e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) { status = cuda_check(ctx, e, "residual replacement"); break; }
+                done = hflags[0] == 0;
             }
-            ctx->launches += (long long)fixed_iters * per_iter;
-            iters = fixed_iters;
-        } else {
-            for (;;) {
-                if (graph_ok) cudaGraphLaunch(gexec, st);
-                else
-                    for (int k = 0; k < chk; ++k) iteration(k);
-                ctx->launches += (long long)chk * per_iter;
-                iters += chk;
-                cudaMemcpyAsync(hflags, sc.flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
-                cudaError_t e = cudaStreamSynchronize(st);
-                if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
-                collect(chk);
-                if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
-                bool done = hflags[0] == 0;
-                if (rel && (hflags[1] || done)) {
-                    reliable();
-                    ++nrel;
-                    cudaMemcpyAsync(hflags, sc.flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
-                    e = cudaStreamSynchronize(st);
-                    if (e != cudaSuccess) { status = cuda_check(ctx, e, "residual replacement"); break; }
-                    done = hflags[0] == 0;
-                }
-                if (done) break;
-                if (iters >= max_iter) {
-                    status = set_err(ctx, SMPQ_ENOCONV, "multishift CG reached max_iter");
-                    break;
-                }
+            if (done) break;
+            if (theta2 > 0 && hflags[3] == 0) break; // every rhs below the switch residual
+            if (iters >= max_iter) {
+                status = set_err(ctx, SMPQ_ENOCONV, "multishift CG reached max_iter");
+                break;
             }
         }
-        cudaEventRecord(ctx->ev2, st);
         if (gexec) cudaGraphExecDestroy(gexec);
-        // statistics: max residual |zeta_i| sqrt(rr/bb), max iterations
+        return status;
+    }
+
+    int finish(SolveOut *out, int fixed) {
+        cudaEventRecord(ctx->ev2, st);
         std::vector<double> hz((size_t)sp.n * B), hrr(B), hbb(B);
         std::vector<int> hit(B);
         cudaMemcpyAsync(hz.data(), sc.zeta, hz.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -778,7 +818,6 @@ template <typename T, int BC> struct Solver {
         cudaMemcpyAsync(hbb.data(), sc.bb, B * sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(hit.data(), sc.iters, B * sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
-        cudaFreeHost(hflags);
         if (e != cudaSuccess) return cuda_check(ctx, e, "multishift statistics");
         double worst = 0;
         int maxit = 0;
@@ -791,26 +830,82 @@ template <typename T, int BC> struct Solver {
         float ms = 0;
         cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2);
         out->y = y;
-        out->iterations = fixed_iters > 0 ? fixed_iters : maxit;
+        out->iterations = fixed > 0 ? fixed : maxit;
         out->reliable_updates = nrel;
         out->max_resid = worst;
         out->solve_ms = ms;
-        if (status == SMPQ_OK) {
-            cudaError_t le = cudaGetLastError();
-            if (le != cudaSuccess) return cuda_check(ctx, le, "multishift launch");
+        return cuda_check(ctx, cudaGetLastError(), "multishift launch");
+    }
+
+    static int run(smpq_ctx *ctx, const SolveSpec &spec, const ShiftParams &sp, double tol, int max_iter,
+                   SolveOut *out, double *hist, int hist_len, int fixed) {
+        Solve S(ctx, spec, sp);
+        int rc = S.setup(tol, hist, hist_len);
+        if (rc) return rc;
+        std::vector<Buf> &ws = ctx->ws;
+        const size_t nf = S.nfield;
+        const bool shifts = spec.n_sup > 0;
+        cudaEventRecord(ctx->ev1, S.st);
+        if (spec.prec == SMPQ_FP64 || spec.prec == SMPQ_MIXED) {
+            if ((rc = ensure(ctx, ws[W_P], nf * sizeof(double2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T], nf * sizeof(double2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_R], nf * sizeof(double2)))) return rc;
+            if (shifts) {
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(double2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
+            }
+            S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            double2 *ps = shifts ? (double2 *)ws[W_PS].p : nullptr;
+            double2 *p = (double2 *)ws[W_P].p, *t = (double2 *)ws[W_T].p, *r = (double2 *)ws[W_R].p;
+            const double theta = spec.prec == SMPQ_MIXED ? ctx->opt.switch_residual : 0.0;
+            rc = S.template phase<double, double>(p, t, r, nullptr, nullptr, nullptr, ps, true, false, theta * theta,
+                                                  fixed, max_iter);
+            if (rc) return rc;
+            if (spec.prec == SMPQ_MIXED && fixed == 0) {
+                // continue in FP32 from the FP64 state
+                if ((rc = ensure(ctx, ws[W_XLO], 3 * nf * sizeof(float2)))) return rc;
+                float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf;
+                const unsigned nb = (unsigned)((nf + 255) / 256);
+                k_to_fp32<<<nb, 256, 0, S.st>>>(p, p32, nf);
+                k_to_fp32<<<nb, 256, 0, S.st>>>(r, r32, nf);
+                ctx->launches += 2;
+                cudaMemcpyAsync(S.hflags, S.sc.flags, sizeof(int), cudaMemcpyDeviceToHost, S.st);
+                cudaStreamSynchronize(S.st);
+                if (S.hflags[0] > 0) {
+                    rc = S.template phase<float, double>(p32, t32, r32, nullptr, nullptr, nullptr, ps, false, false,
+                                                         0.0, 0, max_iter);
+                    if (rc) return rc;
+                }
+            }
+        } else {
+            if ((rc = ensure(ctx, ws[W_P], nf * sizeof(float2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T], nf * sizeof(float2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_R], nf * sizeof(float2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XLO], nf * sizeof(float2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(double2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T64], nf * sizeof(double2)))) return rc;
+            if (shifts) {
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(float2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
+            }
+            S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            rc = S.template phase<float, float>((float2 *)ws[W_P].p, (float2 *)ws[W_T].p, (float2 *)ws[W_R].p,
+                                                (float2 *)ws[W_XLO].p, (double2 *)ws[W_XHI].p,
+                                                (double2 *)ws[W_T64].p, shifts ? (float2 *)ws[W_PS].p : nullptr,
+                                                true, true, 0.0, fixed, max_iter);
+            if (rc) return rc;
         }
-        return status;
+        return S.finish(out, fixed);
     }
 };
 
-template <typename T>
 int dispatch_bc(smpq_ctx *ctx, const SolveSpec &spec, const ShiftParams &sp, double tol, int max_iter, SolveOut *out,
                 double *hist, int hist_len, int fixed) {
     switch (spec.BC) {
-    case 1: return Solver<T, 1>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    case 12: return Solver<T, 12>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    case 24: return Solver<T, 24>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    case 48: return Solver<T, 48>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
+    case 1: return Solve<1>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
+    case 12: return Solve<12>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
+    case 24: return Solve<24>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
+    case 48: return Solve<48>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
     default: return set_err(ctx, SMPQ_EINVAL, "unsupported rhs tile width");
     }
 }
@@ -831,9 +926,7 @@ ShiftParams make_shifts(const smpq_ctx *ctx) {
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out) {
     if (spec.B % spec.BC) return set_err(ctx, SMPQ_EINVAL, "rhs count must be a multiple of the tile width");
     ShiftParams sp = make_shifts(ctx);
-    if (spec.prec == SMPQ_FP32)
-        return dispatch_bc<float>(ctx, spec, sp, ctx->opt.tol, ctx->opt.max_iter, out, nullptr, 0, 0);
-    return dispatch_bc<double>(ctx, spec, sp, ctx->opt.tol, ctx->opt.max_iter, out, nullptr, 0, 0);
+    return dispatch_bc(ctx, spec, sp, ctx->opt.tol, ctx->opt.max_iter, out, nullptr, 0, 0);
 }
 
 // ------------------------------------------------------------------ spectrum (Lanczos from CG coefficients)
@@ -878,7 +971,7 @@ int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi) {
     spec.d_src_field = (const double *)b;
     SolveOut out;
     // the counter lives in the scalar block; reset it through a fresh solve
-    rc = dispatch_bc<double>(ctx, spec, sp, 0.0, iters, &out, hist, iters, iters);
+    rc = dispatch_bc(ctx, spec, sp, 0.0, iters, &out, hist, iters, iters);
     if (rc) return rc;
     std::vector<double> h(2 * (size_t)iters);
     cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);

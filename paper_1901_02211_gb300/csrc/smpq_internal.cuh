@@ -185,7 +185,7 @@ template <typename T> void launch_dslash(const Geom &g, const void *U, const voi
 // msolve.cu : multi-shift CG over a batch (see msolve.cu for the contract)
 struct SolveSpec {
     int B, BC;                 // right-hand sides and tile width
-    int prec;                  // SMPQ_FP64 / SMPQ_FP32
+    int prec;                  // SMPQ_FP64 / SMPQ_FP32 / SMPQ_MIXED
     int full_support;          // 1: shifted vectors on every site (apply_dov); 0: star support
     int n_sup;                 // support entries per rhs
     const int *d_supsite;      // [n_sup_classes][n_sup] site of support entry k for a class

@@ -26,6 +26,7 @@ SMPQ_ENOTSU3 = -7
 SMPQ_ESTATE = -8
 SMPQ_FP64 = 0
 SMPQ_FP32 = 1
+SMPQ_MIXED = 2
 
 _NAMES = {v: k for k, v in globals().items() if k.startswith("SMPQ_E") or k == "SMPQ_OK"}
 
@@ -49,6 +50,7 @@ class smpq_options(ctypes.Structure):
         ("iters_per_check", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("switch_residual", ctypes.c_double),
     ]
 
 

@@ -165,7 +165,7 @@ def test_unit_links_give_zero(S):
 
 
 @pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
 def test_qx_8x16_sampled(S, r, classes, prec):
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
@@ -173,7 +173,7 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     zolo, delta = _zolo(a, b)
     colour, n = probing.color_sites(dims, r, 0)
     ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=classes, batch_colours=len(classes))
-    precision = S.SMPQ_FP64 if prec == "fp64" else S.SMPQ_FP32
+    precision = {"fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32, "mixed": S.SMPQ_MIXED}[prec]
     with _session(S, precision=precision) as s:
         s.load_gauge(dims, U)
         s.set_spectrum(a, b)
@@ -183,9 +183,11 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     err = np.abs(q[mask] - ref[mask]).max()
     print("8^3x16 r=%d %s: max |dq| = %.3e, iterations %d, reliable updates %d" % (
         r, prec, err, st["max_iterations"], st["reliable_updates"]))
-    tol = 1e-8 if prec == "fp64" else 1e-5
+    # FP64 and the FP64-then-FP32 path meet the 1e-8 per-site bar; the FP32
+    # path with FP64 reliable updates has the FP32 floor of its shifted systems
+    tol = 1e-5 if prec == "fp32" else 1e-8
     assert err <= tol
-    assert abs(Q - ref.real[mask].sum()) <= (1e-9 if prec == "fp64" else 1e-4)
+    assert abs(Q - ref.real[mask].sum()) <= (1e-4 if prec == "fp32" else 1e-9)
 
 
 # ----------------------------------------------------------------------------- host/device buffers, determinism, errors
