@@ -215,7 +215,7 @@ def run_gpu(args):
     prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
-                use_graphs=1, profile=1)
+                use_graphs=1, profile=1, switch_residual=args.switch)
     s.load_gauge(dims, U)
     s.set_spectrum(a, b)
     n_classes = s.build_sources(R_MIN, MODE)
@@ -372,7 +372,8 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
                                    "256 classes x 12 = 3072 sources x 14 shifts, tol 1e-10",
                        "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
                                      smpq.SMPQ_FP64: "FP64",
-                                     smpq.SMPQ_MIXED: "FP64 until ||r|| < 1e-4 ||b||, then FP32; FP64 shifted vectors"}[prec],
+                                     smpq.SMPQ_MIXED: "FP64 until ||r|| < %g ||b||, then FP32; FP64 shifted vectors"
+                                     % args.switch}[prec],
                        "batch": B, "l2": "inputs larger than L2 (each solver vector %.1f GB)"
                        % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
             "clocks": clocks,
@@ -404,6 +405,7 @@ def main():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--switch", type=float, default=1e-2, help="SMPQ_MIXED: FP64 -> FP32 switch residual")
     ap.add_argument("--classes", type=int, default=0, help="profiling: only the first N colour classes")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -55,8 +55,9 @@ typedef enum {
 typedef enum {
     SMPQ_FP64 = 0,  /* vectors, dslash and updates in FP64 (reference path) */
     SMPQ_FP32 = 1,  /* FP32 vectors and dslash with FP64 reliable updates, FP64 scalars */
-    SMPQ_MIXED = 2  /* FP64 iterations until ||r|| <= switch_residual ||b||, then FP32;
-                       shifted directions and y in FP64 throughout */
+    SMPQ_MIXED = 2  /* FP64-accurate iterations (float-float arithmetic on FP64-sized data)
+                       until ||r|| <= switch_residual ||b||, then FP32 without residual
+                       replacement; shifted directions and y in FP64 throughout */
 } smpq_precision;
 
 typedef struct {
@@ -95,7 +96,7 @@ typedef struct {
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
- * 10 iterations per check, graphs on, profiling off, switch_residual 1e-4. */
+ * 10 iterations per check, graphs on, profiling off, switch_residual 1e-2. */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.

@@ -304,7 +304,7 @@ int smpq_options_default(smpq_options *o) {
     o->iters_per_check = 10;
     o->use_graphs = 1;
     o->profile = 0;
-    o->switch_residual = 1e-4;
+    o->switch_residual = 1e-2;
     return SMPQ_OK;
 }
 
@@ -351,6 +351,7 @@ int smpq_destroy(smpq_ctx *ctx) {
         for (auto &b : ctx->ws) release(b);
         release(ctx->U64);
         release(ctx->U32);
+        release(ctx->Udf);
         release(ctx->d_colour);
         release(ctx->d_members);
         cudaEventDestroy(ctx->ev0);
@@ -391,6 +392,7 @@ int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int o
     int rc;
     if ((rc = ensure(ctx, ctx->U64, (size_t)V * 36 * sizeof(double2)))) return rc;
     if ((rc = ensure(ctx, ctx->U32, (size_t)V * 36 * sizeof(float2)))) return rc;
+    if ((rc = ensure(ctx, ctx->Udf, (size_t)V * 36 * sizeof(df64c)))) return rc;
     const double *src = links;
     if (!on_device) {
         if ((rc = ensure(ctx, ctx->ws[W_MISC], (size_t)V * 36 * sizeof(double2)))) return rc;
@@ -401,7 +403,7 @@ int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int o
     for (int mu = 0; mu < 4; ++mu) ctx->dims[mu] = dims[mu];
     ctx->V = (int)V;
     set_geom(ctx);
-    launch_pack_links(src, (double *)ctx->U64.p, (float *)ctx->U32.p, (int)V, ctx->stream);
+    launch_pack_links(src, (double *)ctx->U64.p, (float *)ctx->U32.p, ctx->Udf.p, (int)V, ctx->stream);
     if ((rc = ensure(ctx, ctx->ws[W_PART], 64))) return rc;
     double *derr = (double *)ctx->ws[W_PART].p;
     launch_su3_check((const double *)ctx->U64.p, (int)V, derr, ctx->stream);

@@ -1,0 +1,77 @@
+// Float-float ("double-single") arithmetic: a value is the unevaluated sum
+// hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant
+// bits.  The operations are the error-free transformations of Knuth (two-sum)
+// and Dekker (two-product, here with a fused multiply-add), as collected by
+// Hida, Li and Bailey (QD library, 2001) and Thall (GPU double-float, 2006).
+//
+// GB300 executes FP32 about 60 times faster than FP64, so the FP64-accurate
+// first phase of the mixed solver runs on this type: the bytes moved are those
+// of FP64, the arithmetic stays on the FP32 pipes.  No FP64 instruction is
+// issued except in the explicit conversions to and from double.
+#pragma once
+#include <cuda_runtime.h>
+
+struct __align__(8) df64 {
+    float hi, lo;
+    __host__ __device__ __forceinline__ df64() {}
+    __host__ __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ __forceinline__ df64(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ __forceinline__ df64(float v) : hi(v), lo(0.f) {}
+    __host__ __device__ __forceinline__ df64(double v) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    }
+    __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ __forceinline__ explicit operator float() const { return hi + lo; }
+};
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// s + e = a + b exactly when |a| >= |b|
+__device__ __forceinline__ void quick_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    e = b - (s - a);
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    float h, l;
+    quick_two_sum(s, e, h, l);
+    return df64(h, l);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p); // exact error of the product (Dekker, with FMA)
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    float h, l;
+    quick_two_sum(p, e, h, l);
+    return df64(h, l);
+}
+__device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
+
+struct __align__(16) df64c {
+    df64 x, y;
+};
+
+// complex helpers with the signatures of smpq_internal.cuh
+__device__ __forceinline__ df64c cadd(df64c a, df64c b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ df64c csub(df64c a, df64c b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ df64c cmul(df64c a, df64c b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ df64c cfma(df64c a, df64c b, df64c acc) {
+    return {acc.x + (a.x * b.x - a.y * b.y), acc.y + (a.x * b.y + a.y * b.x)};
+}
+__device__ __forceinline__ df64c cfmac(df64c a, df64c b, df64c acc) { // acc + conj(a) b
+    return {acc.x + (a.x * b.x + a.y * b.y), acc.y + (a.x * b.y - a.y * b.x)};
+}
+__device__ __forceinline__ df64c cmuli(df64c a) { return {-a.y, a.x}; }
+__device__ __forceinline__ df64c cneg(df64c a) { return {-a.x, -a.y}; }
+__device__ __forceinline__ df64c cscale(df64 s, df64c a) { return {s * a.x, s * a.y}; }

@@ -7,7 +7,7 @@
 // ------------------------------------------------------------------ links
 // U_aos: double[V][4][3][3][2] -> U64/U32: [(mu * V + s) * 9 + e] complex
 __global__ void pack_links_kernel(const double2 *__restrict__ Uaos, double2 *__restrict__ U64,
-                                  float2 *__restrict__ U32, int V) {
+                                  float2 *__restrict__ U32, df64c *__restrict__ Udf, int V) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= (long)V * 36) return;
     int s = (int)(i / 36), k = (int)(i % 36); // k = mu*9 + e
@@ -15,12 +15,13 @@ __global__ void pack_links_kernel(const double2 *__restrict__ Uaos, double2 *__r
     size_t o = ((size_t)(k / 9) * V + s) * 9 + (k % 9);
     U64[o] = u;
     U32[o] = make_float2((float)u.x, (float)u.y);
+    Udf[o] = df64c{df64(u.x), df64(u.y)};
 }
 
-void launch_pack_links(const double *U_aos, double *U64, float *U32, int V, cudaStream_t st) {
+void launch_pack_links(const double *U_aos, double *U64, float *U32, void *Udf, int V, cudaStream_t st) {
     long n = (long)V * 36;
     pack_links_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)U_aos, (double2 *)U64,
-                                                                     (float2 *)U32, V);
+                                                                     (float2 *)U32, (df64c *)Udf, V);
 }
 
 // max over links of max(|U U^dag - 1|, |det U - 1|), as the bit pattern of a

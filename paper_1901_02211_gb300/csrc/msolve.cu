@@ -40,6 +40,13 @@ constexpr int TPB = 4;
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
+template <> struct MinBlocks<df64> { static constexpr int value = 1; };
+
+// link copy matching the iteration precision
+template <typename T> struct Links;
+template <> struct Links<double> { static const void *get(const smpq_ctx *c) { return c->U64.p; } };
+template <> struct Links<float> { static const void *get(const smpq_ctx *c) { return c->U32.p; } };
+template <> struct Links<df64> { static const void *get(const smpq_ctx *c) { return c->Udf.p; } };
 
 
 // ------------------------------------------------------------------ block reduction per column
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             CR v = r[rbase + ((size_t)site * 12 + c) * BC];
-            rv[c] = mkc<C>(v.x, v.y);
+            rv[c] = mkc<C>(to_d(v.x), to_d(v.y));
         }
         if (init) { // p_i = b (= r at the start), y = 0
             for (int i = 0; i < nshift; ++i)
@@ -580,8 +587,8 @@ template <typename T, int BC> struct NRSel {
     static constexpr int value = (sizeof(T) == 4 && BC % SMPQ_FP32_NR == 0) ? SMPQ_FP32_NR : 1;
 };
 
-// elementwise FP64 -> FP32 copy of a field (same tiled layout)
-__global__ void k_to_fp32(const double2 *__restrict__ in, float2 *__restrict__ out, size_t n) {
+// elementwise float-float -> FP32 copy of a field (same tiled layout)
+__global__ void k_to_fp32(const df64c *__restrict__ in, float2 *__restrict__ out, size_t n) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
@@ -712,7 +719,7 @@ template <int BC> struct Solve {
         const double delta2 = rel ? ctx->opt.reliable_delta * ctx->opt.reliable_delta : 0.0;
         const Geom g = ctx->geom;
         const T kappa = (T)ctx->opt.kappa;
-        const C *U = (const C *)(sizeof(T) == 4 ? ctx->U32.p : ctx->U64.p);
+        const C *U = (const C *)Links<T>::get(ctx);
         const bool shifts = spec.n_sup > 0;
         const int per_iter = 5 + (shifts ? 1 : 0);
         if (init) {
@@ -846,7 +853,7 @@ template <int BC> struct Solve {
         const size_t nf = S.nfield;
         const bool shifts = spec.n_sup > 0;
         cudaEventRecord(ctx->ev1, S.st);
-        if (spec.prec == SMPQ_FP64 || spec.prec == SMPQ_MIXED) {
+        if (spec.prec == SMPQ_FP64) {
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(double2)))) return rc;
             if ((rc = ensure(ctx, ws[W_T], nf * sizeof(double2)))) return rc;
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(double2)))) return rc;
@@ -855,27 +862,40 @@ template <int BC> struct Solve {
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
-            double2 *ps = shifts ? (double2 *)ws[W_PS].p : nullptr;
-            double2 *p = (double2 *)ws[W_P].p, *t = (double2 *)ws[W_T].p, *r = (double2 *)ws[W_R].p;
-            const double theta = spec.prec == SMPQ_MIXED ? ctx->opt.switch_residual : 0.0;
-            rc = S.template phase<double, double>(p, t, r, nullptr, nullptr, nullptr, ps, true, false, theta * theta,
-                                                  fixed, max_iter);
+            rc = S.template phase<double, double>((double2 *)ws[W_P].p, (double2 *)ws[W_T].p, (double2 *)ws[W_R].p,
+                                                  nullptr, nullptr, nullptr,
+                                                  shifts ? (double2 *)ws[W_PS].p : nullptr, true, false, 0.0, fixed,
+                                                  max_iter);
             if (rc) return rc;
-            if (spec.prec == SMPQ_MIXED && fixed == 0) {
-                // continue in FP32 from the FP64 state
-                if ((rc = ensure(ctx, ws[W_XLO], 3 * nf * sizeof(float2)))) return rc;
-                float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf;
-                const unsigned nb = (unsigned)((nf + 255) / 256);
-                k_to_fp32<<<nb, 256, 0, S.st>>>(p, p32, nf);
-                k_to_fp32<<<nb, 256, 0, S.st>>>(r, r32, nf);
-                ctx->launches += 2;
-                cudaMemcpyAsync(S.hflags, S.sc.flags, sizeof(int), cudaMemcpyDeviceToHost, S.st);
-                cudaStreamSynchronize(S.st);
-                if (S.hflags[0] > 0) {
-                    rc = S.template phase<float, double>(p32, t32, r32, nullptr, nullptr, nullptr, ps, false, false,
-                                                         0.0, 0, max_iter);
-                    if (rc) return rc;
-                }
+        } else if (spec.prec == SMPQ_MIXED) {
+            // phase 1: float-float (FP64-accurate) vectors and D_W down to the switch residual
+            if ((rc = ensure(ctx, ws[W_P], nf * sizeof(df64c)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T], nf * sizeof(df64c)))) return rc;
+            if ((rc = ensure(ctx, ws[W_R], nf * sizeof(df64c)))) return rc;
+            if (shifts) {
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(double2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
+            }
+            S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            double2 *ps = shifts ? (double2 *)ws[W_PS].p : nullptr;
+            df64c *p = (df64c *)ws[W_P].p, *t = (df64c *)ws[W_T].p, *r = (df64c *)ws[W_R].p;
+            const double theta = ctx->opt.switch_residual;
+            rc = S.template phase<df64, double>(p, t, r, nullptr, nullptr, nullptr, ps, true, false, theta * theta, 0,
+                                                max_iter);
+            if (rc) return rc;
+            // phase 2: FP32 vectors and D_W from the phase-1 state, shifted vectors stay FP64
+            if ((rc = ensure(ctx, ws[W_XLO], 3 * nf * sizeof(float2)))) return rc;
+            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf;
+            const unsigned nb = (unsigned)((nf + 255) / 256);
+            k_to_fp32<<<nb, 256, 0, S.st>>>(p, p32, nf);
+            k_to_fp32<<<nb, 256, 0, S.st>>>(r, r32, nf);
+            ctx->launches += 2;
+            cudaMemcpyAsync(S.hflags, S.sc.flags, sizeof(int), cudaMemcpyDeviceToHost, S.st);
+            cudaStreamSynchronize(S.st);
+            if (S.hflags[0] > 0) {
+                rc = S.template phase<float, double>(p32, t32, r32, nullptr, nullptr, nullptr, ps, false, false, 0.0, 0,
+                                                     max_iter);
+                if (rc) return rc;
             }
         } else {
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(float2)))) return rc;

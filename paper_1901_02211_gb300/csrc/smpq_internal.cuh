@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/smpq.h"
+#include "df64.cuh"
 
 #define SMPQ_MAX_POLES 32
 
@@ -14,6 +15,12 @@
 template <typename T> struct cplx_t;
 template <> struct cplx_t<double> { typedef double2 type; };
 template <> struct cplx_t<float> { typedef float2 type; };
+template <> struct cplx_t<df64> { typedef df64c type; };
+
+// explicit conversion of a real component to double
+__host__ __device__ __forceinline__ double to_d(double v) { return v; }
+__host__ __device__ __forceinline__ double to_d(float v) { return v; }
+__host__ __device__ __forceinline__ double to_d(df64 v) { return (double)v; }
 
 template <typename C> __host__ __device__ __forceinline__ C mkc(double re, double im) {
     C c;
@@ -126,7 +133,7 @@ struct smpq_ctx {
     Geom geom;
     int dims[4] = {0, 0, 0, 0};
     int V = 0;
-    Buf U64, U32;
+    Buf U64, U32, Udf; // FP64, FP32 and float-float copies of the links
 
     // spectrum / rational
     bool have_spec = false;
@@ -173,7 +180,7 @@ int colour_sites_host(const int dims[4], int r, int mode, std::vector<int> &colo
 
 // ---------------------------------------------------------------- kernel launchers
 // dslash.cu
-void launch_pack_links(const double *U_aos, double *U64, float *U32, int V, cudaStream_t st);
+void launch_pack_links(const double *U_aos, double *U64, float *U32, void *Udf, int V, cudaStream_t st);
 void launch_su3_check(const double *U64, int V, double *dev_maxerr, cudaStream_t st);
 // convert ABI spinors [V][12][B] (FP64) <-> internal tiled layout of precision T
 template <typename T> void launch_to_tiled(const double *in, void *out, int V, int B, int BC, cudaStream_t st);

@@ -165,7 +165,7 @@ def test_unit_links_give_zero(S):
 
 
 @pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed1e-2"])
 def test_qx_8x16_sampled(S, r, classes, prec):
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
@@ -173,8 +173,9 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     zolo, delta = _zolo(a, b)
     colour, n = probing.color_sites(dims, r, 0)
     ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=classes, batch_colours=len(classes))
-    precision = {"fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32, "mixed": S.SMPQ_MIXED}[prec]
-    with _session(S, precision=precision) as s:
+    precision = S.SMPQ_MIXED if prec.startswith("mixed") else {"fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32}[prec]
+    switch = float(prec[5:]) if prec.startswith("mixed") else 1e-2
+    with _session(S, precision=precision, switch_residual=switch) as s:
         s.load_gauge(dims, U)
         s.set_spectrum(a, b)
         s.build_sources(r, 0)
