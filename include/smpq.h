@@ -92,6 +92,12 @@ typedef struct {
     long long dslash_launches;
     double update_ms;       /* profile: summed time of the r -= alpha (D_W^dag t + s0 p) launches */
     long long update_launches;
+    /* profile, FP64-accurate iterations (SMPQ_FP64, and the first phase of
+       SMPQ_MIXED); the four fields above then count FP32 iterations only */
+    double dslash_hi_ms;
+    long long dslash_hi_launches;
+    double update_hi_ms;
+    long long update_hi_launches;
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,

@@ -138,8 +138,8 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
                     smpq_stats *stats, bool full) {
     cudaStream_t st = ctx->stream;
     ctx->launches = 0;
-    ctx->prof_a_ms = ctx->prof_b_ms = 0;
-    ctx->prof_a_n = ctx->prof_b_n = 0;
+    ctx->prof_a_ms = ctx->prof_b_ms = ctx->prof_a_hi_ms = ctx->prof_b_hi_ms = 0;
+    ctx->prof_a_n = ctx->prof_b_n = ctx->prof_a_hi_n = ctx->prof_b_hi_n = 0;
     cudaEventRecord(ctx->evA, st);
     int rc;
     // star support of every class
@@ -280,6 +280,10 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->dslash_launches = ctx->prof_a_n;
         stats->update_ms = ctx->prof_b_ms;
         stats->update_launches = ctx->prof_b_n;
+        stats->dslash_hi_ms = ctx->prof_a_hi_ms;
+        stats->dslash_hi_launches = ctx->prof_a_hi_n;
+        stats->update_hi_ms = ctx->prof_b_hi_ms;
+        stats->update_hi_launches = ctx->prof_b_hi_n;
     }
     ctx->last_Q = tot[0];
     return SMPQ_OK;

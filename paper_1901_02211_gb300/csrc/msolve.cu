@@ -684,7 +684,7 @@ template <int BC> struct Solve {
         if (hflags) cudaFreeHost(hflags);
     }
 
-    void collect(int n) {
+    void collect(int n, bool hi) {
         if (!prof) return;
         for (int k = 0; k < n; ++k) {
             float a = 0, b = 0;
@@ -693,11 +693,11 @@ template <int BC> struct Solve {
                 cudaGetLastError();
                 a = b = 0;
             }
-            ctx->prof_a_ms += a;
-            ctx->prof_b_ms += b;
+            (hi ? ctx->prof_a_hi_ms : ctx->prof_a_ms) += a;
+            (hi ? ctx->prof_b_hi_ms : ctx->prof_b_ms) += b;
         }
-        ctx->prof_a_n += n;
-        ctx->prof_b_n += n;
+        (hi ? ctx->prof_a_hi_n : ctx->prof_a_n) += n;
+        (hi ? ctx->prof_b_hi_n : ctx->prof_b_n) += n;
     }
 
     // Iterate with vectors of precision T and shifted directions of precision TS.
@@ -722,6 +722,7 @@ template <int BC> struct Solve {
         const C *U = (const C *)Links<T>::get(ctx);
         const bool shifts = spec.n_sup > 0;
         const int per_iter = 5 + (shifts ? 1 : 0);
+        const bool hi = sizeof(T) != sizeof(float); // FP64 or float-float iterations
         if (init) {
             k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
             s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, sqrt(tol2));
@@ -763,7 +764,7 @@ template <int BC> struct Solve {
                 iteration(prof ? k % chk : 0);
                 if (prof && k % chk == chk - 1) {
                     cudaStreamSynchronize(st);
-                    collect(chk);
+                    collect(chk, hi);
                 }
             }
             ctx->launches += (long long)fixed * per_iter;
@@ -794,7 +795,7 @@ template <int BC> struct Solve {
             cudaMemcpyAsync(hflags, sc.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
-            collect(chk);
+            collect(chk, hi);
             if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
             bool done = hflags[0] == 0;
             if (rel && (hflags[1] || done)) {

@@ -153,8 +153,10 @@ struct smpq_ctx {
     // launch accounting and optional per-launch timing of the solver's D_W kernels
     long long launches = 0;
     std::vector<cudaEvent_t> prof_ev; // 4 per iteration of one check interval
-    double prof_a_ms = 0, prof_b_ms = 0;
+    double prof_a_ms = 0, prof_b_ms = 0;         // FP32 iterations
     long long prof_a_n = 0, prof_b_n = 0;
+    double prof_a_hi_ms = 0, prof_b_hi_ms = 0;   // FP64-accurate iterations
+    long long prof_a_hi_n = 0, prof_b_hi_n = 0;
 };
 
 // workspace slots of smpq_ctx::ws

@@ -72,6 +72,10 @@ class smpq_stats(ctypes.Structure):
         ("dslash_launches", ctypes.c_longlong),
         ("update_ms", ctypes.c_double),
         ("update_launches", ctypes.c_longlong),
+        ("dslash_hi_ms", ctypes.c_double),
+        ("dslash_hi_launches", ctypes.c_longlong),
+        ("update_hi_ms", ctypes.c_double),
+        ("update_hi_launches", ctypes.c_longlong),
     ]
 
     def as_dict(self):
