@@ -55,6 +55,18 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
     quick_two_sum(p, e, h, l);
     return df64(h, l);
 }
+// a * b + c with one renormalisation
+__device__ __forceinline__ df64 fma_df(df64 a, df64 b, df64 c) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    float s, t;
+    two_sum(p, c.hi, s, t);
+    t += e + c.lo;
+    float h, l;
+    quick_two_sum(s, t, h, l);
+    return df64(h, l);
+}
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 
@@ -67,10 +79,10 @@ __device__ __forceinline__ df64c cadd(df64c a, df64c b) { return {a.x + b.x, a.y
 __device__ __forceinline__ df64c csub(df64c a, df64c b) { return {a.x - b.x, a.y - b.y}; }
 __device__ __forceinline__ df64c cmul(df64c a, df64c b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 __device__ __forceinline__ df64c cfma(df64c a, df64c b, df64c acc) {
-    return {acc.x + (a.x * b.x - a.y * b.y), acc.y + (a.x * b.y + a.y * b.x)};
+    return {fma_df(a.x, b.x, fma_df(-a.y, b.y, acc.x)), fma_df(a.x, b.y, fma_df(a.y, b.x, acc.y))};
 }
 __device__ __forceinline__ df64c cfmac(df64c a, df64c b, df64c acc) { // acc + conj(a) b
-    return {acc.x + (a.x * b.x + a.y * b.y), acc.y + (a.x * b.y - a.y * b.x)};
+    return {fma_df(a.x, b.x, fma_df(a.y, b.y, acc.x)), fma_df(a.x, b.y, fma_df(-a.y, b.x, acc.y))};
 }
 __device__ __forceinline__ df64c cmuli(df64c a) { return {-a.y, a.x}; }
 __device__ __forceinline__ df64c cneg(df64c a) { return {-a.x, -a.y}; }

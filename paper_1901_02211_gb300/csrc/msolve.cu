@@ -40,7 +40,10 @@ constexpr int TPB = 4;
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
-template <> struct MinBlocks<df64> { static constexpr int value = 1; };
+#ifndef SMPQ_DF64_MIN_BLOCKS
+#define SMPQ_DF64_MIN_BLOCKS 1
+#endif
+template <> struct MinBlocks<df64> { static constexpr int value = SMPQ_DF64_MIN_BLOCKS; };
 
 // link copy matching the iteration precision
 template <typename T> struct Links;

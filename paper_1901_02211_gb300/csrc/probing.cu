@@ -133,9 +133,9 @@ __global__ void contract_kernel(Geom g, const double2 *__restrict__ U, const dou
 #define SMPQ_HOP(MU)                                                                                                   \
     {                                                                                                                  \
         neighbour(g, x, MU, +1, &f);                                                                                   \
-        hop_one<double, MU, -1, false, BC>(U, yb, n_sup, g.V, k0 + 1 + 2 * MU, x, (double)f, acc);                     \
+        hop_one<double, MU, -1, false, BC>(U, yb, n_sup, g.V, k0 + 1 + 2 * MU, x, f < 0, acc);                        \
         int xb = neighbour(g, x, MU, -1, &f);                                                                          \
-        hop_one<double, MU, +1, true, BC>(U, yb, n_sup, g.V, k0 + 2 + 2 * MU, xb, (double)f, acc);                     \
+        hop_one<double, MU, +1, true, BC>(U, yb, n_sup, g.V, k0 + 2 + 2 * MU, xb, f < 0, acc);                        \
     }
     SMPQ_HOP(0)
     SMPQ_HOP(1)

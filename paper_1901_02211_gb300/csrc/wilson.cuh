@@ -55,13 +55,14 @@ template <> struct Cols<float2, 2> {
 };
 
 // One hop: acc += (1 + SG g_mu) W psi(nb) * f for NR columns, with W = U
-// (BACK = false) or U^dag (BACK = true) read from link site ls.
+// (BACK = false) or U^dag (BACK = true) read from link site ls; the boundary
+// factor f is +1 or -1 and enters as a sign (flip = f < 0).
 // `in` points at the tile (plus first column): site nb starts at nb * 12 * BC;
 // links U[(MU * Vl + ls) * 9 + e].  (Vf, the field site count, is not needed.)
 template <typename T, int MU, int SG, bool BACK, int BC, int NR = 1>
 __device__ __forceinline__ void hop_one(const typename cplx_t<T>::type *__restrict__ U,
                                         const typename cplx_t<T>::type *__restrict__ in, int Vf, int Vl, int nb,
-                                        int ls, T f, typename cplx_t<T>::type acc[12][NR]) {
+                                        int ls, bool flip, typename cplx_t<T>::type acc[12][NR]) {
     typedef typename cplx_t<T>::type C;
     const C *q = in + (size_t)nb * (12 * BC); // the 12 components of a site are BC apart
     // project colour by colour: only the 4 spin components of one colour are live
@@ -81,33 +82,35 @@ __device__ __forceinline__ void hop_one(const typename cplx_t<T>::type *__restri
             else { h[0][a][r] = csub(p0[r], s0); h[1][a][r] = csub(p1[r], s1); }
         }
     }
-    C u[9];
+    // colour multiply and reconstruct one colour row at a time: only one row
+    // (or column, for U^dag) of the link is live
     const C *ul = U + ((size_t)MU * Vl + ls) * 9; // the 9 elements of a link are contiguous
 #pragma unroll
-    for (int e = 0; e < 9; ++e) u[e] = ul[e];
+    for (int a = 0; a < 3; ++a) {
+        C ur[3];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        // colour multiply
-        C w[2][3];
+        for (int b = 0; b < 3; ++b) ur[b] = BACK ? ul[b * 3 + a] : ul[a * 3 + b];
 #pragma unroll
-        for (int sp = 0; sp < 2; ++sp)
+        for (int r = 0; r < NR; ++r) {
+            C w0 = mkc<C>(0, 0), w1 = mkc<C>(0, 0);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                C t = mkc<C>(0, 0);
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    if (BACK) t = cfmac(u[b * 3 + a], h[sp][b][r], t);
-                    else t = cfma(u[a * 3 + b], h[sp][b][r], t);
+            for (int b = 0; b < 3; ++b) {
+                if (BACK) {
+                    w0 = cfmac(ur[b], h[0][b][r], w0);
+                    w1 = cfmac(ur[b], h[1][b][r], w1);
+                } else {
+                    w0 = cfma(ur[b], h[0][b][r], w0);
+                    w1 = cfma(ur[b], h[1][b][r], w1);
                 }
-                w[sp][a] = cscale(f, t);
             }
-        // reconstruct
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            acc[a][r] = cadd(acc[a][r], w[0][a]);
-            acc[3 + a][r] = cadd(acc[3 + a][r], w[1][a]);
+            if (flip) {
+                w0 = cneg(w0);
+                w1 = cneg(w1);
+            }
+            acc[a][r] = cadd(acc[a][r], w0);
+            acc[3 + a][r] = cadd(acc[3 + a][r], w1);
             C l0, l1;
-            sdag_apply<MU>(w[0][a], w[1][a], l0, l1);
+            sdag_apply<MU>(w0, w1, l0, l1);
             if (SG > 0) { acc[6 + a][r] = cadd(acc[6 + a][r], l0); acc[9 + a][r] = cadd(acc[9 + a][r], l1); }
             else { acc[6 + a][r] = csub(acc[6 + a][r], l0); acc[9 + a][r] = csub(acc[9 + a][r], l1); }
         }
@@ -146,8 +149,8 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const SiteCoords &xc,
     const bool top = c == n - 1, bot = c == 0;
     const int nf = top ? s - (n - 1) * st : s + st;
     const int nbk = bot ? s + (n - 1) * st : s - st;
-    const T ff = top ? (T)g.bcf[MU] : (T)1;
-    const T fb = bot ? (T)g.bcf[MU] : (T)1;
+    const bool ff = top && g.bcf[MU] < 0;
+    const bool fb = bot && g.bcf[MU] < 0;
     // forward: (1 - g) U(x) psi(x+mu)   [DAG: (1 + g)]
     hop_one<T, MU, DAG ? +1 : -1, false, BC, NR>(U, in, g.V, g.V, nf, s, ff, acc);
     SMPQ_HOP_BARRIER();
