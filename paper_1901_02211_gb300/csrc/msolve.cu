@@ -36,12 +36,12 @@ constexpr int TPB = 4;
 // minimum resident blocks per SM requested from the register allocator for
 // the FP32 lattice kernels (240-thread blocks: 2 -> <= 136 registers, 3 -> <= 91)
 #ifndef SMPQ_FP32_MIN_BLOCKS
-#define SMPQ_FP32_MIN_BLOCKS 2
+#define SMPQ_FP32_MIN_BLOCKS 3
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = SMPQ_FP32_MIN_BLOCKS; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
 #ifndef SMPQ_DF64_MIN_BLOCKS
-#define SMPQ_DF64_MIN_BLOCKS 1
+#define SMPQ_DF64_MIN_BLOCKS 2
 #endif
 template <> struct MinBlocks<df64> { static constexpr int value = SMPQ_DF64_MIN_BLOCKS; };
 
@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(SCAL_THREADS)
 // columns per thread of the D_W kernels: two FP32 columns share one 16-byte
 // access and one link fetch
 #ifndef SMPQ_FP32_NR
-#define SMPQ_FP32_NR 2
+#define SMPQ_FP32_NR 1
 #endif
 template <typename T, int BC> struct NRSel {
     static constexpr int value = (sizeof(T) == 4 && BC % SMPQ_FP32_NR == 0) ? SMPQ_FP32_NR : 1;
