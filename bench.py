@@ -139,6 +139,30 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def config_for_rank(rank, name=CONFIG):
+    """The configuration a rank evaluates: rank 0 the named one, rank k > 0 an
+    independent configuration of the same shape and recipe with other seeds
+    (independent problems: no data-path collective between ranks)."""
+    from synth import CONFIGS, make_config
+    if rank == 0:
+        return make_config(name)
+    p = dict(CONFIGS[name])
+    p["seed_noise"] += 100 * rank
+    p["seed_gauge"] += 100 * rank
+    CONFIGS["%s_r%d" % (name, rank)] = p
+    return make_config("%s_r%d" % (name, rank))
+
+
+def max_over_ranks(value, device="cpu"):
+    """Max of a per-rank float over the process group (the timing rule)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -197,7 +221,6 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_1901_02211_gb300 import Session, smpq
-    from synth import CONFIGS, make_config
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -206,14 +229,7 @@ def run_gpu(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream().cuda_stream
 
-    name = CONFIG
-    cfg = make_config(name)
-    if rank > 0:  # an independent configuration per rank (same shape and recipe, other seeds)
-        p = dict(CONFIGS[name])
-        p["seed_noise"] += 100 * rank
-        p["seed_gauge"] += 100 * rank
-        CONFIGS[name + "_r%d" % rank] = p
-        cfg = make_config(name + "_r%d" % rank)
+    cfg = config_for_rank(rank)
     U, dims = cfg["U"], cfg["dims"]
     V = int(np.prod(dims))
     a, b = _spectrum(CONFIG)
@@ -254,10 +270,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     value = ws * V_step / (ms / 1000.0)
     clocks = clk.summary()
 

@@ -165,7 +165,7 @@ def test_unit_links_give_zero(S):
 
 
 @pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed1e-2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed1e-2", "mixed3e-2"])
 def test_qx_8x16_sampled(S, r, classes, prec):
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
