@@ -191,6 +191,14 @@ int smpq_compute_qx(smpq_ctx *ctx, double *q_re, double *q_im, int on_device, do
 int smpq_compute_qx_classes(smpq_ctx *ctx, const int *classes, int n, double *q_re, double *q_im, int on_device,
                             smpq_stats *stats);
 
+/* SMP estimate of the diagonal of D_W^{-1} and of Tr D_W^{-1} (the paper's
+ * closing remark, Sec. 4: the same sources applied to the ultra-local Wilson
+ * operator): t(x) = sum_{alpha,a} <psi(x,alpha,a)| D_W^{-1} |phi_P(S(x),alpha,a)>,
+ * *T = sum_x Re t(x).  D_W^{-1} b = (D_W^dag D_W)^{-1} D_W^dag b by CG in the
+ * context's precision.  Needs a gauge field and a colouring scheme (no
+ * spectrum).  t_re, t_im: double[V], host or device. */
+int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, double *T, smpq_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,3 +102,41 @@ def dense_smp_qx(M, colour):
     diag12 = np.einsum("xiyi->xy", Mr)
     same = colour[:, None] == colour[None, :]
     return 0.5 * np.sum(np.where(same, diag12, 0.0), axis=1)
+
+
+# ----------------------------------------------------------------------------- trace of D_W^{-1} (Sec. 4 outlook)
+
+
+def smp_trace_dwinv(U, dims, kappa, colour, n_colours, tol=1e-13, bc=(1, 1, 1, 1), colours=None, batch_colours=8,
+                    max_iter=100000):
+    """SMP estimate t(x) = sum_{alpha,a} <psi(x,alpha,a)| D_W^{-1} |phi_P(S(x),alpha,a)>.
+
+    D_W^{-1} b is computed as (D_W^dag D_W)^{-1} D_W^dag b (CG on the normal
+    equations; D_W^dag = gamma_5 D_W gamma_5).  Returns (t[V] complex, stats).
+    """
+    V = int(np.prod(dims))
+    if colours is None:
+        colours = range(n_colours)
+    colours = list(colours)
+    out = np.zeros(V, dtype=np.complex128)
+    iters = []
+    for start in range(0, len(colours), batch_colours):
+        cls = colours[start:start + batch_colours]
+        b = probing.smp_sources(colour, cls)
+        bd = dirac.apply_g5(native.apply_dw(U, dirac.apply_g5(b), dims, kappa, bc))
+        xs, k, res = native.multishift_cg(U, dims, kappa, bd, [0.0], tol, bc, max_iter)
+        iters.append(k)
+        x = xs[0]
+        for j, cl in enumerate(cls):
+            sites = np.nonzero(colour == cl)[0]
+            acc = np.zeros(len(sites), dtype=np.complex128)
+            for alpha in range(4):
+                for a in range(3):
+                    acc += x[sites, alpha, a, 12 * j + 3 * alpha + a]
+            out[sites] = acc
+    return out, dict(iterations=iters)
+
+
+def dense_smp_trace(Minv, colour):
+    """t^SMP(x) = sum_{y in S(x)} sum_{alpha,a} Minv[(x,alpha,a), (y,alpha,a)]."""
+    return 2.0 * dense_smp_qx(Minv, colour)

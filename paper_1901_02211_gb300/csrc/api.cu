@@ -134,8 +134,9 @@ size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
     return full + sup;
 }
 
+// kind 0: q^SMP(x) of Eq. 16; kind 1: SMP estimate of diag D_W^{-1}
 int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re, double *q_im, int on_device,
-                    smpq_stats *stats, bool full) {
+                    smpq_stats *stats, bool full, int kind = 0) {
     cudaStream_t st = ctx->stream;
     ctx->launches = 0;
     ctx->prof_a_ms = ctx->prof_b_ms = ctx->prof_a_hi_ms = ctx->prof_b_hi_ms = 0;
@@ -186,6 +187,18 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     spec.d_src_class = d_src_class;
     spec.d_src_comp = d_src_comp;
     spec.d_src_field = nullptr;
+    spec.shifts = nullptr;
+    ShiftParams cg; // kind 1: one unshifted system D_W^dag D_W x = D_W^dag b, y = x
+    if (kind == 1) {
+        cg.n = 1;
+        cg.s0 = 0;
+        cg.sig[0] = 0;
+        cg.c[0] = 1;
+        spec.shifts = &cg;
+        const size_t nf = (size_t)ctx->V * 12 * B;
+        if ((rc = ensure(ctx, ctx->ws[W_SRC], 2 * nf * sizeof(double2)))) return rc;
+        spec.d_src_field = (const double *)((double2 *)ctx->ws[W_SRC].p + nf);
+    }
 
     int maxit = 0, nrel = 0, nb = 0;
     long long totit = 0;
@@ -199,14 +212,25 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
             h_rhs[2 * B + j] = cl;
         }
         cudaMemcpyAsync(d_rhs_class, h_rhs.data(), 3 * (size_t)B * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (kind == 1) { // source D_W^dag b of the normal equations
+            double2 *b = (double2 *)ctx->ws[W_SRC].p;
+            launch_class_source(ctx->V, B, BC, spec.d_colour, d_rhs_class, d_src_comp, b, st);
+            launch_dslash<double>(ctx->geom, ctx->U64.p, b, (void *)spec.d_src_field, B, BC, 1, ctx->opt.kappa, st);
+            ctx->launches += 2;
+        }
         SolveOut out;
         rc = multishift_solve(ctx, spec, &out);
         if (rc) return rc;
-        launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y, st);
+        if (kind == 0) {
+            launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y, st);
+            launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class, d_src_comp,
+                            (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa,
+                            (double2 *)ctx->ws[W_QTERM].p, st);
+        } else {
+            launch_trace_terms(out.y, n_sup, B, BC, d_rhs_class, d_src_comp, ctx->members,
+                               (double2 *)ctx->ws[W_QTERM].p, st);
+        }
         ctx->launches += 2;
-        launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class, d_src_comp,
-                        (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa, (double2 *)ctx->ws[W_QTERM].p,
-                        st);
         maxit = std::max(maxit, out.iterations);
         totit += out.iterations;
         nrel += out.reliable_updates;
@@ -226,7 +250,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         dq_im = dq_re + ctx->V;
     }
     launch_qsum((const double2 *)ctx->ws[W_QTERM].p, d_classes, nc, (const int *)ctx->d_members.p, ctx->members,
-                dq_re, dq_im, st);
+                dq_re, dq_im, kind == 0 ? 0.5 : 1.0, st);
     // Q in site order over the processed sites
     std::vector<int> sites;
     if (!full) {
@@ -604,6 +628,19 @@ int smpq_compute_qx(smpq_ctx *ctx, double *q_re, double *q_im, int on_device, do
     for (int c = 0; c < ctx->n_classes; ++c) cls[c] = c;
     rc = compute_classes(ctx, cls, q_re, q_im, on_device, stats, true);
     if (!rc && Q) *Q = ctx->last_Q;
+    return rc;
+}
+
+int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, double *T, smpq_stats *stats) {
+    int rc = check_ctx(ctx, true, false, true);
+    if (rc) return rc;
+    if (!t_re || !t_im) return set_err(ctx, SMPQ_EINVAL, "null output");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    std::vector<int> cls(ctx->n_classes);
+    for (int c = 0; c < ctx->n_classes; ++c) cls[c] = c;
+    rc = compute_classes(ctx, cls, t_re, t_im, on_device, stats, true, 1);
+    if (!rc && T) *T = ctx->last_Q;
     return rc;
 }
 

@@ -949,7 +949,7 @@ ShiftParams make_shifts(const smpq_ctx *ctx) {
 
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out) {
     if (spec.B % spec.BC) return set_err(ctx, SMPQ_EINVAL, "rhs count must be a multiple of the tile width");
-    ShiftParams sp = make_shifts(ctx);
+    ShiftParams sp = spec.shifts ? *spec.shifts : make_shifts(ctx);
     return dispatch_bc(ctx, spec, sp, ctx->opt.tol, ctx->opt.max_iter, out, nullptr, 0, 0);
 }
 

@@ -164,10 +164,10 @@ void launch_contract(const Geom &g, const double *U64, const double2 *y, int n_s
     }
 }
 
-// q(x_m) = 1/2 sum_{comp = 0..11} qterm  (fixed order)
+// q(x_m) = scale * sum_{comp = 0..11} qterm  (fixed order; scale 1/2 for Eq. 16)
 __global__ void qsum_kernel(const double2 *__restrict__ qterm, const int *__restrict__ classes, int nc,
                             const int *__restrict__ members, int nmem, double *__restrict__ q_re,
-                            double *__restrict__ q_im) {
+                            double *__restrict__ q_im, double scale) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= (long)nc * nmem) return;
     int cl = classes[i / nmem], m = (int)(i % nmem);
@@ -178,14 +178,59 @@ __global__ void qsum_kernel(const double2 *__restrict__ qterm, const int *__rest
         im += v.y;
     }
     int x = members[(size_t)cl * nmem + m];
-    q_re[x] = 0.5 * re;
-    q_im[x] = 0.5 * im;
+    q_re[x] = scale * re;
+    q_im[x] = scale * im;
 }
 
 void launch_qsum(const double2 *qterm, const int *d_classes, int nc, const int *d_members, int members, double *q_re,
-                 double *q_im, cudaStream_t st) {
+                 double *q_im, double scale, cudaStream_t st) {
     long n = (long)nc * members;
-    qsum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(qterm, d_classes, nc, d_members, members, q_re, q_im);
+    qsum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(qterm, d_classes, nc, d_members, members, q_re, q_im,
+                                                             scale);
+}
+
+// ---------------------------------------------------------------- SMP trace of D_W^{-1} (Sec. 4 outlook)
+__global__ void class_source_kernel(int V, int B, int BC, const int *__restrict__ colour,
+                                    const int *__restrict__ rhs_class, const int *__restrict__ src_comp,
+                                    double2 *__restrict__ b) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * 12 * B) return;
+    int jj = (int)(i % BC);
+    long r = i / BC;
+    int c = (int)(r % 12);
+    r /= 12;
+    int s = (int)(r % V);
+    int chunk = (int)(r / V);
+    int j = chunk * BC + jj;
+    int cl = rhs_class[j];
+    b[i] = make_double2((cl >= 0 && colour[s] == cl && c == src_comp[j]) ? 1.0 : 0.0, 0.0);
+}
+
+void launch_class_source(int V, int B, int BC, const int *d_colour, const int *d_rhs_class, const int *d_src_comp,
+                         double2 *b, cudaStream_t st) {
+    long n = (long)V * 12 * B;
+    class_source_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, B, BC, d_colour, d_rhs_class, d_src_comp, b);
+}
+
+__global__ void trace_terms_kernel(const double2 *__restrict__ y, int n_sup, int B, int BC,
+                                   const int *__restrict__ rhs_class, const int *__restrict__ src_comp, int nmem,
+                                   double2 *__restrict__ qterm) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)nmem * B) return;
+    int j = (int)(i % B), m = (int)(i / B);
+    int cl = rhs_class[j];
+    if (cl < 0) return;
+    int c = src_comp[j];
+    // star entry 9 m is the member site itself
+    double2 v = y[(((size_t)(j / BC) * n_sup + 9 * (size_t)m) * 12 + c) * BC + (j % BC)];
+    qterm[((size_t)cl * 12 + c) * nmem + m] = v;
+}
+
+void launch_trace_terms(const double2 *y, int n_sup, int B, int BC, const int *d_rhs_class, const int *d_src_comp,
+                        int members, double2 *qterm, cudaStream_t st) {
+    long n = (long)members * B;
+    trace_terms_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, n_sup, B, BC, d_rhs_class, d_src_comp, members,
+                                                                    qterm);
 }
 
 // one block: out[0] = sum q_re (fixed order), out[1] = max |q_im|

@@ -202,7 +202,8 @@ struct SolveSpec {
     const int *d_colour;       // [V] class of each site (source definition)
     const int *d_src_class;    // [B] colour class whose sites carry rhs j's source (-1: none)
     const int *d_src_comp;     // [B] source component (spin*3 + colour) of rhs j
-    const double *d_src_field; // optional explicit FP64 source, ABI layout [V][12][B] (apply_dov)
+    const double *d_src_field; // optional explicit FP64 source in the solver's tiled layout
+    const ShiftParams *shifts; // nullable: shifts and coefficients other than the context's rational
 };
 struct SolveOut {
     // y = R(H^2) b on the support, FP64, layout [(j/BC)*12 + c][n_sup][BC]
@@ -228,6 +229,12 @@ void launch_contract(const Geom &g, const double *U64, const double2 *y, int n_s
                      double2 *qterm, cudaStream_t st);
 // q(x_m) = 1/2 sum_comp qterm for the listed classes
 void launch_qsum(const double2 *qterm, const int *d_classes, int nc, const int *d_members, int members, double *q_re,
-                 double *q_im, cudaStream_t st);
+                 double *q_im, double scale, cudaStream_t st);
+// tiled FP64 class sources: b_j(s, c) = 1 if colour[s] == rhs_class[j] and c == src_comp[j]
+void launch_class_source(int V, int B, int BC, const int *d_colour, const int *d_rhs_class, const int *d_src_comp,
+                         double2 *b, cudaStream_t st);
+// qterm[(class * 12 + comp) * members + m] = y_j(member m)[comp] (diagonal of the solution, no gamma_5)
+void launch_trace_terms(const double2 *y, int n_sup, int B, int BC, const int *d_rhs_class, const int *d_src_comp,
+                        int members, double2 *qterm, cudaStream_t st);
 // out[0] = sum of q_re over the listed sites (all when d_sites == nullptr), out[1] = max |q_im|
 void launch_qtotal(const double *q_re, const double *q_im, const int *d_sites, int n, double *out2, cudaStream_t st);

@@ -96,3 +96,10 @@ class Session:
             import torch
             return torch.complex(q_re, q_im), Q, st
         return q_re + 1j * q_im, Q, st
+
+    def trace_dwinv(self):
+        """SMP estimate of diag D_W^{-1}: (t complex[V], Tr, stats)."""
+        t_re = np.zeros(self.V)
+        t_im = np.zeros(self.V)
+        T, st = S.smpq_trace_dwinv(self.ctx, t_re, t_im)
+        return t_re + 1j * t_im, T, st

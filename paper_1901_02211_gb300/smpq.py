@@ -86,7 +86,7 @@ EXPORTS = [
     "smpq_options_default", "smpq_create", "smpq_destroy", "smpq_last_error", "smpq_set_options",
     "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
-    "smpq_compute_qx_classes", "smpq_dslash_noalloc",
+    "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv",
 ]
 
 _lib = None
@@ -125,6 +125,7 @@ def load(build_if_missing=True):
         "smpq_apply_dov": [P, P, P, I, I],
         "smpq_compute_qx": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
         "smpq_compute_qx_classes": [P, PI, I, P, P, I, ctypes.POINTER(smpq_stats)],
+        "smpq_trace_dwinv": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -275,3 +276,14 @@ def smpq_compute_qx_classes(ctx, classes, q_re, q_im):
     _check(load().smpq_compute_qx_classes(ctx, cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cl.size, pr, pm, dr,
                                           ctypes.byref(st)), ctx)
     return st.as_dict()
+
+
+def smpq_trace_dwinv(ctx, t_re, t_im):
+    pr, dr = _ptr(t_re)
+    pm, dm = _ptr(t_im)
+    if dr != dm:
+        raise ValueError("t_re and t_im must both be host or both be device buffers")
+    T = ctypes.c_double()
+    st = smpq_stats()
+    _check(load().smpq_trace_dwinv(ctx, pr, pm, dr, ctypes.byref(T), ctypes.byref(st)), ctx)
+    return T.value, st.as_dict()

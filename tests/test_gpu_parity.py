@@ -230,3 +230,63 @@ def test_error_codes(S, flux4):
         with pytest.raises(smpq.SmpqError) as e:
             s.compute_qx()
         assert e.value.code == smpq.SMPQ_ENOCONV
+
+
+# ----------------------------------------------------------------------------- the bench's own launch configuration
+
+
+def test_bench_configuration_sampled(S):
+    """All 256 classes of r_min = 4 on 8^3 x 16 in one batch (3072 sources, the
+    tile width and precision bench.py times), sampled sites against the oracle."""
+    cfg = make_config("flux8x16")
+    U, dims = cfg["U"], cfg["dims"]
+    a, b = _interval("flux8x16")
+    zolo, delta = _zolo(a, b)
+    colour, n = probing.color_sites(dims, 4, 0)
+    sample = [0, 131, 255]
+    ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=sample, batch_colours=len(sample))
+    with _session(S, precision=S.SMPQ_MIXED) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(a, b)
+        s.build_sources(4, 0)
+        q, Q, st = s.compute_qx()
+    assert st["n_rhs"] == 3072 and st["n_batches"] == 1
+    mask = np.isin(colour, sample)
+    err = np.abs(q[mask] - ref[mask]).max()
+    print("bench configuration: max |dq| over %d sampled sites = %.3e, Q = %.9f" % (mask.sum(), err, Q))
+    assert err <= 1e-8
+    assert abs(Q - 2.0) < 0.05  # closed-form index k = 2, r_min = 4 probing bias
+
+
+# ----------------------------------------------------------------------------- SMP trace of D_W^{-1}
+
+
+@pytest.mark.parametrize("r,mode", [(2, 0), (4, 0), (2, 1)])
+def test_trace_dwinv_4x4_vs_dense(S, flux4, dense4, r, mode):
+    U, dims = flux4["U"], flux4["dims"]
+    colour, n = probing.color_sites(dims, r, mode)
+    ref = qx.dense_smp_trace(np.linalg.inv(dense4["Dw"]), colour)
+    with _session(S) as s:
+        s.load_gauge(dims, U)
+        s.build_sources(r, mode)
+        t, T, st = s.trace_dwinv()
+    assert np.abs(t - ref).max() <= 1e-8
+    assert abs(T - ref.real.sum()) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_trace_dwinv_8x16_sampled(S, prec):
+    cfg = make_config("flux8x16")
+    U, dims = cfg["U"], cfg["dims"]
+    colour, n = probing.color_sites(dims, 4, 0)
+    sample = [0, 200]
+    ref, _ = qx.smp_trace_dwinv(U, dims, KAPPA, colour, n, colours=sample, batch_colours=2)
+    precision = S.SMPQ_FP64 if prec == "fp64" else S.SMPQ_MIXED
+    with _session(S, precision=precision) as s:
+        s.load_gauge(dims, U)
+        s.build_sources(4, 0)
+        t, T, st = s.trace_dwinv()
+    mask = np.isin(colour, sample)
+    err = np.abs(t[mask] - ref[mask]).max()
+    print("trace D_W^-1 8^3x16 %s: max |dt| = %.3e, Tr = %.6f" % (prec, err, T))
+    assert err <= 1e-8
