@@ -73,6 +73,7 @@ typedef struct {
     int use_graphs;        /* capture those iterations in a CUDA graph */
     int profile;           /* time every D_W / D_W^dag launch of the solver with CUDA events */
     double switch_residual; /* SMPQ_MIXED: relative residual at which FP64 iterations hand over to FP32 */
+    int autotune;           /* time the RHS tile widths (12, 24, 48) on the first solve of each shape */
 } smpq_options;
 
 typedef struct {
@@ -98,11 +99,13 @@ typedef struct {
     long long dslash_hi_launches;
     double update_hi_ms;
     long long update_hi_launches;
+    int rhs_tile;           /* RHS tile width the solves used (autotuned or fixed) */
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
- * 10 iterations per check, graphs on, profiling off, switch_residual 1e-2. */
+ * 10 iterations per check, graphs on, profiling off, switch_residual 1e-2,
+ * autotuning on. */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.
@@ -190,6 +193,15 @@ int smpq_compute_qx(smpq_ctx *ctx, double *q_re, double *q_im, int on_device, do
  * checkpoint/resume).  Sites of other classes are left untouched in q_re/q_im. */
 int smpq_compute_qx_classes(smpq_ctx *ctx, const int *classes, int n, double *q_re, double *q_im, int on_device,
                             smpq_stats *stats);
+
+/* Uneven batch: q^SMP(x) for n lattices of different sizes and schemes, one
+ * context each (distinct contexts, each with its gauge field, spectrum and
+ * colouring loaded).  The n solves are issued concurrently from n host
+ * threads on the contexts' own streams, so their kernels overlap on the GPU.
+ * q_re[i], q_im[i]: double[V_i]; Q and stats (nullable): arrays of n.
+ * Returns the first non-OK status (its message is on that context). */
+int smpq_compute_qx_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_device, double *Q,
+                          smpq_stats *stats);
 
 /* SMP estimate of the diagonal of D_W^{-1} and of Tr D_W^{-1} (the paper's
  * closing remark, Sec. 4: the same sources applied to the ultra-local Wilson

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "smpq_internal.cuh"
@@ -117,12 +118,41 @@ void set_geom(smpq_ctx *ctx) {
     g.V = ctx->V;
 }
 
-int pick_bc(int B) {
+// RHS tile width: measured once per (V, B, precision) on the first solve of
+// that shape (the autotuner), among the widths that divide B; a fixed choice
+// when autotuning is off or B has a single candidate.  The workspace it times
+// on is the solver's own (allocated anyway for the solve).
+int tune_bc(smpq_ctx *ctx, int B, int prec) {
     if (B == 1) return 1;
-    if (B % 48 == 0) return 48;
-    if (B % 24 == 0) return 24;
-    if (B % 12 == 0) return 12;
-    return 1;
+    std::vector<int> cand;
+    for (int bc : {12, 24, 48})
+        if (B % bc == 0) cand.push_back(bc);
+    if (cand.empty()) return 1;
+    if (!ctx->opt.autotune || cand.size() == 1) return cand.back();
+    for (auto &e : ctx->tuned)
+        if (e[0] == ctx->V && e[1] == B && e[2] == prec) return e[3];
+    const size_t nf = (size_t)B * 12 * ctx->V;
+    if (ensure(ctx, ctx->ws[W_P], 3 * nf * sizeof(df64c)) || ensure(ctx, ctx->ws[W_PART], (size_t)2 * nf / 12 * sizeof(double) + 64) ||
+        ensure(ctx, ctx->ws[W_SCAL], (size_t)B * sizeof(double))) {
+        cudaGetLastError();
+        return cand.back();
+    }
+    cudaMemsetAsync(ctx->ws[W_P].p, 0, 3 * nf * sizeof(df64c), ctx->stream);
+    cudaMemsetAsync(ctx->ws[W_SCAL].p, 0, (size_t)B * sizeof(double), ctx->stream);
+    int best = cand.back();
+    float tbest = 1e30f;
+    for (int bc : cand) {
+        float t = time_dslash_pair(ctx, prec, B, bc, 3, ctx->ws[W_P].p, (double *)ctx->ws[W_PART].p,
+                                   (double *)ctx->ws[W_SCAL].p);
+        ctx->launches += 8 * (prec == SMPQ_MIXED ? 2 : 1);
+        if (t > 0 && t < tbest) {
+            tbest = t;
+            best = bc;
+        }
+    }
+    cudaGetLastError();
+    ctx->tuned.push_back({ctx->V, B, prec, best});
+    return best;
 }
 
 // device bytes one right-hand side costs in the solver (full-lattice vectors)
@@ -164,7 +194,8 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     }
     if (B > 1) B -= B % 12;
     if (B < 1) B = 1;
-    const int BC = pick_bc(B);
+    const int BC = tune_bc(ctx, B, prec);
+    ctx->last_bc = BC;
     // qterm + device q
     if ((rc = ensure(ctx, ctx->ws[W_QTERM], (size_t)ctx->n_classes * 12 * ctx->members * sizeof(double2)))) return rc;
     if ((rc = ensure(ctx, ctx->ws[W_RHS], (size_t)3 * B * sizeof(int) + (size_t)nc * sizeof(int) +
@@ -304,6 +335,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->dslash_launches = ctx->prof_a_n;
         stats->update_ms = ctx->prof_b_ms;
         stats->update_launches = ctx->prof_b_n;
+        stats->rhs_tile = ctx->last_bc;
         stats->dslash_hi_ms = ctx->prof_a_hi_ms;
         stats->dslash_hi_launches = ctx->prof_a_hi_n;
         stats->update_hi_ms = ctx->prof_b_hi_ms;
@@ -333,6 +365,7 @@ int smpq_options_default(smpq_options *o) {
     o->use_graphs = 1;
     o->profile = 0;
     o->switch_residual = 1e-2;
+    o->autotune = 1;
     return SMPQ_OK;
 }
 
@@ -629,6 +662,28 @@ int smpq_compute_qx(smpq_ctx *ctx, double *q_re, double *q_im, int on_device, do
     rc = compute_classes(ctx, cls, q_re, q_im, on_device, stats, true);
     if (!rc && Q) *Q = ctx->last_Q;
     return rc;
+}
+
+int smpq_compute_qx_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_device, double *Q,
+                          smpq_stats *stats) {
+    if (!ctxs || n < 1 || !q_re || !q_im) return SMPQ_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !q_re[i] || !q_im[i]) return SMPQ_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return set_err(ctxs[i], SMPQ_EINVAL, "a context appears twice in the batch");
+    }
+    std::vector<int> rc(n, SMPQ_OK);
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int i = 0; i < n; ++i)
+        th.emplace_back([&, i]() {
+            rc[i] = smpq_compute_qx(ctxs[i], q_re[i], q_im[i], on_device, Q ? &Q[i] : nullptr,
+                                    stats ? &stats[i] : nullptr);
+        });
+    for (auto &t : th) t.join();
+    for (int i = 0; i < n; ++i)
+        if (rc[i]) return rc[i];
+    return SMPQ_OK;
 }
 
 int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, double *T, smpq_stats *stats) {

@@ -1015,3 +1015,56 @@ int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi) {
     tridiag_extremes(diag, off, lo, hi);
     return SMPQ_OK;
 }
+
+// ------------------------------------------------------------------ autotuner support
+// Average time (ms) of one t = D_W p plus one r -= alpha (D_W^dag t + s0 p)
+// launch in the iteration precision T, for B right-hand sides in tiles of BC,
+// on scratch fields (their values do not change the work).  reps launches each.
+namespace {
+template <typename T, int BC> float time_pair(smpq_ctx *ctx, int B, int reps, void *buf, double *part, double *alpha) {
+    typedef typename cplx_t<T>::type C;
+    constexpr int NR = NRSel<T, BC>::value;
+    const int V = ctx->V, nchunk = B / BC;
+    const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
+    const int GN = (ntiles_n + TPB - 1) / TPB;
+    const size_t nf = (size_t)B * 12 * V;
+    C *p = (C *)buf, *t = p + nf, *r = t + nf;
+    const C *U = (const C *)Links<T>::get(ctx);
+    const T kappa = (T)ctx->opt.kappa;
+    cudaStream_t st = ctx->stream;
+    const dim3 gridn(GN, nchunk);
+    const int THN = TileMap<BC, NR>::THREADS;
+    auto once = [&]() {
+        k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(ctx->geom, U, p, t, kappa, part, part + (size_t)nchunk * GN * BC,
+                                                     GN);
+        k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(ctx->geom, U, t, p, r, nullptr, alpha, 0.0, kappa, part,
+                                                            GN);
+    };
+    once(); // warm-up
+    cudaEventRecord(ctx->ev1, st);
+    for (int k = 0; k < reps; ++k) once();
+    cudaEventRecord(ctx->ev2, st);
+    cudaEventSynchronize(ctx->ev2);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2);
+    return ms / reps;
+}
+
+template <typename T> float time_pair_bc(smpq_ctx *ctx, int B, int BC, int reps, void *buf, double *part, double *alpha) {
+    switch (BC) {
+    case 12: return time_pair<T, 12>(ctx, B, reps, buf, part, alpha);
+    case 24: return time_pair<T, 24>(ctx, B, reps, buf, part, alpha);
+    case 48: return time_pair<T, 48>(ctx, B, reps, buf, part, alpha);
+    default: return -1.f;
+    }
+}
+} // namespace
+
+float time_dslash_pair(smpq_ctx *ctx, int prec, int B, int BC, int reps, void *buf, double *part, double *alpha) {
+    if (prec == SMPQ_FP64) return time_pair_bc<double>(ctx, B, BC, reps, buf, part, alpha);
+    float t32 = time_pair_bc<float>(ctx, B, BC, reps, buf, part, alpha);
+    if (prec == SMPQ_FP32) return t32;
+    // SMPQ_MIXED: a fifth of the iterations (switch residual 1e-2) in float-float, the rest in FP32
+    float tdf = time_pair_bc<df64>(ctx, B, BC, reps, buf, part, alpha);
+    return 0.25f * tdf + 0.75f * t32;
+}

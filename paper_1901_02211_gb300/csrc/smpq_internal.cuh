@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -152,6 +153,9 @@ struct smpq_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evA = nullptr, evB = nullptr;
     // launch accounting and optional per-launch timing of the solver's D_W kernels
     long long launches = 0;
+    // autotuned RHS tile width per (V, B, precision)
+    std::vector<std::array<int, 4>> tuned; // {V, B, prec, BC}
+    int last_bc = 0;
     std::vector<cudaEvent_t> prof_ev; // 4 per iteration of one check interval
     double prof_a_ms = 0, prof_b_ms = 0;         // FP32 iterations
     long long prof_a_n = 0, prof_b_n = 0;
@@ -215,6 +219,9 @@ struct SolveOut {
 };
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out);
 int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi);
+// autotuner: average ms of one D_W + D_W^dag-update launch pair (scratch fields in buf:
+// 3 fields of B x 12 x V complex of the widest type used, part: partials, alpha: B doubles)
+float time_dslash_pair(smpq_ctx *ctx, int prec, int B, int BC, int reps, void *buf, double *part, double *alpha);
 
 // probing.cu : sources, star support, contraction, Q
 int build_star_support(smpq_ctx *ctx, Buf &supsite, int *n_sup);

@@ -58,13 +58,24 @@ def r_min_of(r, mode):
     return r * math.sqrt(2) if mode == 1 else float(r)
 
 
-def rmin_sweep(dims, U, lmin2, lmax2, Q_exact, schemes=None, precision=smpq.SMPQ_MIXED, device=0, max_rhs=None):
-    """Q_P and |Q_P - Q| for each scheme; returns a list of dicts."""
+def rmin_sweep(dims, U, lmin2, lmax2, Q_exact, schemes=None, precision=smpq.SMPQ_MIXED, device=0, max_rhs=None,
+               exact_qx=False):
+    """Q_P and |Q_P - Q| for each scheme; returns a list of dicts.
+
+    exact_qx: also evaluate the exact q(x) by point sources (the scheme with
+    r = n_mu, needs a hypercubic lattice) and report the root-mean-square
+    per-site probing error of every scheme against it."""
     rows = []
     with Session(device=device, precision=precision) as s:
         s.load_gauge(dims, U)
         s.set_spectrum(lmin2, lmax2)
         V = int(np.prod(dims))
+        q_exact = None
+        if exact_qx:
+            if len(set(dims)) != 1:
+                raise ValueError("point sources through the scheme r = n need a hypercubic lattice")
+            s.build_sources(dims[0], 0)
+            q_exact, _, _ = s.compute_qx()
         for r, mode in (schemes or schemes_for(dims)):
             n = s.build_sources(r, mode)
             if max_rhs and 12 * n > max_rhs:
@@ -72,9 +83,13 @@ def rmin_sweep(dims, U, lmin2, lmax2, Q_exact, schemes=None, precision=smpq.SMPQ
             t0 = time.perf_counter()
             q, Q, st = s.compute_qx()
             dt = time.perf_counter() - t0
-            rows.append(dict(r=r, mode=mode, m=dims[0] // r, r_min=r_min_of(r, mode), N_smp=12 * n,
-                             ratio=12 * n / (12.0 * V), Q_P=Q, err=abs(Q - Q_exact), max_im_q=st["max_im_q"],
-                             iterations=st["max_iterations"], seconds=dt))
+            row = dict(r=r, mode=mode, m=dims[0] // r, r_min=r_min_of(r, mode), N_smp=12 * n,
+                       ratio=12 * n / (12.0 * V), Q_P=Q, err=abs(Q - Q_exact), max_im_q=st["max_im_q"],
+                       iterations=st["max_iterations"], seconds=dt)
+            if q_exact is not None:
+                row["site_rms"] = float(np.sqrt(np.mean(np.abs(q - q_exact) ** 2)))
+                row["Q_pointsource"] = float(q_exact.real.sum())
+            rows.append(row)
     return rows
 
 

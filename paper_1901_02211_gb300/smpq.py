@@ -51,6 +51,7 @@ class smpq_options(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("switch_residual", ctypes.c_double),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -76,6 +77,7 @@ class smpq_stats(ctypes.Structure):
         ("dslash_hi_launches", ctypes.c_longlong),
         ("update_hi_ms", ctypes.c_double),
         ("update_hi_launches", ctypes.c_longlong),
+        ("rhs_tile", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -86,7 +88,7 @@ EXPORTS = [
     "smpq_options_default", "smpq_create", "smpq_destroy", "smpq_last_error", "smpq_set_options",
     "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
-    "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv",
+    "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv", "smpq_compute_qx_batch",
 ]
 
 _lib = None
@@ -126,6 +128,7 @@ def load(build_if_missing=True):
         "smpq_compute_qx": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
         "smpq_compute_qx_classes": [P, PI, I, P, P, I, ctypes.POINTER(smpq_stats)],
         "smpq_trace_dwinv": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
+        "smpq_compute_qx_batch": [P, I, P, P, I, PD, ctypes.POINTER(smpq_stats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -287,3 +290,22 @@ def smpq_trace_dwinv(ctx, t_re, t_im):
     st = smpq_stats()
     _check(load().smpq_trace_dwinv(ctx, pr, pm, dr, ctypes.byref(T), ctypes.byref(st)), ctx)
     return T.value, st.as_dict()
+
+
+def smpq_compute_qx_batch(ctxs, q_re, q_im):
+    """Uneven batch over several contexts; q_re/q_im: lists of per-lattice buffers."""
+    n = len(ctxs)
+    pr = [_ptr(a) for a in q_re]
+    pm = [_ptr(a) for a in q_im]
+    dev = {d for _, d in pr + pm}
+    if len(dev) != 1:
+        raise ValueError("all buffers must be host or all device")
+    C = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    R = (ctypes.c_void_p * n)(*[p for p, _ in pr])
+    M = (ctypes.c_void_p * n)(*[p for p, _ in pm])
+    Q = (ctypes.c_double * n)()
+    st = (smpq_stats * n)()
+    rc = load().smpq_compute_qx_batch(C, n, R, M, dev.pop(), Q, st)
+    if rc != SMPQ_OK:
+        raise SmpqError(rc, "uneven batch failed")
+    return list(Q), [x.as_dict() for x in st]

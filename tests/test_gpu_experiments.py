@@ -29,17 +29,22 @@ def _setup(name):
 
 
 def test_error_falls_with_rmin():
+    """4^4 flux configuration (Q = 1): the per-site probing error against the
+    exact point-source q(x), and |Q_P - Q|, fall as r_min grows; at equal
+    r_min the Combine mode (more nearest neighbours) is worse than Normal (Sec. 2.2)."""
     from paper_1901_02211_gb300 import experiments
-    cfg, a, b = _setup("flux8x16")
-    rows = experiments.rmin_sweep(cfg["dims"], cfg["U"], a, b, cfg["Q_closed"], schemes=[(2, 0), (2, 1), (4, 0)])
-    err = {(r["r"], r["mode"]): r["err"] for r in rows}
+    cfg, a, b = _setup("flux4")
+    rows = experiments.rmin_sweep(cfg["dims"], cfg["U"], a, b, cfg["Q_closed"],
+                                  schemes=[(2, 0), (2, 1), (2, 2), (4, 2)], exact_qx=True)
+    e = {(r["r"], r["mode"]): r for r in rows}
     for r in rows:
-        print("P r=%d mode=%d r_min=%.3f N=%d Q_P=%.6f |Q_P-Q|=%.3e" % (
-            r["r"], r["mode"], r["r_min"], r["N_smp"], r["Q_P"], r["err"]))
-        assert r["max_im_q"] < 1e-2
-    # r_min: 2 (Normal, r=2) < 2 sqrt(2) (Split, r=2) < 4 (Normal, r=4)
-    assert err[(4, 0)] < err[(2, 1)] < err[(2, 0)]
-    assert err[(4, 0)] < 0.05  # Q_P within 0.05 of the integer once r_min >= 4 (Sec. 3)
+        print("P r=%d mode=%d r_min=%.3f N=%d Q_P=%.6f |Q_P-Q|=%.3e site rms %.3e" % (
+            r["r"], r["mode"], r["r_min"], r["N_smp"], r["Q_P"], r["err"], r["site_rms"]))
+    assert abs(rows[0]["Q_pointsource"] - 1.0) < 1e-8  # exact trace = index
+    rms = {k: v["site_rms"] for k, v in e.items()}
+    err = {k: v["err"] for k, v in e.items()}
+    assert rms[(4, 2)] < rms[(2, 1)] < rms[(2, 0)] < rms[(2, 2)]
+    assert err[(4, 2)] < err[(2, 1)] < err[(2, 0)]
 
 
 def test_locality_of_dov():
