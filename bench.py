@@ -237,17 +237,26 @@ def run_gpu(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream().cuda_stream
 
-    cfg = config_for_rank(rank)
+    cfg = config_for_rank(rank, args.config)
     U, dims = cfg["U"], cfg["dims"]
     V = int(np.prod(dims))
-    a, b = _spectrum(CONFIG)
+    spectrum_note = "oracle ARPACK (tests/golden/spectra.json), widened 0.98/1.02"
+    try:
+        a, b = _spectrum(args.config)
+    except KeyError:  # no oracle spectrum for this workload: Lanczos on the GPU (the production setup step)
+        probe = Session(device=dev, stream=stream)
+        probe.load_gauge(dims, U)
+        lo, hi = probe.measure_spectrum(300)
+        probe.close()
+        a, b = 0.98 * lo, 1.02 * hi
+        spectrum_note = "GPU Lanczos (smpq_measure_spectrum, 300 steps), widened 0.98/1.02"
     prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
                 use_graphs=1, profile=1, switch_residual=args.switch)
     s.load_gauge(dims, U)
     s.set_spectrum(a, b)
-    n_classes = s.build_sources(R_MIN, MODE)
+    n_classes = s.build_sources(args.rmin, MODE)
     q_re = torch.zeros(V, dtype=torch.float64, device="cuda")
     q_im = torch.zeros(V, dtype=torch.float64, device="cuda")
 
@@ -330,6 +339,7 @@ def run_gpu(args):
     else:
         e2e_val = _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws)
     out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream) if rank == 0 else {}
+    out["spectrum"] = {"lmin2": a, "lmax2": b, "source": spectrum_note}
     if rank == 0:
         _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak,
                 peak_kind, traffic, stats, out, sub)
@@ -350,12 +360,12 @@ def _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws):
                  use_graphs=1)
     s2.load_gauge(dims, Upin.numpy())
     s2.set_spectrum(a, b)
-    s2.build_sources(R_MIN, MODE)
+    s2.build_sources(args.rmin, MODE)
 
     def e2e_step():
         smpq.smpq_load_gauge(s2.ctx, dims, Upin)
         s2.set_spectrum(a, b)
-        s2.build_sources(R_MIN, MODE)
+        s2.build_sources(args.rmin, MODE)
         return smpq.smpq_compute_qx(s2.ctx, hq_re, hq_im)
 
     e2e_step()
@@ -387,7 +397,7 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
                          iters_per_check=10, use_graphs=1)
             s3.load_gauge(dims, U)
             s3.set_spectrum(a, b)
-            s3.build_sources(R_MIN, MODE)
+            s3.build_sources(args.rmin, MODE)
             s3.compute_qx()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -403,7 +413,7 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
                          iters_per_check=10, use_graphs=1)
             s3.load_gauge(dims, U)
             s3.set_spectrum(a, b)
-            s3.build_sources(R_MIN, MODE)
+            s3.build_sources(args.rmin, MODE)
             cls = sample if blk == 1 else list(range(0, n_classes, 8))
             s3.compute_qx(classes=cls[:1])
             torch.cuda.synchronize()
@@ -423,6 +433,15 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
     return out
 
 
+def _workload_name(args):
+    from synth import CONFIGS
+    p = CONFIGS[args.config]
+    d = p["dims"]
+    n_cls = (args.rmin ** 4)
+    return ("%dx%dx%dx%d flux Q=%d noise %g + gauge transform, SMP r_min=%d mode 0, %d classes x 12 = %d sources "
+            "x 14 shifts, tol 1e-10" % (d[0], d[1], d[2], d[3], p["k"], p["eps"], args.rmin, n_cls, 12 * n_cls))
+
+
 def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak, peak_kind,
             traffic, stats, out, sub):
     from paper_1901_02211_gb300 import smpq
@@ -433,8 +452,7 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {smpq.SMPQ_FP32: "f32", smpq.SMPQ_FP64: "f64", smpq.SMPQ_MIXED: "f64+f32"}[prec],
             "data": "synthetic",
-            "config": {"workload": "8^3x16 flux Q=2 noise 0.1 + gauge transform, SMP r_min=4 mode 0, "
-                                   "256 classes x 12 = 3072 sources x 14 shifts, tol 1e-10",
+            "config": {"workload": _workload_name(args),
                        "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
                                      smpq.SMPQ_FP64: "FP64",
                                      smpq.SMPQ_MIXED: "FP64 until ||r|| < %g ||b||, then FP32; FP64 shifted vectors"
@@ -475,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--switch", type=float, default=1e-2, help="SMPQ_MIXED: FP64 -> FP32 switch residual")
+    ap.add_argument("--config", default=CONFIG, help="synthetic configuration (synth.CONFIGS)")
+    ap.add_argument("--rmin", type=int, default=R_MIN, help="SMP r (Normal mode)")
     ap.add_argument("--classes", type=int, default=0, help="profiling: only the first N colour classes")
     args = ap.parse_args()
     if args.impl == "reference":

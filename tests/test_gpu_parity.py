@@ -319,3 +319,28 @@ def test_uneven_batch_matches_single_runs(S, flux4):
         assert Qs[i] == Q
     for s in sessions:
         s.close()
+
+
+# ----------------------------------------------------------------------------- 16^3 x 32 (sampled)
+
+
+def test_qx_16x32_sampled(S):
+    """16^3 x 32 flux configuration (Q = -1, noise 0.15), r_min = 4, one class
+    against the oracle.  The Zolotarev interval is fixed a priori (parity only
+    needs both sides to use the same rational)."""
+    cfg = make_config("flux16x32")
+    U, dims = cfg["U"], cfg["dims"]
+    a, b = 0.01, 7.5
+    zolo, delta = _zolo(a, b)
+    colour, n = probing.color_sites(dims, 4, 0)
+    sample = [93]
+    ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=sample, batch_colours=1)
+    with _session(S, precision=S.SMPQ_MIXED) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(a, b)
+        s.build_sources(4, 0)
+        q, Q, st = s.compute_qx(classes=sample)
+    mask = np.isin(colour, sample)
+    err = np.abs(q[mask] - ref[mask]).max()
+    print("16^3x32 mixed: max |dq| over %d sites = %.3e, iterations %d" % (mask.sum(), err, st["max_iterations"]))
+    assert err <= 1e-8
