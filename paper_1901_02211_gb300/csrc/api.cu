@@ -186,8 +186,12 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     else {
         size_t freeb = 0, totb = 0;
         cudaMemGetInfo(&freeb, &totb);
+        // the context's own workspace is reusable: count it as available, so
+        // the batch size does not shrink from one call to the next
+        size_t held = 0;
+        for (const Buf &b : ctx->ws) held += b.bytes;
         size_t per = bytes_per_rhs(ctx, prec, n_sup, ctx->opt.npoles);
-        long cap = (long)((0.6 * (double)freeb) / (double)per);
+        long cap = (long)((0.6 * (double)(freeb + held)) / (double)per);
         cap = std::max(12L, cap - cap % 48);
         B = (int)std::min<long>(nrhs_total, cap);
         if (B > 48) B -= B % 48;
