@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
         int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
         C acc[12][NR];
-        wilson_hop<T, false, BC, NR>(g, U, p + base, s, acc);
+        wilson_hop_auto<T, false, BC, NR>(g, U, p + base, s, acc);
         T st[NR], sp[NR]; // per-site sums in the iteration precision, one FP64 add per site
 #pragma unroll
         for (int r = 0; r < NR; ++r) st[r] = sp[r] = 0;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
         int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
         C acc[12][NR];
-        wilson_hop<T, true, BC, NR>(g, U, t + base, s, acc);
+        wilson_hop_auto<T, true, BC, NR>(g, U, t + base, s, acc);
         T sr[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) sr[q] = 0;

@@ -15,6 +15,8 @@
 // and the neighbour index are fetched once for all NR columns, and two FP32
 // columns move as one 16-byte access.
 #pragma once
+#include <type_traits>
+
 #include "smpq_internal.cuh"
 
 // S_mu l  for the lower 2-spinor l = (l0, l1)
@@ -175,6 +177,132 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const typename cplx_t<
     hop_dir<T, 1, DAG, BC, NR>(g, xc, U, in, s, acc);
     hop_dir<T, 2, DAG, BC, NR>(g, xc, U, in, s, acc);
     hop_dir<T, 3, DAG, BC, NR>(g, xc, U, in, s, acc);
+}
+
+// ---------------------------------------------------------------- rolled variant
+// The same hop with the direction mu a runtime value, for the float-float
+// kernels: their fully unrolled 8-hop code overflows the instruction cache
+// (ncu: most stalls "no instruction").  S_mu and S_mu^dag are unit-modulus
+// permutations, applied with selects.
+
+// c * v for c in {1, -1, i, -i}: rot = multiply by i, neg = negate
+template <typename C> __device__ __forceinline__ C unit_mul(C v, bool rot, bool neg) {
+    C r = rot ? cmuli(v) : v;
+    return neg ? cneg(r) : r;
+}
+// S_mu l: mu 0: (-i l1, -i l0); 1: (-l1, l0); 2: (-i l0, i l1); 3: (l0, l1)
+template <typename C> __device__ __forceinline__ void s_apply_rt(int mu, C l0, C l1, C &o0, C &o1) {
+    const bool sw = mu <= 1;
+    C a = sw ? l1 : l0, b = sw ? l0 : l1;
+    o0 = unit_mul(a, mu == 0 || mu == 2, mu <= 2);
+    o1 = unit_mul(b, mu == 0 || mu == 2, mu == 0);
+}
+// S_mu^dag u: mu 0: (i u1, i u0); 1: (u1, -u0); 2: (i u0, -i u1); 3: (u0, u1)
+template <typename C> __device__ __forceinline__ void sdag_apply_rt(int mu, C u0, C u1, C &o0, C &o1) {
+    const bool sw = mu <= 1;
+    C a = sw ? u1 : u0, b = sw ? u0 : u1;
+    o0 = unit_mul(a, mu == 0 || mu == 2, false);
+    o1 = unit_mul(b, mu == 0 || mu == 2, mu == 1 || mu == 2);
+}
+
+template <typename T, int SG, bool BACK, int BC, int NR>
+__device__ __forceinline__ void hop_one_rt(int mu, const typename cplx_t<T>::type *__restrict__ U,
+                                           const typename cplx_t<T>::type *__restrict__ in, int Vl, int nb, int ls,
+                                           bool flip, typename cplx_t<T>::type acc[12][NR]) {
+    typedef typename cplx_t<T>::type C;
+    const C *q = in + (size_t)nb * (12 * BC);
+    C h[2][3][NR];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        C p0[NR], p1[NR], p2[NR], p3[NR];
+        Cols<C, NR>::load(q + a * BC, p0);
+        Cols<C, NR>::load(q + (3 + a) * BC, p1);
+        Cols<C, NR>::load(q + (6 + a) * BC, p2);
+        Cols<C, NR>::load(q + (9 + a) * BC, p3);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            C s0, s1;
+            s_apply_rt(mu, p2[r], p3[r], s0, s1);
+            if (SG > 0) { h[0][a][r] = cadd(p0[r], s0); h[1][a][r] = cadd(p1[r], s1); }
+            else { h[0][a][r] = csub(p0[r], s0); h[1][a][r] = csub(p1[r], s1); }
+        }
+    }
+    const C *ul = U + ((size_t)mu * Vl + ls) * 9;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        C ur[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ur[b] = BACK ? ul[b * 3 + a] : ul[a * 3 + b];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            C w0 = mkc<C>(0, 0), w1 = mkc<C>(0, 0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (BACK) {
+                    w0 = cfmac(ur[b], h[0][b][r], w0);
+                    w1 = cfmac(ur[b], h[1][b][r], w1);
+                } else {
+                    w0 = cfma(ur[b], h[0][b][r], w0);
+                    w1 = cfma(ur[b], h[1][b][r], w1);
+                }
+            }
+            if (flip) {
+                w0 = cneg(w0);
+                w1 = cneg(w1);
+            }
+            acc[a][r] = cadd(acc[a][r], w0);
+            acc[3 + a][r] = cadd(acc[3 + a][r], w1);
+            C l0, l1;
+            sdag_apply_rt(mu, w0, w1, l0, l1);
+            if (SG > 0) { acc[6 + a][r] = cadd(acc[6 + a][r], l0); acc[9 + a][r] = cadd(acc[9 + a][r], l1); }
+            else { acc[6 + a][r] = csub(acc[6 + a][r], l0); acc[9 + a][r] = csub(acc[9 + a][r], l1); }
+        }
+    }
+}
+
+template <typename T, bool DAG, int BC, int NR = 1>
+__device__ __forceinline__ void wilson_hop_rolled(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
+                                                  const typename cplx_t<T>::type *__restrict__ in, int s,
+                                                  typename cplx_t<T>::type acc[12][NR]) {
+    typedef typename cplx_t<T>::type C;
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[c][r] = mkc<C>(0, 0);
+    const SiteCoords xc(g, s);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        const int n = g.n[mu], st = g.stride[mu], c = xc.x[mu];
+        const bool top = c == n - 1, bot = c == 0;
+        const int nf = top ? s - (n - 1) * st : s + st;
+        const int nbk = bot ? s + (n - 1) * st : s - st;
+        const bool ff = top && g.bcf[mu] < 0;
+        const bool fb = bot && g.bcf[mu] < 0;
+        hop_one_rt<T, DAG ? +1 : -1, false, BC, NR>(mu, U, in, g.V, nf, s, ff, acc);
+        hop_one_rt<T, DAG ? -1 : +1, true, BC, NR>(mu, U, in, g.V, nbk, nbk, fb, acc);
+    }
+}
+
+// full (unrolled) hop for FP32/FP64, rolled directions for float-float
+// (SMPQ_DF64_UNROLLED / SMPQ_FP32_ROLLED switch the choice for tuning)
+template <typename T, bool DAG, int BC, int NR = 1>
+__device__ __forceinline__ void wilson_hop_auto(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
+                                                const typename cplx_t<T>::type *__restrict__ in, int s,
+                                                typename cplx_t<T>::type acc[12][NR]) {
+#ifdef SMPQ_DF64_UNROLLED
+    constexpr bool roll_df = false;
+#else
+    constexpr bool roll_df = true;
+#endif
+#ifdef SMPQ_FP32_ROLLED
+    constexpr bool roll_f = true;
+#else
+    constexpr bool roll_f = false;
+#endif
+    if constexpr ((std::is_same<T, df64>::value && roll_df) || (std::is_same<T, float>::value && roll_f))
+        wilson_hop_rolled<T, DAG, BC, NR>(g, U, in, s, acc);
+    else
+        wilson_hop<T, DAG, BC, NR>(g, U, in, s, acc);
 }
 
 // Thread -> (tile, site, column) mapping shared by the lattice kernels:
