@@ -777,10 +777,13 @@ template <int BC> struct Solve {
         // (profiling records CUDA events between launches, so it runs without a graph)
         cudaGraphExec_t gexec = nullptr;
         bool graph_ok = false;
+        // the phase that ends at the switch residual checks every 2 iterations:
+        // its iterations are the expensive ones, and overshoot would waste them
+        const int ck = theta2 > 0 ? std::min(chk, 2) : chk;
         if (ctx->opt.use_graphs && !prof) {
             cudaGraph_t graph;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                for (int k = 0; k < chk; ++k) iteration(k);
+                for (int k = 0; k < ck; ++k) iteration(k);
                 if (cudaStreamEndCapture(st, &graph) == cudaSuccess) {
                     if (cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess) graph_ok = true;
                     cudaGraphDestroy(graph);
@@ -792,13 +795,13 @@ template <int BC> struct Solve {
         for (;;) {
             if (graph_ok) cudaGraphLaunch(gexec, st);
             else
-                for (int k = 0; k < chk; ++k) iteration(k);
-            ctx->launches += (long long)chk * per_iter;
-            iters += chk;
+                for (int k = 0; k < ck; ++k) iteration(k);
+            ctx->launches += (long long)ck * per_iter;
+            iters += ck;
             cudaMemcpyAsync(hflags, sc.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
-            collect(chk, hi);
+            collect(ck, hi);
             if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
             bool done = hflags[0] == 0;
             if (rel && (hflags[1] || done)) {
