@@ -254,7 +254,7 @@ def run_gpu(args):
     prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
-                use_graphs=1, profile=1, switch_residual=args.switch)
+                use_graphs=1, profile=1, switch_residual=args.switch, autotune=0 if args.no_autotune else 1)
     s.load_gauge(dims, U)
     s.set_spectrum(a, b)
     n_classes = s.build_sources(args.rmin, MODE)
@@ -458,7 +458,7 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
                                      smpq.SMPQ_FP64: "FP64",
                                      smpq.SMPQ_MIXED: "FP64 until ||r|| < %g ||b||, then FP32; FP64 shifted vectors"
                                      % args.switch}[prec],
-                       "batch": B, "l2": "inputs larger than L2 (each solver vector %.1f GB)"
+                       "batch": B, "rhs_tile": int(st.get("rhs_tile", 0)), "l2": "inputs larger than L2 (each solver vector %.1f GB)"
                        % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
             "clocks": clocks,
             "e2e": None if e2e_val is None else {
@@ -497,6 +497,8 @@ def main():
     ap.add_argument("--config", default=CONFIG, help="synthetic configuration (synth.CONFIGS)")
     ap.add_argument("--rmin", type=int, default=R_MIN, help="SMP r (Normal mode)")
     ap.add_argument("--classes", type=int, default=0, help="profiling: only the first N colour classes")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="widest RHS tile that divides the batch, without timing the candidates")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
