@@ -42,11 +42,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CONFIG = "flux8x16"
-# algorithmic arithmetic per site and source of one launch (derived in the design doc):
-# float-float D_W: 8 hops x (12 + 24 additions x 11 ops + 72 fused multiply-adds x 15 ops)
-# = 11808, plus the epilogue (1368 for t = D_W p with norms, 1824 for the r update)
-DF64_OPS_A = 11808 + 1368
-DF64_OPS_B = 11808 + 1824
+# algorithmic arithmetic per site and source of one launch, in FP32 operations:
+# float-float D_W = 8 hops x (36 additions x 11 ops + 12 real parts of three-term
+# complex dot products x 70 ops) = 9888, plus the epilogue (1368 for t = D_W p
+# with norms, 1824 for the r update)
+DF64_OPS_A = 9888 + 1368
+DF64_OPS_B = 9888 + 1824
 # FP64 D_W: 1320 flop hopping + 24 (kappa scale) + 24 (norm) / + 72 (update and norm)
 FP64_FLOP_A = 1320 + 48
 FP64_FLOP_B = 1320 + 96
@@ -315,7 +316,7 @@ def run_gpu(args):
     # ones by arithmetic -- float-float runs on the FP32 pipes (152 SMs x 128
     # lanes x clock, one lane-operation per FP32 instruction), native FP64 on
     # the FP64 units (1.25 TFLOP/s nominal).  Algorithmic operation counts per
-    # site and source are derived from the kernels' arithmetic.
+    # site and source are the DF64_OPS_* and FP64_FLOP_* constants above.
     for key, k in kern.items():
         if "fp32" in key:
             k.update(bound="hbm", unit="GB/s", peak=peak_hbm, peak_source=peak_kind,

@@ -84,6 +84,43 @@ __device__ __forceinline__ df64c cfma(df64c a, df64c b, df64c acc) {
 __device__ __forceinline__ df64c cfmac(df64c a, df64c b, df64c acc) { // acc + conj(a) b
     return {fma_df(a.x, b.x, fma_df(a.y, b.y, acc.x)), fma_df(a.x, b.y, fma_df(-a.y, b.x, acc.y))};
 }
+// sum_b a[b] * v[b] over three complex terms with one renormalisation per
+// component: the high parts of the six real products of each component are
+// summed with two-sum, their exact errors (and the low-part cross terms) in a
+// single FP32 accumulator; 70 FP32 operations per component against 90 for a
+// chain of fma_df.
+__device__ __forceinline__ void ff_prod(float ah, float al, float bh, float bl, float &p, float &q) {
+    p = ah * bh;
+    q = fmaf(ah, bh, -p);
+    q = fmaf(ah, bl, fmaf(al, bh, q));
+}
+__device__ __forceinline__ void ff_acc(float &s, float &e, float ah, float al, float bh, float bl) {
+    float p, q, t, u;
+    ff_prod(ah, al, bh, bl, p, q);
+    two_sum(s, p, t, u);
+    s = t;
+    e += q + u;
+}
+__device__ __forceinline__ df64 ff_finish(float s, float e) {
+    float h, l;
+    two_sum(s, e, h, l);
+    return df64(h, l);
+}
+__device__ __forceinline__ df64c cdot3(const df64c a[3], const df64c v[3]) {
+    float sr, er, si, ei;
+    ff_prod(a[0].x.hi, a[0].x.lo, v[0].x.hi, v[0].x.lo, sr, er);
+    ff_acc(sr, er, -a[0].y.hi, -a[0].y.lo, v[0].y.hi, v[0].y.lo);
+    ff_prod(a[0].x.hi, a[0].x.lo, v[0].y.hi, v[0].y.lo, si, ei);
+    ff_acc(si, ei, a[0].y.hi, a[0].y.lo, v[0].x.hi, v[0].x.lo);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+        ff_acc(sr, er, a[b].x.hi, a[b].x.lo, v[b].x.hi, v[b].x.lo);
+        ff_acc(sr, er, -a[b].y.hi, -a[b].y.lo, v[b].y.hi, v[b].y.lo);
+        ff_acc(si, ei, a[b].x.hi, a[b].x.lo, v[b].y.hi, v[b].y.lo);
+        ff_acc(si, ei, a[b].y.hi, a[b].y.lo, v[b].x.hi, v[b].x.lo);
+    }
+    return {ff_finish(sr, er), ff_finish(si, ei)};
+}
 __device__ __forceinline__ df64c cmuli(df64c a) { return {-a.y, a.x}; }
 __device__ __forceinline__ df64c cneg(df64c a) { return {-a.x, -a.y}; }
 __device__ __forceinline__ df64c cscale(df64 s, df64c a) { return {s * a.x, s * a.y}; }

@@ -180,10 +180,11 @@ __device__ __forceinline__ void wilson_hop(const Geom &g, const typename cplx_t<
 }
 
 // ---------------------------------------------------------------- rolled variant
-// The same hop with the direction mu a runtime value, for the float-float
-// kernels: their fully unrolled 8-hop code overflows the instruction cache
-// (ncu: most stalls "no instruction").  S_mu and S_mu^dag are unit-modulus
-// permutations, applied with selects.
+// The same hop as one loop over the 8 (direction, orientation) pairs, for the
+// float-float kernels: their unrolled code overflows the instruction cache
+// (ncu: "no instruction" the leading stall).  S_mu and S_mu^dag are
+// unit-modulus permutations applied with selects, the projector sign and the
+// link orientation are runtime values.
 
 // c * v for c in {1, -1, i, -i}: rot = multiply by i, neg = negate
 template <typename C> __device__ __forceinline__ C unit_mul(C v, bool rot, bool neg) {
@@ -205,8 +206,14 @@ template <typename C> __device__ __forceinline__ void sdag_apply_rt(int mu, C u0
     o1 = unit_mul(b, mu == 0 || mu == 2, mu == 1 || mu == 2);
 }
 
-template <typename T, int SG, bool BACK, int BC, int NR>
-__device__ __forceinline__ void hop_one_rt(int mu, const typename cplx_t<T>::type *__restrict__ U,
+// U^dag is read as the transpose of U with conjugated elements (back = true).
+template <typename C> __device__ __forceinline__ C conj_if(C v, bool c) {
+    C r = v;
+    if (c) r.y = -r.y;
+    return r;
+}
+template <typename T, int BC, int NR>
+__device__ __forceinline__ void hop_one_rt(int mu, bool plus, bool back, const typename cplx_t<T>::type *__restrict__ U,
                                            const typename cplx_t<T>::type *__restrict__ in, int Vl, int nb, int ls,
                                            bool flip, typename cplx_t<T>::type acc[12][NR]) {
     typedef typename cplx_t<T>::type C;
@@ -223,25 +230,33 @@ __device__ __forceinline__ void hop_one_rt(int mu, const typename cplx_t<T>::typ
         for (int r = 0; r < NR; ++r) {
             C s0, s1;
             s_apply_rt(mu, p2[r], p3[r], s0, s1);
-            if (SG > 0) { h[0][a][r] = cadd(p0[r], s0); h[1][a][r] = cadd(p1[r], s1); }
-            else { h[0][a][r] = csub(p0[r], s0); h[1][a][r] = csub(p1[r], s1); }
+            if (!plus) { s0 = cneg(s0); s1 = cneg(s1); }
+            h[0][a][r] = cadd(p0[r], s0);
+            h[1][a][r] = cadd(p1[r], s1);
         }
     }
     const C *ul = U + ((size_t)mu * Vl + ls) * 9;
+    const int ra = back ? 1 : 3, rb = back ? 3 : 1; // element (a, b) of W at ul[a * ra + b * rb]
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         C ur[3];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) ur[b] = BACK ? ul[b * 3 + a] : ul[a * 3 + b];
+        for (int b = 0; b < 3; ++b) ur[b] = conj_if(ul[a * ra + b * rb], back);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            C w0 = mkc<C>(0, 0), w1 = mkc<C>(0, 0);
+            C w0, w1;
+#ifndef SMPQ_DF64_CHAINED
+            if constexpr (std::is_same<T, df64>::value) {
+                const C v0[3] = {h[0][0][r], h[0][1][r], h[0][2][r]}, v1[3] = {h[1][0][r], h[1][1][r], h[1][2][r]};
+                w0 = cdot3(ur, v0);
+                w1 = cdot3(ur, v1);
+            } else
+#endif
+            {
+                w0 = mkc<C>(0, 0);
+                w1 = mkc<C>(0, 0);
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (BACK) {
-                    w0 = cfmac(ur[b], h[0][b][r], w0);
-                    w1 = cfmac(ur[b], h[1][b][r], w1);
-                } else {
+                for (int b = 0; b < 3; ++b) {
                     w0 = cfma(ur[b], h[0][b][r], w0);
                     w1 = cfma(ur[b], h[1][b][r], w1);
                 }
@@ -254,8 +269,9 @@ __device__ __forceinline__ void hop_one_rt(int mu, const typename cplx_t<T>::typ
             acc[3 + a][r] = cadd(acc[3 + a][r], w1);
             C l0, l1;
             sdag_apply_rt(mu, w0, w1, l0, l1);
-            if (SG > 0) { acc[6 + a][r] = cadd(acc[6 + a][r], l0); acc[9 + a][r] = cadd(acc[9 + a][r], l1); }
-            else { acc[6 + a][r] = csub(acc[6 + a][r], l0); acc[9 + a][r] = csub(acc[9 + a][r], l1); }
+            if (!plus) { l0 = cneg(l0); l1 = cneg(l1); }
+            acc[6 + a][r] = cadd(acc[6 + a][r], l0);
+            acc[9 + a][r] = cadd(acc[9 + a][r], l1);
         }
     }
 }
@@ -271,20 +287,21 @@ __device__ __forceinline__ void wilson_hop_rolled(const Geom &g, const typename 
         for (int r = 0; r < NR; ++r) acc[c][r] = mkc<C>(0, 0);
     const SiteCoords xc(g, s);
 #pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
+    for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1;
+        const bool back = k & 1;
         const int n = g.n[mu], st = g.stride[mu], c = xc.x[mu];
-        const bool top = c == n - 1, bot = c == 0;
-        const int nf = top ? s - (n - 1) * st : s + st;
-        const int nbk = bot ? s + (n - 1) * st : s - st;
-        const bool ff = top && g.bcf[mu] < 0;
-        const bool fb = bot && g.bcf[mu] < 0;
-        hop_one_rt<T, DAG ? +1 : -1, false, BC, NR>(mu, U, in, g.V, nf, s, ff, acc);
-        hop_one_rt<T, DAG ? -1 : +1, true, BC, NR>(mu, U, in, g.V, nbk, nbk, fb, acc);
+        const bool edge = back ? c == 0 : c == n - 1;
+        const int nb = back ? (edge ? s + (n - 1) * st : s - st) : (edge ? s - (n - 1) * st : s + st);
+        const bool flip = edge && g.bcf[mu] < 0;
+        // forward: (1 - g) [DAG: (1 + g)], backward: (1 + g) [DAG: (1 - g)]
+        const bool plus = back != DAG;
+        hop_one_rt<T, BC, NR>(mu, plus, back, U, in, g.V, nb, back ? nb : s, flip, acc);
     }
 }
 
-// full (unrolled) hop for FP32/FP64, rolled directions for float-float
-// (SMPQ_DF64_UNROLLED / SMPQ_FP32_ROLLED switch the choice for tuning)
+// Unrolled hop for FP32/FP64, rolled for float-float (SMPQ_DF64_UNROLLED and
+// SMPQ_FP32_ROLLED switch the choice for tuning sweeps).
 template <typename T, bool DAG, int BC, int NR = 1>
 __device__ __forceinline__ void wilson_hop_auto(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
                                                 const typename cplx_t<T>::type *__restrict__ in, int s,
