@@ -19,7 +19,10 @@ scipy FP64, written for readability, not speed:
                (Sec. 2.2, Eqs. 15, 18-19; Tables 1-2);
   qx.py        q(x) = 1/2 tr(gamma_5 D_ov)(x, x) by point sources (Eq. 5) and its
                SMP estimate (Eq. 16), and Q = sum_x q(x);
-  spectrum.py  spectral bounds of H_W^2 (setup for Eq. 4; the paper is silent).
+  spectrum.py  spectral bounds of H_W^2 (setup for Eq. 4; the paper is silent);
+  lowmodes.py  the lowest eigenmodes of H_W treated exactly in eps(H_W) (Eq. 4),
+               with the rational on the shortened interval (not in the paper;
+               its Sec. 3 compares against low modes of D_ov).
 
 Parity status: every function here is pinned by tests/test_oracle_*.py against
 closed forms, dense linear algebra on 4^4 or the integers the paper prints.
