@@ -135,6 +135,34 @@ int smpq_set_spectrum(smpq_ctx *ctx, double lmin2, double lmax2);
  * Outputs (nullable) receive the unwidened Ritz values. */
 int smpq_measure_spectrum(smpq_ctx *ctx, int iters, double *lmin2, double *lmax2);
 
+/* Low modes of H_W = gamma_5 D_W treated exactly in the sign function (a
+ * standard overlap technique; the paper evaluates eps(H_W) of Eq. 4 with the
+ * rational alone and mentions low modes only of D_ov, end of Sec. 3):
+ *   eps(H) = sum_{j<k} sign(lambda_j) v_j v_j^dag + H R(H^2) (1 - sum_j v_j v_j^dag).
+ * Computes the k + 1 eigenpairs of H_W of smallest |lambda| by Chebyshev-
+ * filtered subspace iteration on H_W^2 (block of `block` vectors, a multiple of
+ * 12 up to 48; 0 chooses about 2k + 2), FP64, until ||H v - lambda v|| <= tol
+ * (<= 0: 1e-11) for all k + 1, at most max_iter filter steps (<= 0: 200).
+ * Needs a gauge field and a spectral interval whose upper end bounds H_W^2.
+ * evals, resid (nullable): k + 1 doubles, signed lambda_j ordered by |lambda|
+ * and residual norms; *iterations (nullable): filter steps.  From then on,
+ * smpq_compute_qx[_classes] and smpq_apply_dov treat the first k modes exactly:
+ * the solves run on the projected sources and q^SMP(x) gains the low-mode term
+ * 1/2 sum_{alpha,a} sum_j sign(lambda_j) v_j(x,alpha,a) (v_j^dag b_{alpha,a}).
+ * The rational still follows the context's interval: set it next with
+ * smpq_set_spectrum(ctx, 0.98 * evals[k]^2, b) to shorten it.  Loading a gauge
+ * field or smpq_clear_low_modes drops the modes.  1 <= k <= 43; SMPQ_ENOCONV if
+ * not converged (no modes kept). */
+int smpq_low_modes(smpq_ctx *ctx, int k, int block, double tol, int max_iter, double *evals, double *resid,
+                   int *iterations);
+
+/* The modes in use: *k (nullable) = their number (0: none); evals (nullable):
+ * k doubles; evecs (nullable): host double[V][4][3][k][2], orthonormal. */
+int smpq_get_low_modes(smpq_ctx *ctx, double *evecs, double *evals, int *k);
+
+/* Drop the low modes: back to the rational on the whole spectrum. */
+int smpq_clear_low_modes(smpq_ctx *ctx);
+
 /* Zolotarev coefficients of R(x) = c0 + sum_i c[i]/(x + q[i]) ~ 1/sqrt(x) on
  * [a, b] (Eq. 4), type (npoles, npoles), q ascending; *delta = max relative
  * error.  Pure host computation; c and q hold npoles doubles. */

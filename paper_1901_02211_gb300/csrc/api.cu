@@ -191,6 +191,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         size_t held = 0;
         for (const Buf &b : ctx->ws) held += b.bytes;
         size_t per = bytes_per_rhs(ctx, prec, n_sup, ctx->opt.npoles);
+        if (kind == 0 && ctx->lm_k > 0) per += (size_t)ctx->V * 12 * sizeof(double2); // projected source field
         long cap = (long)((0.6 * (double)(freeb + held)) / (double)per);
         cap = std::max(12L, cap - cap % 48);
         B = (int)std::min<long>(nrhs_total, cap);
@@ -234,6 +235,12 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         if ((rc = ensure(ctx, ctx->ws[W_SRC], 2 * nf * sizeof(double2)))) return rc;
         spec.d_src_field = (const double *)((double2 *)ctx->ws[W_SRC].p + nf);
     }
+    const bool project = kind == 0 && ctx->lm_k > 0; // low modes of H_W treated exactly
+    if (project) {
+        if ((rc = ensure(ctx, ctx->ws[W_SRC], (size_t)ctx->V * 12 * B * sizeof(double2)))) return rc;
+        spec.d_src_field = (const double *)ctx->ws[W_SRC].p;
+        if ((rc = lowmodes_class_overlaps(ctx, st))) return rc;
+    }
 
     int maxit = 0, nrel = 0, nb = 0;
     long long totit = 0;
@@ -253,11 +260,17 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
             launch_dslash<double>(ctx->geom, ctx->U64.p, b, (void *)spec.d_src_field, B, BC, 1, ctx->opt.kappa, st);
             ctx->launches += 2;
         }
+        if (project) lowmodes_source(ctx, (double2 *)ctx->ws[W_SRC].p, B, BC, d_rhs_class, d_src_comp, st);
         SolveOut out;
         rc = multishift_solve(ctx, spec, &out);
         if (rc) return rc;
         if (kind == 0) {
-            launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y, st);
+            if (project)
+                lowmodes_add_c0b(ctx, n_sup, B, BC, spec.d_supsite, d_rhs_class, (const double2 *)ctx->ws[W_SRC].p,
+                                 out.y, st);
+            else
+                launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y,
+                               st);
             launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class, d_src_comp,
                             (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa,
                             (double2 *)ctx->ws[W_QTERM].p, st);
@@ -284,6 +297,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         dq_re = (double *)ctx->ws[W_Q].p;
         dq_im = dq_re + ctx->V;
     }
+    if (project) lowmodes_qterm(ctx, d_classes, nc, (double2 *)ctx->ws[W_QTERM].p, st);
     launch_qsum((const double2 *)ctx->ws[W_QTERM].p, d_classes, nc, (const int *)ctx->d_members.p, ctx->members,
                 dq_re, dq_im, kind == 0 ? 0.5 : 1.0, st);
     // Q in site order over the processed sites
@@ -419,6 +433,7 @@ int smpq_destroy(smpq_ctx *ctx) {
         release(ctx->Udf);
         release(ctx->d_colour);
         release(ctx->d_members);
+        lowmodes_clear(ctx);
         cudaEventDestroy(ctx->ev0);
         cudaEventDestroy(ctx->ev1);
         cudaEventDestroy(ctx->ev2);
@@ -454,6 +469,8 @@ int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int o
     if (V > (1L << 28)) return set_err(ctx, SMPQ_EINVAL, "lattice volume above 2^28 sites");
     DeviceGuard dg(ctx->device);
     StreamEntry se(ctx, ctx->user_stream);
+    cudaStreamSynchronize(ctx->stream);
+    lowmodes_clear(ctx); // modes of the previous gauge field
     int rc;
     if ((rc = ensure(ctx, ctx->U64, (size_t)V * 36 * sizeof(double2)))) return rc;
     if ((rc = ensure(ctx, ctx->U32, (size_t)V * 36 * sizeof(float2)))) return rc;
@@ -528,6 +545,54 @@ int smpq_measure_spectrum(smpq_ctx *ctx, int iters, double *lmin2, double *lmax2
     if (lmin2) *lmin2 = lo;
     if (lmax2) *lmax2 = hi;
     return smpq_set_spectrum(ctx, 0.98 * lo, 1.02 * hi);
+}
+
+int smpq_low_modes(smpq_ctx *ctx, int k, int block, double tol, int max_iter, double *evals, double *resid,
+                   int *iterations) {
+    int rc = check_ctx(ctx, true, true, false);
+    if (rc) return rc;
+    if (k < 1 || k > 43) return set_err(ctx, SMPQ_EINVAL, "low modes: need 1 <= k <= 43");
+    int m = block;
+    if (m <= 0) m = std::min(48, 12 * ((2 * k + 2 + 11) / 12));
+    if (m < k + 5) m = 12 * ((k + 5 + 11) / 12);
+    if (!(tol > 0)) tol = 1e-11;
+    if (max_iter <= 0) max_iter = 200;
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    ctx->launches = 0;
+    return lowmodes_compute(ctx, k, m, tol, max_iter, 20, evals, resid, iterations);
+}
+
+int smpq_get_low_modes(smpq_ctx *ctx, double *evecs, double *evals, int *k) {
+    if (!ctx) return SMPQ_EINVAL;
+    if (k) *k = ctx->lm_k;
+    if (ctx->lm_k == 0) return SMPQ_OK;
+    if (evals) std::copy(ctx->lm_val.begin(), ctx->lm_val.begin() + ctx->lm_k, evals);
+    if (!evecs) return SMPQ_OK;
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    const int V = ctx->V, m = ctx->lm_m, kk = ctx->lm_k;
+    const size_t n = (size_t)V * 12 * m;
+    int rc = ensure(ctx, ctx->ws[W_OUT], n * sizeof(double2));
+    if (rc) return rc;
+    launch_from_tiled<double>(ctx->lm_vec.p, (double *)ctx->ws[W_OUT].p, V, m, 12, ctx->stream);
+    std::vector<double> h(2 * n);
+    cudaMemcpyAsync(h.data(), ctx->ws[W_OUT].p, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+    if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "get_low_modes"))) return rc;
+    for (size_t sc = 0; sc < (size_t)V * 12; ++sc)
+        for (int j = 0; j < kk; ++j) {
+            evecs[2 * (sc * kk + j)] = h[2 * (sc * m + j)];
+            evecs[2 * (sc * kk + j) + 1] = h[2 * (sc * m + j) + 1];
+        }
+    return SMPQ_OK;
+}
+
+int smpq_clear_low_modes(smpq_ctx *ctx) {
+    if (!ctx) return SMPQ_EINVAL;
+    DeviceGuard dg(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    lowmodes_clear(ctx);
+    return SMPQ_OK;
 }
 
 int smpq_colour_sites(const int dims[4], int r, int mode, int *colour, int *n_classes) {
@@ -617,10 +682,11 @@ int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_d
     StreamEntry se(ctx, ctx->user_stream);
     cudaStream_t st = ctx->stream;
     const size_t n = (size_t)ctx->V * 12 * B;
-    if ((rc = ensure(ctx, ctx->ws[W_SRC], 3 * n * 16))) return rc;
+    const bool project = ctx->lm_k > 0;
+    if ((rc = ensure(ctx, ctx->ws[W_SRC], (project ? 4 : 3) * n * 16))) return rc;
     if ((rc = ensure(ctx, ctx->ws[W_RHS], 2 * (size_t)B * sizeof(int)))) return rc;
     double *abi = (double *)ctx->ws[W_SRC].p;
-    double2 *b64 = (double2 *)(abi + 2 * n), *z = b64 + n;
+    double2 *b64 = (double2 *)(abi + 2 * n), *z = b64 + n, *bp = z + n;
     const double *din = in;
     if (!on_device) {
         cudaMemcpyAsync(abi, in, n * 16, cudaMemcpyHostToDevice, st);
@@ -628,6 +694,9 @@ int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_d
     }
     const int BC = 1;
     launch_to_tiled<double>(din, b64, ctx->V, B, BC, st);
+    std::vector<double> wd; // V^dag b with the low modes treated exactly
+    if (project && (rc = lowmodes_dov_project(ctx, b64, bp, B, wd, st))) return rc;
+    const double2 *bsol = project ? bp : b64;
     cudaMemsetAsync(ctx->ws[W_RHS].p, 0, 2 * (size_t)B * sizeof(int), st); // every rhs in support class 0
     SolveSpec spec{};
     spec.B = B;
@@ -640,13 +709,14 @@ int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_d
     spec.d_src_class = (const int *)ctx->ws[W_RHS].p;
     spec.d_src_comp = (const int *)ctx->ws[W_RHS].p + B;
     spec.d_colour = nullptr;
-    spec.d_src_field = (const double *)b64;
+    spec.d_src_field = (const double *)bsol;
     SolveOut o;
     if ((rc = multishift_solve(ctx, spec, &o))) return rc;
-    // y = c0 b + sum c_i x_i ; out = b + D_W y
-    launch_axpy(o.y, b64, ctx->c0, n, st);
+    // y = c0 b + sum c_i x_i ; out = b + D_W y  (b -> b_perp in y, plus gamma_5 V sign V^dag b)
+    launch_axpy(o.y, bsol, ctx->c0, n, st);
     launch_dslash<double>(ctx->geom, ctx->U64.p, o.y, z, B, BC, 0, ctx->opt.kappa, st);
     launch_axpy(z, b64, 1.0, n, st);
+    if (project && (rc = lowmodes_dov_finish(ctx, z, B, wd, st))) return rc;
     double *dout = on_device ? out : abi;
     launch_from_tiled<double>(z, dout, ctx->V, B, BC, st);
     if (!on_device) cudaMemcpyAsync(out, abi, n * 16, cudaMemcpyDeviceToHost, st);

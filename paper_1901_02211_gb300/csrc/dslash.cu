@@ -2,6 +2,7 @@
 // dslash D_W / D_W^dag (Sec. 2.1, around Eq. 3) used by smpq_dslash.
 #include <string>
 
+#include "smpq_internal.cuh"
 #include "wilson.cuh"
 
 // ------------------------------------------------------------------ links

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "smpq_internal.cuh"
 #include "wilson.cuh"
 
 namespace {

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "smpq_internal.cuh"
 #include "wilson.cuh"
 
 int colour_sites_host(const int dims[4], int r, int mode, std::vector<int> &colour, int *n_classes,

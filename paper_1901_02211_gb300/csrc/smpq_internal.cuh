@@ -8,105 +8,9 @@
 #include <vector>
 
 #include "../../include/smpq.h"
-#include "df64.cuh"
+#include "device.cuh"
 
 #define SMPQ_MAX_POLES 32
-
-// ---------------------------------------------------------------- complex helpers
-template <typename T> struct cplx_t;
-template <> struct cplx_t<double> { typedef double2 type; };
-template <> struct cplx_t<float> { typedef float2 type; };
-template <> struct cplx_t<df64> { typedef df64c type; };
-
-// explicit conversion of a real component to double
-__host__ __device__ __forceinline__ double to_d(double v) { return v; }
-__host__ __device__ __forceinline__ double to_d(float v) { return v; }
-__host__ __device__ __forceinline__ double to_d(df64 v) { return (double)v; }
-
-template <typename C> __host__ __device__ __forceinline__ C mkc(double re, double im) {
-    C c;
-    c.x = re;
-    c.y = im;
-    return c;
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// a * b
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// acc + a * b
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
-    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-    return acc;
-}
-__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
-    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
-    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
-    return acc;
-}
-// acc + conj(a) * b
-__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
-    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
-    return acc;
-}
-__device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 acc) {
-    acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
-    acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
-    return acc;
-}
-// i * a
-__device__ __forceinline__ double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }
-__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }
-__device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
-__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
-__device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
-__device__ __forceinline__ double norm2(double2 a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double norm2(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
-
-// ---------------------------------------------------------------- lattice geometry
-struct Geom {
-    int n[4];      // nx, ny, nz, nt
-    int stride[4]; // 1, nx, nx*ny, nx*ny*nz
-    int V;
-    float bcf[4];  // boundary factor for hops crossing the boundary in mu
-};
-
-// Neighbour of s in direction mu (dir = +1 or -1); *f receives the boundary factor.
-__device__ __forceinline__ int neighbour(const Geom &g, int s, int mu, int dir, float *f) {
-    int c = (s / g.stride[mu]) % g.n[mu];
-    if (dir > 0) {
-        if (c == g.n[mu] - 1) {
-            *f = g.bcf[mu];
-            return s - (g.n[mu] - 1) * g.stride[mu];
-        }
-        *f = 1.f;
-        return s + g.stride[mu];
-    }
-    if (c == 0) {
-        *f = g.bcf[mu];
-        return s + (g.n[mu] - 1) * g.stride[mu];
-    }
-    *f = 1.f;
-    return s - g.stride[mu];
-}
-
-// ---------------------------------------------------------------- field layout
-// A batch of B right-hand sides is stored in RHS tiles of BC columns:
-//   element (component c in 0..11 = spin*3 + colour, site s, rhs j)
-//   at (((j / BC) * V + s) * 12 + c) * BC + (j % BC),
-// i.e. one tile is [site][component][column]: a warp reads consecutive columns
-// of one site component, and the 12 components of a site sit at fixed
-// offsets (immediates in the load instructions).
-// Links: U[(mu * V + s) * 9 + row * 3 + col] (the 9 elements of one link contiguous).
 
 // ---------------------------------------------------------------- solver state
 struct ShiftParams {
@@ -161,6 +65,13 @@ struct smpq_ctx {
     long long prof_a_n = 0, prof_b_n = 0;
     double prof_a_hi_ms = 0, prof_b_hi_ms = 0;   // FP64-accurate iterations
     long long prof_a_hi_n = 0, prof_b_hi_n = 0;
+    // low modes of H_W treated exactly (lowmodes.cu): lm_k > 0 switches the
+    // projection on in compute_qx and apply_dov
+    int lm_k = 0, lm_m = 0;     // modes in use, columns of the block
+    Buf lm_vec;                 // FP64 tiled [m columns, tile 12], ordered by |lambda|
+    Buf lm_sgn;                 // double[lm_k]: sign(lambda_j)
+    Buf lm_w;                   // class overlaps v_j^dag b (per compute_qx call)
+    std::vector<double> lm_val; // lambda_j, j < lm_m, ordered by |lambda|
 };
 
 // workspace slots of smpq_ctx::ws
@@ -219,6 +130,26 @@ struct SolveOut {
 };
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out);
 int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi);
+// lowmodes.cu : the k + 1 eigenpairs of H_W of smallest |lambda| (block of m
+// columns, m a multiple of 12, at most 48) into ctx->lm_*; evals / resid get
+// k + 1 entries
+int lowmodes_compute(smpq_ctx *ctx, int k, int m, double tol, int max_iter, int degree, double *evals,
+                     double *resid, int *iterations);
+void lowmodes_clear(smpq_ctx *ctx);
+// projection of the SMP sources of one batch: w = v^dag b per class (once per
+// call, for classes listed in d_classes), b_perp = b - V w into the tiled
+// source field, y += c0 b_perp on the support, and the low-mode term of q(x)
+int lowmodes_class_overlaps(smpq_ctx *ctx, cudaStream_t st);
+void lowmodes_source(smpq_ctx *ctx, double2 *bperp, int B, int BC, const int *d_rhs_class, const int *d_src_comp,
+                     cudaStream_t st);
+void lowmodes_add_c0b(smpq_ctx *ctx, int n_sup, int B, int BC, const int *d_supsite, const int *d_rhs_class,
+                      const double2 *bperp, double2 *y, cudaStream_t st);
+void lowmodes_qterm(smpq_ctx *ctx, const int *d_classes, int nc, double2 *qterm, cudaStream_t st);
+// apply_dov (tile 1, B columns): b_perp = b - V (V^dag b) into bperp, keeping
+// V^dag b for lowmodes_dov_finish, which adds gamma_5 V sign (V^dag b) to out
+int lowmodes_dov_project(smpq_ctx *ctx, const double2 *b, double2 *bperp, int B, std::vector<double> &wd,
+                         cudaStream_t st);
+int lowmodes_dov_finish(smpq_ctx *ctx, double2 *out, int B, const std::vector<double> &wd, cudaStream_t st);
 // autotuner: average ms of one D_W + D_W^dag-update launch pair (scratch fields in buf:
 // 3 fields of B x 12 x V complex of the widest type used, part: partials, alpha: B doubles)
 float time_dslash_pair(smpq_ctx *ctx, int prec, int B, int BC, int reps, void *buf, double *part, double *alpha);

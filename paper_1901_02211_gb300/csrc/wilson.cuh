@@ -17,7 +17,7 @@
 #pragma once
 #include <type_traits>
 
-#include "smpq_internal.cuh"
+#include "device.cuh"
 
 // S_mu l  for the lower 2-spinor l = (l0, l1)
 template <int MU, typename C> __device__ __forceinline__ void s_apply(C l0, C l1, C &o0, C &o1) {
@@ -206,6 +206,17 @@ template <typename C> __device__ __forceinline__ void sdag_apply_rt(int mu, C u0
     o1 = unit_mul(b, mu == 0 || mu == 2, mu == 1 || mu == 2);
 }
 
+// Float-float sums inside the hop are left unnormalised (cadd_lazy, cdot3_lazy)
+// and the 12 accumulators are renormalised once after the 8 hops;
+// SMPQ_DF64_EAGER renormalises after every operation instead.
+#ifdef SMPQ_DF64_EAGER
+#define SMPQ_HADD cadd
+#define SMPQ_HDOT cdot3
+#else
+#define SMPQ_HADD cadd_lazy
+#define SMPQ_HDOT cdot3_lazy
+#endif
+
 // U^dag is read as the transpose of U with conjugated elements (back = true).
 template <typename C> __device__ __forceinline__ C conj_if(C v, bool c) {
     C r = v;
@@ -231,8 +242,8 @@ __device__ __forceinline__ void hop_one_rt(int mu, bool plus, bool back, const t
             C s0, s1;
             s_apply_rt(mu, p2[r], p3[r], s0, s1);
             if (!plus) { s0 = cneg(s0); s1 = cneg(s1); }
-            h[0][a][r] = cadd(p0[r], s0);
-            h[1][a][r] = cadd(p1[r], s1);
+            h[0][a][r] = SMPQ_HADD(p0[r], s0);
+            h[1][a][r] = SMPQ_HADD(p1[r], s1);
         }
     }
     const C *ul = U + ((size_t)mu * Vl + ls) * 9;
@@ -248,8 +259,8 @@ __device__ __forceinline__ void hop_one_rt(int mu, bool plus, bool back, const t
 #ifndef SMPQ_DF64_CHAINED
             if constexpr (std::is_same<T, df64>::value) {
                 const C v0[3] = {h[0][0][r], h[0][1][r], h[0][2][r]}, v1[3] = {h[1][0][r], h[1][1][r], h[1][2][r]};
-                w0 = cdot3(ur, v0);
-                w1 = cdot3(ur, v1);
+                w0 = SMPQ_HDOT(ur, v0);
+                w1 = SMPQ_HDOT(ur, v1);
             } else
 #endif
             {
@@ -265,13 +276,13 @@ __device__ __forceinline__ void hop_one_rt(int mu, bool plus, bool back, const t
                 w0 = cneg(w0);
                 w1 = cneg(w1);
             }
-            acc[a][r] = cadd(acc[a][r], w0);
-            acc[3 + a][r] = cadd(acc[3 + a][r], w1);
+            acc[a][r] = SMPQ_HADD(acc[a][r], w0);
+            acc[3 + a][r] = SMPQ_HADD(acc[3 + a][r], w1);
             C l0, l1;
             sdag_apply_rt(mu, w0, w1, l0, l1);
             if (!plus) { l0 = cneg(l0); l1 = cneg(l1); }
-            acc[6 + a][r] = cadd(acc[6 + a][r], l0);
-            acc[9 + a][r] = cadd(acc[9 + a][r], l1);
+            acc[6 + a][r] = SMPQ_HADD(acc[6 + a][r], l0);
+            acc[9 + a][r] = SMPQ_HADD(acc[9 + a][r], l1);
         }
     }
 }
@@ -298,6 +309,10 @@ __device__ __forceinline__ void wilson_hop_rolled(const Geom &g, const typename 
         const bool plus = back != DAG;
         hop_one_rt<T, BC, NR>(mu, plus, back, U, in, g.V, nb, back ? nb : s, flip, acc);
     }
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[c][r] = crenorm(acc[c][r]);
 }
 
 // Unrolled hop for FP32/FP64, rolled for float-float (SMPQ_DF64_UNROLLED and

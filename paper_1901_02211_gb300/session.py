@@ -58,6 +58,17 @@ class Session:
     def measure_spectrum(self, iters=200):
         return S.smpq_measure_spectrum(self.ctx, iters)
 
+    def low_modes(self, k, block=0, tol=0.0, max_iter=0):
+        """Treat the k lowest modes of H_W exactly from now on; returns
+        (evals[k+1], residuals[k+1], filter steps)."""
+        return S.smpq_low_modes(self.ctx, k, block, tol, max_iter)
+
+    def get_low_modes(self):
+        return S.smpq_get_low_modes(self.ctx, self.V)
+
+    def clear_low_modes(self):
+        S.smpq_clear_low_modes(self.ctx)
+
     def zolotarev(self):
         return S.smpq_get_zolotarev(self.ctx, self.options.npoles)
 

@@ -89,6 +89,7 @@ EXPORTS = [
     "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
     "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv", "smpq_compute_qx_batch",
+    "smpq_low_modes", "smpq_get_low_modes", "smpq_clear_low_modes",
 ]
 
 _lib = None
@@ -129,6 +130,9 @@ def load(build_if_missing=True):
         "smpq_compute_qx_classes": [P, PI, I, P, P, I, ctypes.POINTER(smpq_stats)],
         "smpq_trace_dwinv": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
         "smpq_compute_qx_batch": [P, I, P, P, I, PD, ctypes.POINTER(smpq_stats)],
+        "smpq_low_modes": [P, I, I, D, I, P, P, PI],
+        "smpq_get_low_modes": [P, P, P, PI],
+        "smpq_clear_low_modes": [P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -201,6 +205,31 @@ def smpq_measure_spectrum(ctx, iters=200):
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _check(load().smpq_measure_spectrum(ctx, iters, ctypes.byref(lo), ctypes.byref(hi)), ctx)
     return lo.value, hi.value
+
+
+def smpq_low_modes(ctx, k, block=0, tol=0.0, max_iter=0):
+    """(evals[k+1] signed, ordered by |lambda|; residual norms[k+1]; filter steps)."""
+    ev = np.zeros(k + 1)
+    res = np.zeros(k + 1)
+    it = ctypes.c_int()
+    _check(load().smpq_low_modes(ctx, k, block, tol, max_iter, ev.ctypes.data, res.ctypes.data, ctypes.byref(it)),
+           ctx)
+    return ev, res, it.value
+
+
+def smpq_get_low_modes(ctx, V):
+    """(evals[k], evecs complex[V, 4, 3, k]) of the modes in use (k may be 0)."""
+    k = ctypes.c_int()
+    _check(load().smpq_get_low_modes(ctx, None, None, ctypes.byref(k)), ctx)
+    ev = np.zeros(k.value)
+    vec = np.zeros((V, 4, 3, k.value), dtype=np.complex128)
+    if k.value:
+        _check(load().smpq_get_low_modes(ctx, vec.ctypes.data, ev.ctypes.data, ctypes.byref(k)), ctx)
+    return ev, vec
+
+
+def smpq_clear_low_modes(ctx):
+    _check(load().smpq_clear_low_modes(ctx), ctx)
 
 
 def smpq_zolotarev(npoles, a, b):
