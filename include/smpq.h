@@ -104,7 +104,7 @@ typedef struct {
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
- * 10 iterations per check, graphs on, profiling off, switch_residual 1e-2,
+ * 10 iterations per check, graphs on, profiling off, switch_residual 7e-3,
  * autotuning on. */
 int smpq_options_default(smpq_options *opt);
 

@@ -382,7 +382,7 @@ int smpq_options_default(smpq_options *o) {
     o->iters_per_check = 10;
     o->use_graphs = 1;
     o->profile = 0;
-    o->switch_residual = 1e-2;
+    o->switch_residual = 7e-3;
     o->autotune = 1;
     return SMPQ_OK;
 }

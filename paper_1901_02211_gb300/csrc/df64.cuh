@@ -138,6 +138,69 @@ __device__ __forceinline__ df64c cdot3_lazy(const df64c a[3], const df64c v[3]) 
     }
     return {df64(sr, er), df64(si, ei)};
 }
+// The same unnormalised dot product for two right-hand vectors v0, v1 that
+// share the matrix row a (the two spin rows of a projected hop), with packed
+// two-lane FP32 instructions: lane 0 computes a . v0, lane 1 a . v1.
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    float2 bb = __fadd2_rn(s, f2neg(a));
+    e = __fadd2_rn(__fadd2_rn(a, f2neg(__fadd2_rn(s, f2neg(bb)))), __fadd2_rn(b, f2neg(bb)));
+}
+__device__ __forceinline__ void ff_prod2(float2 ah, float2 al, float2 bh, float2 bl, float2 &p, float2 &q) {
+    p = __fmul2_rn(ah, bh);
+    q = __ffma2_rn(ah, bh, f2neg(p));
+    q = __ffma2_rn(ah, bl, __ffma2_rn(al, bh, q));
+}
+__device__ __forceinline__ void ff_acc2(float2 &s, float2 &e, float2 ah, float2 al, float2 bh, float2 bl) {
+    float2 p, q, t, u;
+    ff_prod2(ah, al, bh, bl, p, q);
+    two_sum2(s, p, t, u);
+    s = t;
+    e = __fadd2_rn(e, __fadd2_rn(q, u));
+}
+// lanes: 0 -> a . v0, 1 -> a . v1; (sr, er) real part, (si, ei) imaginary part
+__device__ __forceinline__ void cdot3x2_pairs(const df64c a[3], const df64c v0[3], const df64c v1[3], float2 &sr,
+                                              float2 &er, float2 &si, float2 &ei) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const float2 axh = f2b(a[b].x.hi), axl = f2b(a[b].x.lo), ayh = f2b(a[b].y.hi), ayl = f2b(a[b].y.lo);
+        const float2 vxh = make_float2(v0[b].x.hi, v1[b].x.hi), vxl = make_float2(v0[b].x.lo, v1[b].x.lo);
+        const float2 vyh = make_float2(v0[b].y.hi, v1[b].y.hi), vyl = make_float2(v0[b].y.lo, v1[b].y.lo);
+        if (b == 0) {
+            ff_prod2(axh, axl, vxh, vxl, sr, er);
+            ff_prod2(axh, axl, vyh, vyl, si, ei);
+        } else {
+            ff_acc2(sr, er, axh, axl, vxh, vxl);
+            ff_acc2(si, ei, axh, axl, vyh, vyl);
+        }
+        ff_acc2(sr, er, f2neg(ayh), f2neg(ayl), vyh, vyl);
+        ff_acc2(si, ei, ayh, ayl, vxh, vxl);
+    }
+}
+__device__ __forceinline__ void cdot3x2_lazy(const df64c a[3], const df64c v0[3], const df64c v1[3], df64c &w0,
+                                             df64c &w1) {
+    float2 sr, er, si, ei;
+    cdot3x2_pairs(a, v0, v1, sr, er, si, ei);
+    w0 = {df64(sr.x, er.x), df64(si.x, ei.x)};
+    w1 = {df64(sr.y, er.y), df64(si.y, ei.y)};
+}
+// Two complex float-float values in packed form (lane 0, lane 1), unnormalised.
+struct f2c {
+    float2 xh, xl, yh, yl;
+};
+// a += (s_x * bx, s_y * by) lazily; the sign pairs are +-1 (exact products)
+__device__ __forceinline__ void f2c_add_lazy(f2c &a, float2 sx, float2 sy, float2 bxh, float2 bxl, float2 byh,
+                                             float2 byl) {
+    float2 t, e;
+    two_sum2(a.xh, __fmul2_rn(sx, bxh), t, e);
+    a.xh = t;
+    a.xl = __fadd2_rn(e, __fadd2_rn(a.xl, __fmul2_rn(sx, bxl)));
+    two_sum2(a.yh, __fmul2_rn(sy, byh), t, e);
+    a.yh = t;
+    a.yl = __fadd2_rn(e, __fadd2_rn(a.yl, __fmul2_rn(sy, byl)));
+}
 // a + b without the final renormalisation: the high parts are added with
 // two-sum, the low parts and the rounding error in plain FP32 (8 operations
 // instead of 11).  hi + lo stays exact to about 2^-46 relative but lo may

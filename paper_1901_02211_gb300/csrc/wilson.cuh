@@ -208,7 +208,9 @@ template <typename C> __device__ __forceinline__ void sdag_apply_rt(int mu, C u0
 
 // Float-float sums inside the hop are left unnormalised (cadd_lazy, cdot3_lazy)
 // and the 12 accumulators are renormalised once after the 8 hops;
-// SMPQ_DF64_EAGER renormalises after every operation instead.
+// SMPQ_DF64_EAGER renormalises after every operation instead.  The colour
+// products of the two spin rows run together in packed two-lane FP32
+// instructions (cdot3x2_lazy); SMPQ_DF64_UNPAIRED computes them one by one.
 #ifdef SMPQ_DF64_EAGER
 #define SMPQ_HADD cadd
 #define SMPQ_HDOT cdot3
@@ -259,8 +261,12 @@ __device__ __forceinline__ void hop_one_rt(int mu, bool plus, bool back, const t
 #ifndef SMPQ_DF64_CHAINED
             if constexpr (std::is_same<T, df64>::value) {
                 const C v0[3] = {h[0][0][r], h[0][1][r], h[0][2][r]}, v1[3] = {h[1][0][r], h[1][1][r], h[1][2][r]};
+#if !defined(SMPQ_DF64_UNPAIRED) && !defined(SMPQ_DF64_EAGER)
+                cdot3x2_lazy(ur, v0, v1, w0, w1); // both spin rows in packed two-lane FP32
+#else
                 w0 = SMPQ_HDOT(ur, v0);
                 w1 = SMPQ_HDOT(ur, v1);
+#endif
             } else
 #endif
             {
@@ -315,6 +321,83 @@ __device__ __forceinline__ void wilson_hop_rolled(const Geom &g, const typename 
         for (int r = 0; r < NR; ++r) acc[c][r] = crenorm(acc[c][r]);
 }
 
+// Float-float hop with the accumulators of the two spin rows of each half in
+// packed two-lane form: upper half (acc[a], acc[3 + a]) and lower half
+// (acc[6 + a], acc[9 + a]).  The colour products come out of cdot3x2_pairs in
+// that form; S_mu^dag on the lower half is a lane swap (mu <= 1), a
+// multiplication by i (mu = 0, 2) and a lane-1 sign (mu = 1, 2), and the
+// projector sign and the boundary factor enter as sign pairs.
+template <int BC>
+__device__ __forceinline__ void hop_one_pairs(int mu, bool plus, bool back, const df64c *__restrict__ U,
+                                              const df64c *__restrict__ in, int Vl, int nb, int ls, bool flip,
+                                              f2c accU[3], f2c accL[3]) {
+    const df64c *q = in + (size_t)nb * (12 * BC);
+    df64c h0[3], h1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        df64c p0 = q[a * BC], p1 = q[(3 + a) * BC], p2 = q[(6 + a) * BC], p3 = q[(9 + a) * BC];
+        df64c s0, s1;
+        s_apply_rt(mu, p2, p3, s0, s1);
+        if (!plus) { s0 = cneg(s0); s1 = cneg(s1); }
+        h0[a] = cadd_lazy(p0, s0);
+        h1[a] = cadd_lazy(p1, s1);
+    }
+    const df64c *ul = U + ((size_t)mu * Vl + ls) * 9;
+    const int ra = back ? 1 : 3, rb = back ? 3 : 1; // element (a, b) of W at ul[a * ra + b * rb]
+    const float f = flip ? -1.f : 1.f, g = plus ? f : -f, g1 = (mu == 1 || mu == 2) ? -g : g;
+    const bool swp = mu <= 1, rot = mu == 0 || mu == 2;
+    const float2 su = make_float2(f, f), sy = make_float2(g, g1), sx = rot ? make_float2(-g, -g1) : sy;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        df64c ur[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ur[b] = conj_if(ul[a * ra + b * rb], back);
+        float2 sr, er, si, ei;
+        cdot3x2_pairs(ur, h0, h1, sr, er, si, ei);
+        f2c_add_lazy(accU[a], su, su, sr, er, si, ei);
+        if (swp) {
+            sr = make_float2(sr.y, sr.x);
+            er = make_float2(er.y, er.x);
+            si = make_float2(si.y, si.x);
+            ei = make_float2(ei.y, ei.x);
+        }
+        if (rot) f2c_add_lazy(accL[a], sx, sy, si, ei, sr, er);
+        else f2c_add_lazy(accL[a], sx, sy, sr, er, si, ei);
+    }
+}
+
+template <bool DAG, int BC>
+__device__ __forceinline__ void wilson_hop_pairs(const Geom &g, const df64c *__restrict__ U,
+                                                 const df64c *__restrict__ in, int s, df64c acc[12][1]) {
+    f2c accU[3], accL[3];
+    const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) accU[a] = accL[a] = f2c{z, z, z, z};
+    const SiteCoords xc(g, s);
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1;
+        const bool back = k & 1;
+        const int n = g.n[mu], st = g.stride[mu], c = xc.x[mu];
+        const bool edge = back ? c == 0 : c == n - 1;
+        const int nb = back ? (edge ? s + (n - 1) * st : s - st) : (edge ? s - (n - 1) * st : s + st);
+        const bool flip = edge && g.bcf[mu] < 0;
+        hop_one_pairs<BC>(mu, back != DAG, back, U, in, g.V, nb, back ? nb : s, flip, accU, accL);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float2 xh, xl, yh, yl;
+        two_sum2(accU[a].xh, accU[a].xl, xh, xl);
+        two_sum2(accU[a].yh, accU[a].yl, yh, yl);
+        acc[a][0] = {df64(xh.x, xl.x), df64(yh.x, yl.x)};
+        acc[3 + a][0] = {df64(xh.y, xl.y), df64(yh.y, yl.y)};
+        two_sum2(accL[a].xh, accL[a].xl, xh, xl);
+        two_sum2(accL[a].yh, accL[a].yl, yh, yl);
+        acc[6 + a][0] = {df64(xh.x, xl.x), df64(yh.x, yl.x)};
+        acc[9 + a][0] = {df64(xh.y, xl.y), df64(yh.y, yl.y)};
+    }
+}
+
 // Unrolled hop for FP32/FP64, rolled for float-float (SMPQ_DF64_UNROLLED and
 // SMPQ_FP32_ROLLED switch the choice for tuning sweeps).
 template <typename T, bool DAG, int BC, int NR = 1>
@@ -331,7 +414,14 @@ __device__ __forceinline__ void wilson_hop_auto(const Geom &g, const typename cp
 #else
     constexpr bool roll_f = false;
 #endif
-    if constexpr ((std::is_same<T, df64>::value && roll_df) || (std::is_same<T, float>::value && roll_f))
+#ifdef SMPQ_DF64_PAIRACC
+    constexpr bool pairacc = true;
+#else
+    constexpr bool pairacc = false;
+#endif
+    if constexpr (std::is_same<T, df64>::value && roll_df && pairacc && NR == 1)
+        wilson_hop_pairs<DAG, BC>(g, U, in, s, acc);
+    else if constexpr ((std::is_same<T, df64>::value && roll_df) || (std::is_same<T, float>::value && roll_f))
         wilson_hop_rolled<T, DAG, BC, NR>(g, U, in, s, acc);
     else
         wilson_hop<T, DAG, BC, NR>(g, U, in, s, acc);
