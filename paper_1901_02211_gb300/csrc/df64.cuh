@@ -140,7 +140,8 @@ __device__ __forceinline__ df64c cdot3_lazy(const df64c a[3], const df64c v[3]) 
 }
 // The same unnormalised dot product for two right-hand vectors v0, v1 that
 // share the matrix row a (the two spin rows of a projected hop), with packed
-// two-lane FP32 instructions: lane 0 computes a . v0, lane 1 a . v1.
+// two-lane FP32 instructions (sm_100 and later): lane 0 computes a . v0,
+// lane 1 a . v1.
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
@@ -178,13 +179,6 @@ __device__ __forceinline__ void cdot3x2_pairs(const df64c a[3], const df64c v0[3
         ff_acc2(sr, er, f2neg(ayh), f2neg(ayl), vyh, vyl);
         ff_acc2(si, ei, ayh, ayl, vxh, vxl);
     }
-}
-__device__ __forceinline__ void cdot3x2_lazy(const df64c a[3], const df64c v0[3], const df64c v1[3], df64c &w0,
-                                             df64c &w1) {
-    float2 sr, er, si, ei;
-    cdot3x2_pairs(a, v0, v1, sr, er, si, ei);
-    w0 = {df64(sr.x, er.x), df64(si.x, ei.x)};
-    w1 = {df64(sr.y, er.y), df64(si.y, ei.y)};
 }
 // Two complex float-float values in packed form (lane 0, lane 1), unnormalised.
 struct f2c {

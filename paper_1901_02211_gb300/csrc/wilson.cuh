@@ -208,9 +208,9 @@ template <typename C> __device__ __forceinline__ void sdag_apply_rt(int mu, C u0
 
 // Float-float sums inside the hop are left unnormalised (cadd_lazy, cdot3_lazy)
 // and the 12 accumulators are renormalised once after the 8 hops;
-// SMPQ_DF64_EAGER renormalises after every operation instead.  The colour
-// products of the two spin rows run together in packed two-lane FP32
-// instructions (cdot3x2_lazy); SMPQ_DF64_UNPAIRED computes them one by one.
+// SMPQ_DF64_EAGER renormalises after every operation instead.  (The default
+// float-float path is hop_one_pairs below; this generic one serves it with
+// SMPQ_DF64_UNPAIRED or SMPQ_DF64_EAGER, and FP32 with SMPQ_FP32_ROLLED.)
 #ifdef SMPQ_DF64_EAGER
 #define SMPQ_HADD cadd
 #define SMPQ_HDOT cdot3
@@ -261,12 +261,8 @@ __device__ __forceinline__ void hop_one_rt(int mu, bool plus, bool back, const t
 #ifndef SMPQ_DF64_CHAINED
             if constexpr (std::is_same<T, df64>::value) {
                 const C v0[3] = {h[0][0][r], h[0][1][r], h[0][2][r]}, v1[3] = {h[1][0][r], h[1][1][r], h[1][2][r]};
-#if !defined(SMPQ_DF64_UNPAIRED) && !defined(SMPQ_DF64_EAGER)
-                cdot3x2_lazy(ur, v0, v1, w0, w1); // both spin rows in packed two-lane FP32
-#else
                 w0 = SMPQ_HDOT(ur, v0);
                 w1 = SMPQ_HDOT(ur, v1);
-#endif
             } else
 #endif
             {
@@ -398,7 +394,8 @@ __device__ __forceinline__ void wilson_hop_pairs(const Geom &g, const df64c *__r
     }
 }
 
-// Unrolled hop for FP32/FP64, rolled for float-float (SMPQ_DF64_UNROLLED and
+// Unrolled hop for FP32/FP64, rolled with packed two-lane accumulators for
+// float-float (SMPQ_DF64_UNROLLED, SMPQ_DF64_UNPAIRED, SMPQ_DF64_EAGER and
 // SMPQ_FP32_ROLLED switch the choice for tuning sweeps).
 template <typename T, bool DAG, int BC, int NR = 1>
 __device__ __forceinline__ void wilson_hop_auto(const Geom &g, const typename cplx_t<T>::type *__restrict__ U,
@@ -414,10 +411,10 @@ __device__ __forceinline__ void wilson_hop_auto(const Geom &g, const typename cp
 #else
     constexpr bool roll_f = false;
 #endif
-#ifdef SMPQ_DF64_PAIRACC
-    constexpr bool pairacc = true;
-#else
+#if defined(SMPQ_DF64_UNPAIRED) || defined(SMPQ_DF64_EAGER)
     constexpr bool pairacc = false;
+#else
+    constexpr bool pairacc = true;
 #endif
     if constexpr (std::is_same<T, df64>::value && roll_df && pairacc && NR == 1)
         wilson_hop_pairs<DAG, BC>(g, U, in, s, acc);
