@@ -464,6 +464,32 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
             out[key] = {"value": V / (per_class * n_classes), "unit": "sites/s", "extrapolated": True,
                         "sample": "%d of %d classes (%d sources), %.3f s" % (len(cls), n_classes, 12 * len(cls), dt),
                         "max_iterations": st3["max_iterations"]}
+        # ablation of the star support: the shifted directions on every site
+        # (14 full-lattice vectors per source) against the restricted path, on
+        # the same sample of classes and in the same precision
+        prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
+        cls = list(range(0, n_classes, max(1, n_classes // 16)))[:16]
+        res = {}
+        for full in (0, 1):
+            s3 = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
+                         use_graphs=1, switch_residual=args.switch, full_support=full)
+            s3.load_gauge(dims, U)
+            s3.set_spectrum(a, b)
+            s3.build_sources(args.rmin, MODE)
+            s3.compute_qx(classes=cls[:1])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q, Qs, st3 = s3.compute_qx(classes=cls)
+            dt = time.perf_counter() - t0
+            s3.close()
+            res[full] = (V / (dt / len(cls) * n_classes), q, dt)
+        colour, _ = smpq.smpq_colour_sites(dims, args.rmin, MODE)
+        mask = np.isin(colour, cls)
+        out["support_ablation"] = {
+            "restricted": res[0][0], "full_support": res[1][0], "unit": "sites/s", "extrapolated": True,
+            "sample": "%d of %d classes (%d sources), %.3f s restricted / %.3f s full" % (
+                len(cls), n_classes, 12 * len(cls), res[0][2], res[1][2]),
+            "max_abs_dq": float(np.abs(res[0][1][mask] - res[1][1][mask]).max())}
         if not args.no_cpu:
             v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1)
             out["cpu_baseline"] = {"value": v, "unit": "sites/s", "cores": thr, "kind": "oracle",

@@ -74,6 +74,9 @@ typedef struct {
     int profile;           /* time every D_W / D_W^dag launch of the solver with CUDA events */
     double switch_residual; /* SMPQ_MIXED: relative residual at which FP64 iterations hand over to FP32 */
     int autotune;           /* time the RHS tile widths (12, 24, 48) on the first solve of each shape */
+    int full_support;       /* q(x): keep the shifted directions on every site instead of only where
+                               z = D_W y is read (the ablation of that restriction; same result,
+                               14 full-lattice vectors per source) */
 } smpq_options;
 
 typedef struct {

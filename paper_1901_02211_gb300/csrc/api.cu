@@ -176,6 +176,9 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     // star support of every class
     int n_sup = 0;
     if ((rc = build_star_support(ctx, ctx->ws[W_SUP], &n_sup))) return rc;
+    // ablation of the star support: shifted directions on every site
+    const bool full_sup = kind == 0 && ctx->opt.full_support;
+    if (full_sup) n_sup = ctx->V;
     const int prec = ctx->opt.precision;
     const int nc = (int)classes.size();
     const int nrhs_total = 12 * nc;
@@ -217,7 +220,8 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     spec.prec = prec;
     spec.full_support = 0;
     spec.n_sup = n_sup;
-    spec.d_supsite = (const int *)ctx->ws[W_SUP].p;
+    spec.d_supsite = full_sup ? nullptr : (const int *)ctx->ws[W_SUP].p;
+    spec.full_support = full_sup ? 1 : 0;
     spec.d_rhs_class = d_rhs_class;
     spec.d_colour = (const int *)ctx->d_colour.p;
     spec.d_src_class = d_src_class;
@@ -271,9 +275,18 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
             else
                 launch_add_c0b(n_sup, B, BC, spec.d_supsite, d_rhs_class, d_src_comp, spec.d_colour, ctx->c0, out.y,
                                st);
-            launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class, d_src_comp,
-                            (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa,
-                            (double2 *)ctx->ws[W_QTERM].p, st);
+            if (full_sup) { // y is a whole-lattice field: z = D_W y everywhere, read at the members
+                if ((rc = ensure(ctx, ctx->ws[W_OUT], (size_t)ctx->V * 12 * B * sizeof(double2)))) return rc;
+                double2 *z = (double2 *)ctx->ws[W_OUT].p;
+                launch_dslash<double>(ctx->geom, ctx->U64.p, out.y, z, B, BC, 0, ctx->opt.kappa, st);
+                launch_contract_full(z, ctx->V, B, BC, d_rhs_class, d_src_comp, (const int *)ctx->d_members.p,
+                                     ctx->members, (double2 *)ctx->ws[W_QTERM].p, st);
+                ctx->launches += 1;
+            } else {
+                launch_contract(ctx->geom, (const double *)ctx->U64.p, out.y, n_sup, B, BC, d_rhs_class,
+                                d_src_comp, (const int *)ctx->d_members.p, ctx->members, ctx->opt.kappa,
+                                (double2 *)ctx->ws[W_QTERM].p, st);
+            }
         } else {
             launch_trace_terms(out.y, n_sup, B, BC, d_rhs_class, d_src_comp, ctx->members,
                                (double2 *)ctx->ws[W_QTERM].p, st);

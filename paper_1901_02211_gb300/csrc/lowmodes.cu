@@ -222,7 +222,7 @@ __global__ void k_lm_add_c0b(int n_sup, int B, int BC, int V, const int *__restr
     const int c = (int)(r % 12), e = (int)(r / 12);
     const int cl = rhs_class[j];
     if (cl < 0) return;
-    const int site = supsite[(size_t)cl * n_sup + e];
+    const int site = supsite ? supsite[(size_t)cl * n_sup + e] : e;
     const double2 bv = bperp[tix(site, c, j, V, BC)];
     const size_t o = (((size_t)(j / BC) * n_sup + e) * 12 + c) * BC + (j % BC);
     y[o].x += c0 * bv.x;

@@ -90,7 +90,7 @@ int build_star_support(smpq_ctx *ctx, Buf &supsite, int *n_sup) {
     return SMPQ_OK;
 }
 
-// y += c0 b on the support (y layout [(j/BC)*12 + c][n_sup][BC])
+// y += c0 b on the support (y layout [j/BC][n_sup][12][BC]; supsite null: entry = site)
 __global__ void add_c0b_kernel(int n_sup, int B, int BC, const int *__restrict__ supsite,
                                const int *__restrict__ rhs_class, const int *__restrict__ src_comp,
                                const int *__restrict__ colour, double c0, double2 *__restrict__ y) {
@@ -99,7 +99,7 @@ __global__ void add_c0b_kernel(int n_sup, int B, int BC, const int *__restrict__
     int j = (int)(i % B), k = (int)(i / B);
     int cl = rhs_class[j];
     if (cl < 0) return;
-    int site = supsite[(size_t)cl * n_sup + k];
+    int site = supsite ? supsite[(size_t)cl * n_sup + k] : k;
     if (colour[site] != cl) return;
     int c = src_comp[j];
     size_t o = (((size_t)(j / BC) * n_sup + k) * 12 + c) * BC + (j % BC);
@@ -163,6 +163,29 @@ void launch_contract(const Geom &g, const double *U64, const double2 *y, int n_s
     case 48: contract_kernel<48><<<grid, 128, 0, st>>>(g, U, y, n_sup, B, d_rhs_class, d_src_comp, d_members, members, kappa, qterm); break;
     default: break;
     }
+}
+
+// Whole-lattice variant (the star-support ablation): z = D_W y is a field in
+// the tile layout; qterm[(class * 12 + comp) * members + m] = gamma5(comp) z(x_m, comp, j).
+__global__ void contract_full_kernel(const double2 *__restrict__ z, int V, int B, int BC,
+                                     const int *__restrict__ rhs_class, const int *__restrict__ src_comp,
+                                     const int *__restrict__ members, int nmem, double2 *__restrict__ qterm) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)nmem * B) return;
+    int j = (int)(i % B), m = (int)(i / B);
+    int cl = rhs_class[j];
+    if (cl < 0) return;
+    int x = members[(size_t)cl * nmem + m], c = src_comp[j];
+    double2 v = z[(((size_t)(j / BC) * V + x) * 12 + c) * BC + (j % BC)];
+    double g5 = (c / 3) < 2 ? 1.0 : -1.0;
+    qterm[((size_t)cl * 12 + c) * nmem + m] = make_double2(g5 * v.x, g5 * v.y);
+}
+
+void launch_contract_full(const double2 *z, int V, int B, int BC, const int *d_rhs_class, const int *d_src_comp,
+                          const int *d_members, int members, double2 *qterm, cudaStream_t st) {
+    long n = (long)members * B;
+    contract_full_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(z, V, B, BC, d_rhs_class, d_src_comp, d_members,
+                                                                      members, qterm);
 }
 
 // q(x_m) = scale * sum_{comp = 0..11} qterm  (fixed order; scale 1/2 for Eq. 16)

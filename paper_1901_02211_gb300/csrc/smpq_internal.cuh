@@ -121,7 +121,8 @@ struct SolveSpec {
     const ShiftParams *shifts; // nullable: shifts and coefficients other than the context's rational
 };
 struct SolveOut {
-    // y = R(H^2) b on the support, FP64, layout [(j/BC)*12 + c][n_sup][BC]
+    // y = R(H^2) b on the support, FP64, layout [j/BC][n_sup][12][BC] (the field
+    // tile layout when the support is the whole lattice)
     double2 *y = nullptr;
     int iterations = 0;
     int reliable_updates = 0;
@@ -165,6 +166,10 @@ void launch_add_c0b(int n_sup, int B, int BC, const int *d_supsite, const int *d
 void launch_contract(const Geom &g, const double *U64, const double2 *y, int n_sup, int B, int BC,
                      const int *d_rhs_class, const int *d_src_comp, const int *d_members, int members, double kappa,
                      double2 *qterm, cudaStream_t st);
+// the same from z = D_W y on the whole lattice (field tile layout), for the
+// full-support ablation
+void launch_contract_full(const double2 *z, int V, int B, int BC, const int *d_rhs_class, const int *d_src_comp,
+                          const int *d_members, int members, double2 *qterm, cudaStream_t st);
 // q(x_m) = 1/2 sum_comp qterm for the listed classes
 void launch_qsum(const double2 *qterm, const int *d_classes, int nc, const int *d_members, int members, double *q_re,
                  double *q_im, double scale, cudaStream_t st);

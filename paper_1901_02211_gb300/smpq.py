@@ -52,6 +52,7 @@ class smpq_options(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("switch_residual", ctypes.c_double),
         ("autotune", ctypes.c_int),
+        ("full_support", ctypes.c_int),
     ]
 
 

@@ -196,6 +196,29 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     assert abs(Q - ref.real[mask].sum()) <= qtol
 
 
+# ----------------------------------------------------------------------------- star support against the whole lattice
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_support_ablation_4x4(S, flux4, zolo4, g5dov4, prec):
+    """The shifted directions kept on every site (full_support) give the same
+    q^SMP(x) as the star support: their recurrences never couple sites, so the
+    restriction is exact (only rounding differs)."""
+    U, dims = flux4["U"], flux4["dims"]
+    colour, n = probing.color_sites(dims, 2, 0)
+    ref = qx.dense_smp_qx(g5dov4, colour)
+    precision = S.SMPQ_FP64 if prec == "fp64" else S.SMPQ_MIXED
+    out = {}
+    for full in (0, 1):
+        with _session(S, precision=precision, full_support=full) as s:
+            s.load_gauge(dims, U)
+            s.set_spectrum(zolo4["a"], zolo4["b"])
+            s.build_sources(2, 0)
+            out[full] = s.compute_qx()[0]
+    assert np.abs(out[1] - out[0]).max() <= 1e-12
+    assert np.abs(out[1] - ref).max() <= 1e-8
+
+
 # ----------------------------------------------------------------------------- host/device buffers, determinism, errors
 
 
