@@ -180,11 +180,11 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(U, dims, a, b, n_classes=1, tol=1e-10):
+def cpu_oracle_sample(U, dims, a, b, n_classes=1, tol=1e-10, rmin=R_MIN):
     """FP64 oracle on `n_classes` colour classes (12 sources each); returns (sites/s, sites, sec, threads)."""
     from oracle import native, probing, qx, zolotarev
     c0, c, q, _ = zolotarev.zolotarev(14, a, b)
-    colour, n = probing.color_sites(dims, R_MIN, MODE)
+    colour, n = probing.color_sites(dims, rmin, MODE)
     classes = list(range(n_classes))
     t0 = time.perf_counter()
     qv, st = qx.smp_qx(U, dims, KAPPA, (c0, c, q), colour, n, tol=tol, colours=classes, batch_colours=n_classes)
@@ -200,16 +200,22 @@ def run_reference(args):
     from oracle import native
     from synth import make_config
     native.build()
-    cfg = make_config(CONFIG)
+    cfg = make_config(args.config)
     U, dims = cfg["U"], cfg["dims"]
-    a, b = _spectrum(CONFIG)
+    try:
+        a, b = _spectrum(args.config)
+    except KeyError:  # no stored spectrum for this workload: ARPACK in the oracle
+        from oracle import spectrum
+        lo, hi = spectrum.h2_extremes(U, dims, KAPPA, tol=1e-8)
+        a, b = 0.98 * lo, 1.02 * hi
     V = int(np.prod(dims))
+    n_cls = args.rmin ** 4
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; bounded steps only
     vals = []
     t_all = 0.0
     for _ in range(args.steps):
-        v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1)
+        v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1, rmin=args.rmin)
         vals.append(v)
         t_all += dt
     value = float(np.median(vals))
@@ -217,10 +223,11 @@ def run_reference(args):
         "impl": "reference", "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * V / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "8^3x16 flux Q=2 noise 0.1, SMP r_min=4 mode 0, 3072 sources x 14 shifts, tol 1e-10",
-                   "sample": "1 colour class (12 sources, 32 sites) per step"},
+        "config": {"workload": _workload_name(args),
+                   "sample": "1 colour class (12 sources, %d sites) per step" % sites},
         "cpu_baseline": {"value": value, "unit": "sites/s", "cores": thr, "kind": "oracle",
-                         "sample": "1 of 256 colour classes per step (12 sources, 32 sites), FP64, tol 1e-10"},
+                         "sample": "1 of %d colour classes per step (12 sources, %d sites), FP64, tol 1e-10"
+                                   % (n_cls, sites)},
         "e2e": {"value": value, "unit": "sites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -491,7 +498,7 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
                 len(cls), n_classes, 12 * len(cls), res[0][2], res[1][2]),
             "max_abs_dq": float(np.abs(res[0][1][mask] - res[1][1][mask]).max())}
         if not args.no_cpu:
-            v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1)
+            v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1, rmin=args.rmin)
             out["cpu_baseline"] = {"value": v, "unit": "sites/s", "cores": thr, "kind": "oracle",
                                    "sample": "1 of %d colour classes (12 sources, %d sites), FP64 tol 1e-10, %.1f s"
                                              % (n_classes, sites, dt)}
