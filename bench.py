@@ -348,6 +348,8 @@ def run_gpu(args):
     else:
         e2e_val = _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws)
     out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream) if rank == 0 else {}
+    if rank == 0 and args.uneven:
+        out["uneven_batch"] = _uneven(args, prec, dev, stream)
     if rank == 0 and not args.no_baselines and args.low_modes > 0 and sub is None:
         q_ref = (q_re + 1j * q_im).cpu().numpy()
         out["low_mode_projection"] = _low_modes(args, dims, U, V, a, b, prec, dev, stream, q_ref)
@@ -430,6 +432,44 @@ def _low_modes(args, dims, U, V, a, b, prec, dev, stream, q_ref):
             "note": "setup (the eigen-solve) is per gauge field and not in value"}
 
 
+def _uneven(args, prec, dev, stream):
+    """The uneven batch: three lattices of different size and scheme (8^3x16 r = 2
+    Q = 1, 12^3x24 r = 4 Q = 2, 16^3x32 r = 4 Q = 3), one context each, issued
+    together through smpq_compute_qx_batch; sites of all three per second."""
+    import torch
+
+    from paper_1901_02211_gb300 import Session, smpq
+    from synth import make_config
+    # fixed batch sizes, so the three concurrent solves share device memory
+    # (the automatic size would give each one 60 % of what is free)
+    lattices = (("flux8x16_b", 2, 192), ("flux12x24", 4, 1536), ("flux16x32_b", 4, 768))
+    sessions, re_, im_, sites, names = [], [], [], 0, []
+    for name, r, blk in lattices:
+        cfg = make_config(name)
+        s4 = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=blk, iters_per_check=10,
+                     use_graphs=1, switch_residual=args.switch, autotune=0)
+        s4.load_gauge(cfg["dims"], cfg["U"])
+        s4.measure_spectrum(300)
+        s4.build_sources(r, MODE)
+        V = int(np.prod(cfg["dims"]))
+        sessions.append(s4)
+        re_.append(torch.zeros(V, dtype=torch.float64, device="cuda"))
+        im_.append(torch.zeros(V, dtype=torch.float64, device="cuda"))
+        sites += V
+        names.append("%s r=%d (V=%d, Q=%d)" % (name, r, V, cfg["Q_closed"]))
+    ctxs = [s4.ctx for s4 in sessions]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Qs, st = smpq.smpq_compute_qx_batch(ctxs, re_, im_)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for s4 in sessions:
+        s4.close()
+    return {"value": sites / dt, "unit": "sites/s", "seconds": dt, "lattices": names, "Q": Qs,
+            "rhs": [x["n_rhs"] for x in st], "iterations": [x["max_iterations"] for x in st],
+            "note": "fixed batches 192 / 1536 / 768, RHS tile 48; GPU Lanczos intervals"}
+
+
 def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
     import torch
 
@@ -510,8 +550,12 @@ def _workload_name(args):
     p = CONFIGS[args.config]
     d = p["dims"]
     n_cls = (args.rmin ** 4)
-    return ("%dx%dx%dx%d flux Q=%d noise %g + gauge transform, SMP r_min=%d mode 0, %d classes x 12 = %d sources "
-            "x 14 shifts, tol 1e-10" % (d[0], d[1], d[2], d[3], p["k"], p["eps"], args.rmin, n_cls, 12 * n_cls))
+    if "stout" in p:
+        links = "Haar seed %d + %d stout steps rho %g" % (p["seed"], p["stout"][1], p["stout"][0])
+    else:
+        links = "flux Q=%d noise %g + gauge transform" % (p["k"], p["eps"])
+    return ("%dx%dx%dx%d %s, SMP r_min=%d mode 0, %d classes x 12 = %d sources x 14 shifts, tol 1e-10"
+            % (d[0], d[1], d[2], d[3], links, args.rmin, n_cls, 12 * n_cls))
 
 
 def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak, peak_kind,
@@ -570,6 +614,8 @@ def main():
     ap.add_argument("--classes", type=int, default=0, help="profiling: only the first N colour classes")
     ap.add_argument("--low-modes", type=int, default=20,
                     help="also time the variant with this many low modes of H_W exact (0: skip)")
+    ap.add_argument("--uneven", action="store_true",
+                    help="also time the uneven batch of three lattices (8^3x16, 12^3x24, 16^3x32) in one call")
     ap.add_argument("--no-autotune", action="store_true",
                     help="widest RHS tile that divides the batch, without timing the candidates")
     args = ap.parse_args()

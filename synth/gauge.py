@@ -194,6 +194,10 @@ CONFIGS = {
     # small variants used by the fast tests
     "flux4_k0": dict(dims=(4, 4, 4, 4), k=0, eps=0.05, seed_noise=1012, seed_gauge=1011),
     "flux4x8": dict(dims=(4, 4, 4, 8), k=1, eps=0.05, seed_noise=1022, seed_gauge=1021),
+    # seeded Haar-random links smoothed by 20 stout steps (rho = 0.1): a rough
+    # background with no closed-form charge, the largest lattice of the set
+    "stout32x64": dict(dims=(32, 32, 32, 64), stout=(0.1, 20), seed=5001),
+    "stout8x16": dict(dims=(8, 8, 8, 16), stout=(0.1, 20), seed=5011),
 }
 
 
@@ -206,6 +210,11 @@ def make_config(name, gauge=True):
     p = CONFIGS[name]
     dims = tuple(p["dims"])
     V = int(np.prod(dims))
+    if "stout" in p:
+        from . import native
+        rho, steps = p["stout"]
+        U = haar_su3(np.random.default_rng(p["seed"]), 4 * V).reshape(V, 4, 3, 3)
+        return dict(dims=dims, U=native.stout(U, dims, rho, steps), Q_closed=None, name=name)
     U = flux_field(dims, p["k"])
     U = apply_noise(U, np.random.default_rng(p["seed_noise"]), p["eps"])
     if gauge:
