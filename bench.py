@@ -588,7 +588,8 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
                                  "frac": v["achieved"] / v["peak"], "avg_launch_ms": v["ms"], "launches": v["n"]}
                              for k, v in kern.items()},
             "solver": {"iterations": st["max_iterations"], "reliable_updates": st["reliable_updates"],
-                       "max_resid": st["max_resid"], "Q": st["Q"], "max_im_q": st["max_im_q"],
+                       "max_resid": st["max_resid"], "Q": st["Q"], "abs_Q_minus_round": st["q_round_dev"],
+                       "max_im_q": st["max_im_q"],
                        "kernel_ms": {k: v["share_ms"] / args.steps for k, v in kern.items()},
                        "kernel_avg_launch_ms": {k: v["ms"] for k, v in kern.items()}},
         }

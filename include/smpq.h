@@ -103,6 +103,7 @@ typedef struct {
     double update_hi_ms;
     long long update_hi_launches;
     int rhs_tile;           /* RHS tile width the solves used (autotuned or fixed) */
+    double q_round_dev;     /* |Q - round(Q)| of the processed sites (the charge is an integer) */
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,

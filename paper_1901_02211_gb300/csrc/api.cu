@@ -359,6 +359,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->max_resid = worst;
         stats->max_im_q = tot[1];
         stats->Q = tot[0];
+        stats->q_round_dev = std::fabs(tot[0] - std::nearbyint(tot[0]));
         stats->solve_ms = solve_ms;
         stats->total_ms = tms;
         stats->kernel_launches = ctx->launches;

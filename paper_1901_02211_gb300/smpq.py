@@ -79,6 +79,7 @@ class smpq_stats(ctypes.Structure):
         ("update_hi_ms", ctypes.c_double),
         ("update_hi_launches", ctypes.c_longlong),
         ("rhs_tile", ctypes.c_int),
+        ("q_round_dev", ctypes.c_double),
     ]
 
     def as_dict(self):
