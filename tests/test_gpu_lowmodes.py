@@ -140,3 +140,24 @@ def test_projected_qx_8x16_sampled(S):
         it, np.abs(ev - lam).max(), err, st["max_iterations"]))
     assert np.abs(ev - lam).max() <= 1e-9
     assert err <= 1e-8
+
+
+def test_low_modes_errors(S, flux4, zolo4):
+    """Out-of-order and invalid requests return status codes, not faults."""
+    from paper_1901_02211_gb300 import Session
+    U, dims = flux4["U"], flux4["dims"]
+    with Session(precision=S.SMPQ_FP64) as s:
+        s.load_gauge(dims, U)
+        with pytest.raises(S.SmpqError) as e:
+            s.low_modes(4)  # no spectral interval yet
+        assert e.value.code == S.SMPQ_ESTATE
+        s.set_spectrum(zolo4["a"], zolo4["b"])
+        for k, block in ((0, 0), (44, 0), (4, 20), (4, 60)):
+            with pytest.raises(S.SmpqError) as e:
+                s.low_modes(k, block=block)
+            assert e.value.code == S.SMPQ_EINVAL
+        assert s.get_low_modes()[0].size == 0
+        ev, res, it = s.low_modes(4, block=12, tol=1e-10)
+        assert ev.size == 5 and res.max() <= 1e-10
+        s.load_gauge(dims, U)  # a new gauge field drops the modes
+        assert s.get_low_modes()[0].size == 0
