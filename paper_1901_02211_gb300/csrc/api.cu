@@ -159,7 +159,7 @@ int tune_bc(smpq_ctx *ctx, int B, int prec) {
 size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
     size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16) : (prec == SMPQ_MIXED ? 3 * 16 + 3 * 8 : 3 * 16);
     size_t full = (size_t)ctx->V * 12 * per;
-    size_t eb = prec == SMPQ_FP32 ? 8 : 16;
+    size_t eb = prec == SMPQ_FP32 ? 8 : (prec == SMPQ_MIXED ? 16 + 8 : 16); // MIXED: FP64 and FP32 copies
     size_t sup = (size_t)n_sup * 12 * (npoles * eb + 16);
     return full + sup;
 }

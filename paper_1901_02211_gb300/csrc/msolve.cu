@@ -596,6 +596,19 @@ __global__ void k_to_fp32(const df64c *__restrict__ in, float2 *__restrict__ out
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
+__global__ void k_d2f(const double2 *__restrict__ in, float2 *__restrict__ out, size_t n) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// The second phase of SMPQ_MIXED keeps the shifted directions in FP32: their
+// updates after the switch only add terms of the size of the (already small)
+// residual, like the FP32 base vectors.  SMPQ_PS64 keeps them in FP64.
+#ifdef SMPQ_PS64
+constexpr bool ps32_phase2 = false;
+#else
+constexpr bool ps32_phase2 = true;
+#endif
 
 // One multi-shift solve of B right-hand sides in tiles of BC columns.  The
 // solve runs in one or two phases:
@@ -603,7 +616,8 @@ __global__ void k_to_fp32(const df64c *__restrict__ in, float2 *__restrict__ out
 //   SMPQ_FP32  : FP32 iterations with FP64 reliable updates of the base system;
 //   SMPQ_MIXED : FP64 iterations until every right-hand side has
 //                ||r|| <= theta ||b||, then FP32 iterations without residual
-//                replacement; the shifted directions and y stay FP64 throughout.
+//                replacement; the shifted directions are FP64 in the first
+//                phase and FP32 in the second, y stays FP64 throughout.
 // Scalars, reductions and y are FP64 in every mode.
 template <int BC> struct Solve {
     smpq_ctx *ctx;
@@ -891,16 +905,27 @@ template <int BC> struct Solve {
             rc = S.template phase<df64, double>(p, t, r, nullptr, nullptr, nullptr, ps, true, false, theta * theta, 0,
                                                 max_iter);
             if (rc) return rc;
-            // phase 2: FP32 vectors and D_W from the phase-1 state, shifted vectors stay FP64
-            if ((rc = ensure(ctx, ws[W_XLO], 3 * nf * sizeof(float2)))) return rc;
-            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf;
+            // phase 2: FP32 vectors and D_W from the phase-1 state; the shifted
+            // directions in FP32 too (ps32_phase2), y stays FP64
+            const size_t nps = shifts ? (size_t)sp.n * S.nsupf : 0;
+            const bool ps32 = ps32_phase2 && shifts;
+            if ((rc = ensure(ctx, ws[W_XLO], 3 * nf * sizeof(float2) + (ps32 ? nps * sizeof(float2) : 0)))) return rc;
+            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf, *ps32p = r32 + nf;
             const unsigned nb = (unsigned)((nf + 255) / 256);
             k_to_fp32<<<nb, 256, 0, S.st>>>(p, p32, nf);
             k_to_fp32<<<nb, 256, 0, S.st>>>(r, r32, nf);
             ctx->launches += 2;
+            if (ps32) {
+                k_d2f<<<(unsigned)((nps + 255) / 256), 256, 0, S.st>>>(ps, ps32p, nps);
+                ctx->launches += 1;
+            }
             cudaMemcpyAsync(S.hflags, S.sc.flags, sizeof(int), cudaMemcpyDeviceToHost, S.st);
             cudaStreamSynchronize(S.st);
-            if (S.hflags[0] > 0) {
+            if (S.hflags[0] > 0 && ps32) {
+                rc = S.template phase<float, float>(p32, t32, r32, nullptr, nullptr, nullptr, ps32p, false, false, 0.0,
+                                                    0, max_iter);
+                if (rc) return rc;
+            } else if (S.hflags[0] > 0) {
                 rc = S.template phase<float, double>(p32, t32, r32, nullptr, nullptr, nullptr, ps, false, false, 0.0, 0,
                                                      max_iter);
                 if (rc) return rc;
