@@ -261,6 +261,14 @@ def run_gpu(args):
         spectrum_note = "GPU Lanczos (smpq_measure_spectrum, 300 steps), widened 0.98/1.02"
     prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
 
+    if args.dslash_only:  # profiling entry: the stand-alone D_W formats alone, no solve
+        s = Session(device=dev, stream=stream)
+        s.load_gauge(dims, U)
+        print(json.dumps({"workload": "%dx%dx%dx%d stand-alone D_W" % tuple(dims),
+                          "dslash": _dslash_formats(s, V, args.dslash_columns)}), flush=True)
+        s.close()
+        return
+
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
                 use_graphs=1, profile=1, switch_residual=args.switch, autotune=0 if args.no_autotune else 1)
     s.load_gauge(dims, U)
@@ -354,12 +362,30 @@ def run_gpu(args):
         q_ref = (q_re + 1j * q_im).cpu().numpy()
         out["low_mode_projection"] = _low_modes(args, dims, U, V, a, b, prec, dev, stream, q_ref)
     out["spectrum"] = {"lmin2": a, "lmax2": b, "source": spectrum_note}
+    if rank == 0 and not args.no_dslash:
+        out["dslash"] = _dslash_formats(s, V, B)
     if rank == 0:
         _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak,
                 peak_kind, traffic, stats, out, sub)
     s.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _dslash_formats(s, V, B, reps=20):
+    """Stand-alone D_W (smpq_time_dslash) on the workload's B columns in every
+    storage format: CUDA-event time per launch on the context's stream and
+    algorithmic bytes (spinor in + out per site and column, links once) against
+    the measured HBM bandwidth."""
+    from paper_1901_02211_gb300 import smpq
+    peak, kind = _peaks()
+    res = {"columns": B, "reps": reps, "peak": peak, "peak_source": kind, "unit": "GB/s"}
+    for name, prec in (("fp16n_recon12", smpq.SMPQ_FP16N), ("bf16n_recon12", smpq.SMPQ_BF16N),
+                       ("fp32", smpq.SMPQ_FP32), ("fp64", smpq.SMPQ_FP64)):
+        ms, nbytes = smpq.smpq_time_dslash(s.ctx, B, False, prec, reps)
+        gbs = nbytes / (ms / 1000.0) / 1e9
+        res[name] = {"avg_launch_ms": ms, "algorithmic_bytes": nbytes, "achieved": gbs, "frac": gbs / peak}
+    return res
 
 
 def _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws):
@@ -571,7 +597,7 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
             "config": {"workload": _workload_name(args),
                        "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
                                      smpq.SMPQ_FP64: "FP64",
-                                     smpq.SMPQ_MIXED: "FP64 until ||r|| < %g ||b||, then FP32; FP64 shifted vectors"
+                                     smpq.SMPQ_MIXED: "FP64-accurate until ||r|| < %g ||b||, then FP32 (shifted vectors too)"
                                      % args.switch}[prec],
                        "batch": B, "rhs_tile": int(st.get("rhs_tile", 0)), "l2": "inputs larger than L2 (each solver vector %.1f GB)"
                        % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
@@ -609,6 +635,11 @@ def main():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dslash", action="store_true",
+                    help="skip the stand-alone D_W timing in every storage format")
+    ap.add_argument("--dslash-only", action="store_true",
+                    help="time only the stand-alone D_W in every storage format (no solve)")
+    ap.add_argument("--dslash-columns", type=int, default=3072, help="--dslash-only: right-hand sides")
     ap.add_argument("--switch", type=float, default=7e-3, help="SMPQ_MIXED: FP64 -> FP32 switch residual")
     ap.add_argument("--config", default=CONFIG, help="synthetic configuration (synth.CONFIGS)")
     ap.add_argument("--rmin", type=int, default=R_MIN, help="SMP r (Normal mode)")

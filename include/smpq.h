@@ -55,9 +55,15 @@ typedef enum {
 typedef enum {
     SMPQ_FP64 = 0,  /* vectors, dslash and updates in FP64 (reference path) */
     SMPQ_FP32 = 1,  /* FP32 vectors and dslash with FP64 reliable updates, FP64 scalars */
-    SMPQ_MIXED = 2  /* FP64-accurate iterations (float-float arithmetic on FP64-sized data)
+    SMPQ_MIXED = 2, /* FP64-accurate iterations (float-float arithmetic on FP64-sized data)
                        until ||r|| <= switch_residual ||b||, then FP32 without residual
-                       replacement; shifted directions and y in FP64 throughout */
+                       replacement; shifted directions in FP64 in the first phase and
+                       FP32 in the second, y in FP64 throughout */
+    SMPQ_FP16N = 3, /* stand-alone D_W only (smpq_dslash, smpq_time_dslash): spinor components
+                       stored in FP16 and scaled by one FP32 norm per site and right-hand
+                       side, links stored as FP16 rows 0 and 1 (reconstruct-12), FP32
+                       arithmetic.  The solver options reject it (SMPQ_EINVAL). */
+    SMPQ_BF16N = 4  /* as SMPQ_FP16N with BF16 storage */
 } smpq_precision;
 
 typedef struct {
@@ -185,10 +191,26 @@ int smpq_build_sources(smpq_ctx *ctx, int r, int mode, int *n_classes);
  * validation as smpq_build_sources. */
 int smpq_colour_sites(const int dims[4], int r, int mode, int *colour, int *n_classes);
 
-/* D_W (or gamma_5 D_W gamma_5 = D_W^dag if dagger) applied to B fields,
- * computed in `precision` (FP64 or FP32 kernel; in/out FP64 at the ABI).
- * in/out: double[V][4][3][B][2], host or device (on_device). */
+/* D_W (or gamma_5 D_W gamma_5 = D_W^dag if dagger) applied to B fields
+ * (Sec. 2.1, Eq. 3), computed in `precision`: SMPQ_FP64 or SMPQ_FP32 kernels,
+ * or SMPQ_FP16N / SMPQ_BF16N (the input is rounded to the half format on the
+ * device, the result leaves the kernel in that format and is widened back to
+ * FP64).  in/out FP64 at the ABI: double[V][4][3][B][2], host or device
+ * (on_device).  SMPQ_EINVAL for SMPQ_MIXED or an unknown precision. */
 int smpq_dslash(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision, int on_device);
+
+/* Average device time of one stand-alone D_W launch (the kernel behind
+ * smpq_dslash, Sec. 2.1, Eq. 3) on B right-hand sides held in `precision`
+ * (SMPQ_FP64, SMPQ_FP32, SMPQ_FP16N or SMPQ_BF16N), in the RHS tile the
+ * library picks for B.  The input and output fields are scratch in the
+ * context's workspace, set once to the byte 0x3F (finite values in every
+ * format; the values do not change the work).  Two untimed launches, then
+ * `reps` (>= 1) launches back to back on the context's stream between two
+ * CUDA events.  *ms (nullable): average milliseconds per launch; *bytes
+ * (nullable): algorithmic bytes of one launch, V * B * (spinor bytes read +
+ * written per site and rhs) + V * 4 * (bytes per stored link).  Needs a gauge
+ * field (SMPQ_ESTATE otherwise). */
+int smpq_time_dslash(smpq_ctx *ctx, int B, int dagger, int precision, int reps, double *ms, double *bytes);
 
 /* Allocation-free variant of smpq_dslash (the paper has no counterpart; this
  * is a service for callers of this library).  Some callers cannot call

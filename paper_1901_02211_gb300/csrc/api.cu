@@ -445,6 +445,8 @@ int smpq_destroy(smpq_ctx *ctx) {
         release(ctx->U64);
         release(ctx->U32);
         release(ctx->Udf);
+        release(ctx->Uh16);
+        release(ctx->Ub16);
         release(ctx->d_colour);
         release(ctx->d_members);
         lowmodes_clear(ctx);
@@ -489,6 +491,8 @@ int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int o
     if ((rc = ensure(ctx, ctx->U64, (size_t)V * 36 * sizeof(double2)))) return rc;
     if ((rc = ensure(ctx, ctx->U32, (size_t)V * 36 * sizeof(float2)))) return rc;
     if ((rc = ensure(ctx, ctx->Udf, (size_t)V * 36 * sizeof(df64c)))) return rc;
+    if ((rc = ensure(ctx, ctx->Uh16, (size_t)V * 24 * 4))) return rc;
+    if ((rc = ensure(ctx, ctx->Ub16, (size_t)V * 24 * 4))) return rc;
     const double *src = links;
     if (!on_device) {
         if ((rc = ensure(ctx, ctx->ws[W_MISC], (size_t)V * 36 * sizeof(double2)))) return rc;
@@ -500,6 +504,7 @@ int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int o
     ctx->V = (int)V;
     set_geom(ctx);
     launch_pack_links(src, (double *)ctx->U64.p, (float *)ctx->U32.p, ctx->Udf.p, (int)V, ctx->stream);
+    launch_pack_links12(src, ctx->Uh16.p, ctx->Ub16.p, (int)V, ctx->stream);
     if ((rc = ensure(ctx, ctx->ws[W_PART], 64))) return rc;
     double *derr = (double *)ctx->ws[W_PART].p;
     launch_su3_check((const double *)ctx->U64.p, (int)V, derr, ctx->stream);
@@ -652,40 +657,104 @@ int smpq_build_sources(smpq_ctx *ctx, int r, int mode, int *n_classes) {
     return SMPQ_OK;
 }
 
+static bool is_half(int precision) { return precision == SMPQ_FP16N || precision == SMPQ_BF16N; }
+
+static const void *dslash_links(const smpq_ctx *ctx, int precision) {
+    switch (precision) {
+    case SMPQ_FP64: return ctx->U64.p;
+    case SMPQ_FP32: return ctx->U32.p;
+    case SMPQ_FP16N: return ctx->Uh16.p;
+    default: return ctx->Ub16.p;
+    }
+}
+
+// bytes of one field of B columns in the stand-alone D_W's format, rounded up
+// to 256 so that a second field can follow it
+static size_t dslash_field_bytes(const smpq_ctx *ctx, int precision, int B) {
+    const size_t n = (size_t)ctx->V * 12 * B;
+    const size_t b = is_half(precision) ? half_field_bytes(ctx->V, B) : n * (precision == SMPQ_FP64 ? 16 : 8);
+    return (b + 255) / 256 * 256;
+}
+
 int smpq_dslash(smpq_ctx *ctx, const double *in, double *out, int B, int dagger, int precision, int on_device) {
     int rc = check_ctx(ctx, true, false, false);
     if (rc) return rc;
     if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad dslash arguments");
-    if (precision != SMPQ_FP64 && precision != SMPQ_FP32) return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    if (precision != SMPQ_FP64 && precision != SMPQ_FP32 && !is_half(precision))
+        return set_err(ctx, SMPQ_EINVAL, "bad precision");
     DeviceGuard dg(ctx->device);
     StreamEntry se(ctx, ctx->user_stream);
     cudaStream_t st = ctx->stream;
     const size_t n = (size_t)ctx->V * 12 * B;
-    const size_t esz = precision == SMPQ_FP64 ? 16 : 8;
-    if ((rc = ensure(ctx, ctx->ws[W_SRC], n * 16 + 2 * n * esz))) return rc;
+    const size_t fb = dslash_field_bytes(ctx, precision, B);
+    if ((rc = ensure(ctx, ctx->ws[W_SRC], n * 16 + 2 * fb))) return rc;
     double *abi = (double *)ctx->ws[W_SRC].p;
-    char *tin = (char *)ctx->ws[W_SRC].p + n * 16, *tout = tin + n * esz;
+    char *tin = (char *)ctx->ws[W_SRC].p + n * 16, *tout = tin + fb;
     const double *din = in;
     if (!on_device) {
         cudaMemcpyAsync(abi, in, n * 16, cudaMemcpyHostToDevice, st);
         din = abi;
     }
     const int BC = 1;
-    const void *U = precision == SMPQ_FP64 ? ctx->U64.p : ctx->U32.p;
+    const void *U = dslash_links(ctx, precision);
     double *dout = on_device ? out : abi;
     if (precision == SMPQ_FP64) {
         launch_to_tiled<double>(din, tin, ctx->V, B, BC, st);
         launch_dslash<double>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
         launch_from_tiled<double>(tout, dout, ctx->V, B, BC, st);
-    } else {
+    } else if (precision == SMPQ_FP32) {
         launch_to_tiled<float>(din, tin, ctx->V, B, BC, st);
         launch_dslash<float>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
         launch_from_tiled<float>(tout, dout, ctx->V, B, BC, st);
+    } else {
+        launch_to_half(precision, din, tin, ctx->V, B, st);
+        launch_dslash_half(precision, ctx->geom, U, tin, tout, B, dagger, ctx->opt.kappa, st);
+        launch_from_half(precision, tout, dout, ctx->V, B, st);
     }
     if (!on_device) cudaMemcpyAsync(out, abi, n * 16, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "dslash");
     return cuda_check(ctx, cudaGetLastError(), "dslash launch");
+}
+
+int smpq_time_dslash(smpq_ctx *ctx, int B, int dagger, int precision, int reps, double *ms, double *bytes) {
+    int rc = check_ctx(ctx, true, false, false);
+    if (rc) return rc;
+    if (B < 1 || reps < 1) return set_err(ctx, SMPQ_EINVAL, "bad time_dslash arguments");
+    if (precision != SMPQ_FP64 && precision != SMPQ_FP32 && !is_half(precision))
+        return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    DeviceGuard dg(ctx->device);
+    StreamEntry se(ctx, ctx->user_stream);
+    cudaStream_t st = ctx->stream;
+    const size_t fb = dslash_field_bytes(ctx, precision, B);
+    if ((rc = ensure(ctx, ctx->ws[W_SRC], 2 * fb))) return rc;
+    char *tin = (char *)ctx->ws[W_SRC].p, *tout = tin + fb;
+    cudaMemsetAsync(tin, 0x3F, 2 * fb, st);
+    // the FP64 / FP32 tile: the widest of 48, 12 and 1 that divides B
+    const int BC = B % 48 == 0 ? 48 : (B % 12 == 0 ? 12 : 1);
+    const void *U = dslash_links(ctx, precision);
+    auto launch = [&]() {
+        if (precision == SMPQ_FP64) launch_dslash<double>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+        else if (precision == SMPQ_FP32) launch_dslash<float>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+        else launch_dslash_half(precision, ctx->geom, U, tin, tout, B, dagger, ctx->opt.kappa, st);
+    };
+    launch();
+    launch();
+    cudaEventRecord(ctx->ev1, st);
+    for (int k = 0; k < reps; ++k) launch();
+    cudaEventRecord(ctx->ev2, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "time_dslash");
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "time_dslash launch"))) return rc;
+    float t = 0;
+    if ((e = cudaEventElapsedTime(&t, ctx->ev1, ctx->ev2)) != cudaSuccess) return cuda_check(ctx, e, "time_dslash events");
+    ctx->launches += reps + 2;
+    const double V = ctx->V;
+    const double spinor = precision == SMPQ_FP64 ? 192 : (precision == SMPQ_FP32 ? 96 : 52); // per site and rhs
+    const double link = precision == SMPQ_FP64 ? 144 : (precision == SMPQ_FP32 ? 72 : 24);   // per stored link
+    if (ms) *ms = (double)t / reps;
+    if (bytes) *bytes = V * B * 2 * spinor + V * 4 * link;
+    return SMPQ_OK;
 }
 
 int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_device) {

@@ -1,0 +1,504 @@
+// Half-precision storage for the stand-alone Wilson dslash D_W (Sec. 2.1,
+// around Eq. 3):
+//   - spinor components in FP16 or BF16, scaled by one FP32 norm per site and
+//     right-hand side (the largest |re| or |im| of its 12 components), so the
+//     stored values lie in [-1, 1];
+//   - links stored as their first two rows (reconstruct-12): for U in SU(3)
+//     the third row is the complex conjugate of the cross product of the
+//     first two, recomputed in FP32 at every use;
+//   - arithmetic and accumulation in FP32.
+// These formats serve smpq_dslash and smpq_time_dslash only: the multi-shift
+// solver does not iterate in them (a half-precision Krylov basis would leave
+// every shifted system with an error floor near the format's unit roundoff).
+//
+// Layouts (RHS tiles of BC columns, as the FP32 and FP64 fields):
+//   components [j / BC][V][12][BC] of H2 (one complex number as two halves)
+//   norms      [j / BC][V][BC] float; component value = norm * stored value
+//   links      [(mu * V + s) * 6 + row * 3 + col], rows 0 and 1
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <string.h>
+
+#include "smpq_internal.cuh"
+#include "wilson.cuh"
+
+struct H16 {
+    typedef __half2 h2;
+    static __device__ __forceinline__ float2 f2(h2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ h2 pack(float2 v) { return __float22half2_rn(v); }
+};
+struct B16 {
+    typedef __nv_bfloat162 h2;
+    static __device__ __forceinline__ float2 f2(h2 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ h2 pack(float2 v) { return __float22bfloat162_rn(v); }
+};
+
+template <typename HT> __device__ __forceinline__ float2 f2_bits(unsigned w) {
+    typename HT::h2 v;
+    memcpy(&v, &w, 4);
+    return HT::f2(v);
+}
+template <typename HT> __device__ __forceinline__ unsigned bits_f2(float2 v) {
+    typename HT::h2 h = HT::pack(v);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+}
+
+// NR adjacent columns of one component (NR = 2: one 8-byte access)
+template <typename HT, int NR>
+__device__ __forceinline__ void ld_cols(const typename HT::h2 *__restrict__ p, float2 v[NR]) {
+    if constexpr (NR == 2) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        v[0] = f2_bits<HT>(q.x);
+        v[1] = f2_bits<HT>(q.y);
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = HT::f2(p[r]);
+    }
+}
+template <typename HT, int NR> __device__ __forceinline__ void st_cols(typename HT::h2 *p, const float2 v[NR]) {
+    if constexpr (NR == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(bits_f2<HT>(v[0]), bits_f2<HT>(v[1]));
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) p[r] = HT::pack(v[r]);
+    }
+}
+template <int NR> __device__ __forceinline__ void ld_norms(const float *__restrict__ p, float v[NR]) {
+    if constexpr (NR == 2) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = p[r];
+    }
+}
+
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// The link of (mu, s) as a full 3x3 matrix: rows 0 and 1 from memory (24 bytes,
+// three 8-byte loads), row 2 = conj(row 0 x row 1).
+template <typename HT>
+__device__ __forceinline__ void load_link12(const typename HT::h2 *__restrict__ U, size_t idx, float2 m[3][3]) {
+    const uint2 *p = reinterpret_cast<const uint2 *>(U + idx * 6);
+    const uint2 a = p[0], b = p[1], c = p[2];
+    m[0][0] = f2_bits<HT>(a.x);
+    m[0][1] = f2_bits<HT>(a.y);
+    m[0][2] = f2_bits<HT>(b.x);
+    m[1][0] = f2_bits<HT>(b.y);
+    m[1][1] = f2_bits<HT>(c.x);
+    m[1][2] = f2_bits<HT>(c.y);
+    m[2][0] = conjf2(csub(cmul(m[0][1], m[1][2]), cmul(m[0][2], m[1][1])));
+    m[2][1] = conjf2(csub(cmul(m[0][2], m[1][0]), cmul(m[0][0], m[1][2])));
+    m[2][2] = conjf2(csub(cmul(m[0][0], m[1][1]), cmul(m[0][1], m[1][0])));
+}
+
+// One hop, acc += f (1 + SG g_mu) W psi(nb) for NR columns, W = U(ls) or
+// U(ls)^dag (BACK); f = the neighbour's norm, negated across an antiperiodic
+// boundary (flip).  Same projection as the FP32 hop (S_mu on the lower half).
+template <typename HT, int MU, int SG, bool BACK, int BC, int NR>
+__device__ __forceinline__ void hop_half(const typename HT::h2 *__restrict__ U, const typename HT::h2 *__restrict__ in,
+                                         const float *__restrict__ nrm, int Vl, int nb, int ls, bool flip,
+                                         float2 acc[12][NR]) {
+    const typename HT::h2 *q = in + (size_t)nb * (12 * BC);
+    float f[NR];
+    ld_norms<NR>(nrm + (size_t)nb * BC, f);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        if (flip) f[r] = -f[r];
+    float2 h[2][3][NR];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float2 p0[NR], p1[NR], p2[NR], p3[NR];
+        ld_cols<HT, NR>(q + a * BC, p0);
+        ld_cols<HT, NR>(q + (3 + a) * BC, p1);
+        ld_cols<HT, NR>(q + (6 + a) * BC, p2);
+        ld_cols<HT, NR>(q + (9 + a) * BC, p3);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float2 s0, s1;
+            s_apply<MU>(p2[r], p3[r], s0, s1);
+            if (SG > 0) { h[0][a][r] = cadd(p0[r], s0); h[1][a][r] = cadd(p1[r], s1); }
+            else { h[0][a][r] = csub(p0[r], s0); h[1][a][r] = csub(p1[r], s1); }
+        }
+    }
+    float2 m[3][3];
+    load_link12<HT>(U, (size_t)MU * Vl + ls, m);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (BACK) { // (U^dag)_{ab} = conj(U_{ba})
+                    w0 = cfmac(m[b][a], h[0][b][r], w0);
+                    w1 = cfmac(m[b][a], h[1][b][r], w1);
+                } else {
+                    w0 = cfma(m[a][b], h[0][b][r], w0);
+                    w1 = cfma(m[a][b], h[1][b][r], w1);
+                }
+            }
+            w0 = cscale(f[r], w0);
+            w1 = cscale(f[r], w1);
+            acc[a][r] = cadd(acc[a][r], w0);
+            acc[3 + a][r] = cadd(acc[3 + a][r], w1);
+            float2 l0, l1;
+            sdag_apply<MU>(w0, w1, l0, l1);
+            if (SG > 0) { acc[6 + a][r] = cadd(acc[6 + a][r], l0); acc[9 + a][r] = cadd(acc[9 + a][r], l1); }
+            else { acc[6 + a][r] = csub(acc[6 + a][r], l0); acc[9 + a][r] = csub(acc[9 + a][r], l1); }
+        }
+    }
+}
+
+template <typename HT, int MU, bool DAG, int BC, int NR>
+__device__ __forceinline__ void hop_dir_half(const Geom &g, const SiteCoords &xc, const typename HT::h2 *U,
+                                             const typename HT::h2 *in, const float *nrm, int s,
+                                             float2 acc[12][NR]) {
+    const int n = g.n[MU], st = g.stride[MU], c = xc.x[MU];
+    const bool top = c == n - 1, bot = c == 0;
+    const int nf = top ? s - (n - 1) * st : s + st;
+    const int nbk = bot ? s + (n - 1) * st : s - st;
+    hop_half<HT, MU, DAG ? +1 : -1, false, BC, NR>(U, in, nrm, g.V, nf, s, top && g.bcf[MU] < 0, acc);
+    hop_half<HT, MU, DAG ? -1 : +1, true, BC, NR>(U, in, nrm, g.V, nbk, nbk, bot && g.bcf[MU] < 0, acc);
+}
+
+// out = D_W in (DAG: D_W^dag), both in the half format; the output norm is
+// taken from the FP32 result before it is rounded to the half format.
+// (one column per thread fits 80 registers, three 256-thread blocks per SM;
+// the two-column form of this scalar kernel is held to two blocks per SM)
+template <typename HT, bool DAG, int BC, int NR>
+__global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, NR == 1 ? 3 : 2)
+    dslash_half_kernel(Geom g, const typename HT::h2 *__restrict__ U, const typename HT::h2 *__restrict__ in,
+                       const float *__restrict__ nin, typename HT::h2 *__restrict__ out, float *__restrict__ nout,
+                       float kappa) {
+    typedef TileMap<BC, NR> TM;
+    const int s = blockIdx.x * TM::SPB + threadIdx.x / TM::TPS;
+    const int jj = (threadIdx.x % TM::TPS) * NR;
+    if (s >= g.V) return;
+    const size_t fb = (size_t)blockIdx.y * 12 * g.V * BC + jj, nbase = (size_t)blockIdx.y * g.V * BC + jj;
+    const typename HT::h2 *pin = in + fb;
+    const float *pn = nin + nbase;
+    float2 acc[12][NR];
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[c][r] = make_float2(0.f, 0.f);
+    const SiteCoords xc(g, s);
+    hop_dir_half<HT, 0, DAG, BC, NR>(g, xc, U, pin, pn, s, acc);
+    hop_dir_half<HT, 1, DAG, BC, NR>(g, xc, U, pin, pn, s, acc);
+    hop_dir_half<HT, 2, DAG, BC, NR>(g, xc, U, pin, pn, s, acc);
+    hop_dir_half<HT, 3, DAG, BC, NR>(g, xc, U, pin, pn, s, acc);
+    float ns[NR], mx[NR];
+    ld_norms<NR>(pn + (size_t)s * BC, ns);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) mx[r] = 0.f;
+    const typename HT::h2 *ps = pin + (size_t)s * 12 * BC;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        float2 v[NR];
+        ld_cols<HT, NR>(ps + c * BC, v);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float2 o;
+            o.x = fmaf(ns[r], v[r].x, -kappa * acc[c][r].x);
+            o.y = fmaf(ns[r], v[r].y, -kappa * acc[c][r].y);
+            acc[c][r] = o;
+            mx[r] = fmaxf(mx[r], fmaxf(fabsf(o.x), fabsf(o.y)));
+        }
+    }
+    float inv[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) inv[r] = mx[r] > 0.f ? 1.f / mx[r] : 0.f;
+    typename HT::h2 *po = out + fb + (size_t)s * 12 * BC;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        float2 v[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = cscale(inv[r], acc[c][r]);
+        st_cols<HT, NR>(po + c * BC, v);
+    }
+    float *pno = nout + nbase + (size_t)s * BC;
+    if constexpr (NR == 2) *reinterpret_cast<float2 *>(pno) = make_float2(mx[0], mx[1]);
+    else
+#pragma unroll
+        for (int r = 0; r < NR; ++r) pno[r] = mx[r];
+}
+
+// ---------------------------------------------------------------- two columns in packed lanes
+// Two adjacent right-hand-side columns per thread, held as the two lanes of
+// packed FP32 instructions (FFMA2, FADD2, FMUL2 on sm_100 and later): every
+// complex value is a pair of float2, .r = (re col 0, re col 1) and .i = (im
+// col 0, im col 1).  Each arithmetic instruction then serves both columns, and
+// a link (loaded and reconstructed once) serves both.
+struct c2 {
+    float2 r, i;
+};
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+template <typename HT> __device__ __forceinline__ c2 ld_c2(const typename HT::h2 *__restrict__ p) {
+    const uint2 q = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = f2_bits<HT>(q.x), b = f2_bits<HT>(q.y);
+    return {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+}
+template <typename HT> __device__ __forceinline__ void st_c2(typename HT::h2 *p, float2 r, float2 i) {
+    *reinterpret_cast<uint2 *>(p) =
+        make_uint2(bits_f2<HT>(make_float2(r.x, i.x)), bits_f2<HT>(make_float2(r.y, i.y)));
+}
+
+// a + g * u * v for a unit u: K = 0: 1, 1: -1, 2: i, 3: -i
+template <int K> __device__ __forceinline__ c2 fma_unit(float g, c2 v, c2 a) {
+    if (K == 0) return {__ffma2_rn(bc2(g), v.r, a.r), __ffma2_rn(bc2(g), v.i, a.i)};
+    if (K == 1) return {__ffma2_rn(bc2(-g), v.r, a.r), __ffma2_rn(bc2(-g), v.i, a.i)};
+    if (K == 2) return {__ffma2_rn(bc2(-g), v.i, a.r), __ffma2_rn(bc2(g), v.r, a.i)};
+    return {__ffma2_rn(bc2(g), v.i, a.r), __ffma2_rn(bc2(-g), v.r, a.i)};
+}
+// S_mu (l0, l1) = (u0 l_{J0}, u1 l_{J1}) and S_mu^dag (w0, w1) = (v0 w_{D0}, v1 w_{D1});
+// unit codes as in fma_unit
+template <int MU> struct SPerm {
+    static constexpr int J0 = (MU == 0 || MU == 1) ? 1 : 0, J1 = 1 - J0;
+    static constexpr int U0 = MU == 0 ? 3 : MU == 1 ? 1 : MU == 2 ? 3 : 0;
+    static constexpr int U1 = MU == 0 ? 3 : MU == 1 ? 0 : MU == 2 ? 2 : 0;
+    static constexpr int D0 = J0, D1 = J1;
+    static constexpr int V0 = MU == 0 ? 2 : MU == 1 ? 0 : MU == 2 ? 2 : 0;
+    static constexpr int V1 = MU == 0 ? 2 : MU == 1 ? 1 : MU == 2 ? 3 : 0;
+};
+
+template <typename HT, int MU, int SG, bool BACK, int BC>
+__device__ __forceinline__ void hop_half_c2(const typename HT::h2 *__restrict__ U, const typename HT::h2 *__restrict__ in,
+                                            const float *__restrict__ nrm, int Vl, int nb, int ls, bool flip,
+                                            c2 acc[12]) {
+    typedef SPerm<MU> P;
+    const typename HT::h2 *q = in + (size_t)nb * (12 * BC);
+    float2 f = *reinterpret_cast<const float2 *>(nrm + (size_t)nb * BC);
+    if (flip) f = make_float2(-f.x, -f.y);
+    const float g = (float)SG;
+    c2 h0[3], h1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const c2 p0 = ld_c2<HT>(q + a * BC), p1 = ld_c2<HT>(q + (3 + a) * BC);
+        const c2 p2 = ld_c2<HT>(q + (6 + a) * BC), p3 = ld_c2<HT>(q + (9 + a) * BC);
+        h0[a] = fma_unit<P::U0>(g, P::J0 ? p3 : p2, p0);
+        h1[a] = fma_unit<P::U1>(g, P::J1 ? p3 : p2, p1);
+    }
+    float2 m[3][3];
+    load_link12<HT>(U, (size_t)MU * Vl + ls, m);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c2 w0 = {bc2(0.f), bc2(0.f)}, w1 = w0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 e = BACK ? m[b][a] : m[a][b]; // W_ab = conj(U_ba) for BACK
+            const float2 ex = bc2(e.x), ey = bc2(BACK ? -e.y : e.y), ney = bc2(BACK ? e.y : -e.y);
+            w0.r = __ffma2_rn(ex, h0[b].r, __ffma2_rn(ney, h0[b].i, w0.r));
+            w0.i = __ffma2_rn(ex, h0[b].i, __ffma2_rn(ey, h0[b].r, w0.i));
+            w1.r = __ffma2_rn(ex, h1[b].r, __ffma2_rn(ney, h1[b].i, w1.r));
+            w1.i = __ffma2_rn(ex, h1[b].i, __ffma2_rn(ey, h1[b].r, w1.i));
+        }
+        w0 = {__fmul2_rn(f, w0.r), __fmul2_rn(f, w0.i)};
+        w1 = {__fmul2_rn(f, w1.r), __fmul2_rn(f, w1.i)};
+        acc[a] = {__fadd2_rn(acc[a].r, w0.r), __fadd2_rn(acc[a].i, w0.i)};
+        acc[3 + a] = {__fadd2_rn(acc[3 + a].r, w1.r), __fadd2_rn(acc[3 + a].i, w1.i)};
+        acc[6 + a] = fma_unit<P::V0>(g, P::D0 ? w1 : w0, acc[6 + a]);
+        acc[9 + a] = fma_unit<P::V1>(g, P::D1 ? w1 : w0, acc[9 + a]);
+    }
+}
+
+template <typename HT, int MU, bool DAG, int BC>
+__device__ __forceinline__ void hop_dir_half_c2(const Geom &g, const SiteCoords &xc, const typename HT::h2 *U,
+                                                const typename HT::h2 *in, const float *nrm, int s, c2 acc[12]) {
+    const int n = g.n[MU], st = g.stride[MU], c = xc.x[MU];
+    const bool top = c == n - 1, bot = c == 0;
+    const int nf = top ? s - (n - 1) * st : s + st;
+    const int nbk = bot ? s + (n - 1) * st : s - st;
+    hop_half_c2<HT, MU, DAG ? +1 : -1, false, BC>(U, in, nrm, g.V, nf, s, top && g.bcf[MU] < 0, acc);
+    hop_half_c2<HT, MU, DAG ? -1 : +1, true, BC>(U, in, nrm, g.V, nbk, nbk, bot && g.bcf[MU] < 0, acc);
+}
+
+// out = D_W in for two columns per thread (BC even), packed lanes
+template <typename HT, bool DAG, int BC>
+__global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
+    dslash_half_c2_kernel(Geom g, const typename HT::h2 *__restrict__ U, const typename HT::h2 *__restrict__ in,
+                          const float *__restrict__ nin, typename HT::h2 *__restrict__ out, float *__restrict__ nout,
+                          float kappa) {
+    typedef TileMap<BC, 2> TM;
+    const int s = blockIdx.x * TM::SPB + threadIdx.x / TM::TPS;
+    const int jj = (threadIdx.x % TM::TPS) * 2;
+    if (s >= g.V) return;
+    const size_t fb = (size_t)blockIdx.y * 12 * g.V * BC + jj, nbase = (size_t)blockIdx.y * g.V * BC + jj;
+    const typename HT::h2 *pin = in + fb;
+    const float *pn = nin + nbase;
+    c2 acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = {bc2(0.f), bc2(0.f)};
+    const SiteCoords xc(g, s);
+    hop_dir_half_c2<HT, 0, DAG, BC>(g, xc, U, pin, pn, s, acc);
+    hop_dir_half_c2<HT, 1, DAG, BC>(g, xc, U, pin, pn, s, acc);
+    hop_dir_half_c2<HT, 2, DAG, BC>(g, xc, U, pin, pn, s, acc);
+    hop_dir_half_c2<HT, 3, DAG, BC>(g, xc, U, pin, pn, s, acc);
+    const float2 ns = *reinterpret_cast<const float2 *>(pn + (size_t)s * BC), nk = bc2(-kappa);
+    float mx0 = 0.f, mx1 = 0.f;
+    const typename HT::h2 *ps = pin + (size_t)s * 12 * BC;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const c2 v = ld_c2<HT>(ps + c * BC);
+        acc[c].r = __ffma2_rn(ns, v.r, __fmul2_rn(nk, acc[c].r));
+        acc[c].i = __ffma2_rn(ns, v.i, __fmul2_rn(nk, acc[c].i));
+        mx0 = fmaxf(mx0, fmaxf(fabsf(acc[c].r.x), fabsf(acc[c].i.x)));
+        mx1 = fmaxf(mx1, fmaxf(fabsf(acc[c].r.y), fabsf(acc[c].i.y)));
+    }
+    const float2 inv = make_float2(mx0 > 0.f ? 1.f / mx0 : 0.f, mx1 > 0.f ? 1.f / mx1 : 0.f);
+    typename HT::h2 *po = out + fb + (size_t)s * 12 * BC;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) st_c2<HT>(po + c * BC, __fmul2_rn(inv, acc[c].r), __fmul2_rn(inv, acc[c].i));
+    *reinterpret_cast<float2 *>(nout + nbase + (size_t)s * BC) = make_float2(mx0, mx1);
+}
+
+// ------------------------------------------------------------------ packing and conversion
+// U_aos double[V][4][3][3][2] -> rows 0 and 1 of every link, FP16 and BF16
+__global__ void pack_links12_kernel(const double2 *__restrict__ Uaos, __half2 *__restrict__ Uh,
+                                    __nv_bfloat162 *__restrict__ Ub, int V) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * 24) return;
+    const int s = (int)(i / 24), k = (int)(i % 24), mu = k / 6, e = k % 6; // e = row * 3 + col, row < 2
+    const double2 u = Uaos[(size_t)s * 36 + mu * 9 + e];
+    const float2 f = make_float2((float)u.x, (float)u.y);
+    const size_t o = ((size_t)mu * V + s) * 6 + e;
+    Uh[o] = H16::pack(f);
+    Ub[o] = B16::pack(f);
+}
+
+void launch_pack_links12(const double *U_aos, void *Uh, void *Ub, int V, cudaStream_t st) {
+    const long n = (long)V * 24;
+    pack_links12_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)U_aos, (__half2 *)Uh,
+                                                                      (__nv_bfloat162 *)Ub, V);
+}
+
+// ABI double[V][12][B][2] -> half format (tile BC); one thread per (site, rhs).
+// norm = FP32 copy of max |re|, |im|; stored value = component / norm.
+template <typename HT>
+__global__ void to_half_kernel(const double2 *__restrict__ in, typename HT::h2 *__restrict__ out,
+                               float *__restrict__ nout, int V, int B, int BC) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * B) return;
+    const int j = (int)(i % B), s = (int)(i / B);
+    double2 v[12];
+    double mx = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        v[c] = in[((size_t)s * 12 + c) * B + j];
+        mx = fmax(mx, fmax(fabs(v[c].x), fabs(v[c].y)));
+    }
+    const float n = (float)mx;
+    const double dn = n > 0.f ? (double)n : 1.0;
+    const size_t t = (size_t)(j / BC), jj = (size_t)(j % BC);
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+        out[((t * V + s) * 12 + c) * BC + jj] = HT::pack(make_float2((float)(v[c].x / dn), (float)(v[c].y / dn)));
+    nout[(t * V + s) * BC + jj] = n;
+}
+
+template <typename HT>
+__global__ void from_half_kernel(const typename HT::h2 *__restrict__ in, const float *__restrict__ nin,
+                                 double2 *__restrict__ out, int V, int B, int BC) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)V * B) return;
+    const int j = (int)(i % B), s = (int)(i / B);
+    const size_t t = (size_t)(j / BC), jj = (size_t)(j % BC);
+    const double n = nin[(t * V + s) * BC + jj];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const float2 f = HT::f2(in[((t * V + s) * 12 + c) * BC + jj]);
+        out[((size_t)s * 12 + c) * B + j] = make_double2(n * (double)f.x, n * (double)f.y);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+// Tile width of the half-format fields for B columns: 16-column tiles (a
+// site's component is 64 contiguous bytes) when B allows, else one column.
+int half_tile(int B) { return B % 16 == 0 ? 16 : 1; }
+
+// columns per thread in 16-column tiles: 2 = dslash_half_c2_kernel (packed
+// lanes, 8-byte accesses, 128 registers), 1 = dslash_half_kernel (80
+// registers).  On the 8^3x16 lattice with 3072 columns: 1.37 / 1.33 ms per
+// FP16 / BF16 launch with 2, 1.58 / 1.73 ms with 1.
+#ifndef SMPQ_HALF_NR
+#define SMPQ_HALF_NR 2
+#endif
+
+size_t half_field_bytes(int V, int B) { return (size_t)V * B * (12 * 4) + (size_t)V * B * 4; }
+
+template <typename HT, int BC, int NR>
+static void dslash_half_bc(const Geom &g, const void *U, const void *in, void *out, int B, int dagger, float kappa,
+                           cudaStream_t st) {
+    typedef typename HT::h2 h2;
+    typedef TileMap<BC, NR> TM;
+    const size_t ncomp = (size_t)g.V * 12 * B;
+    const h2 *pin = (const h2 *)in;
+    const float *nin = (const float *)(pin + ncomp);
+    h2 *pout = (h2 *)out;
+    float *nout = (float *)(pout + ncomp);
+    const dim3 grid((g.V + TM::SPB - 1) / TM::SPB, B / BC);
+    if constexpr (NR == 2) {
+        if (dagger)
+            dslash_half_c2_kernel<HT, true, BC><<<grid, TM::THREADS, 0, st>>>(g, (const h2 *)U, pin, nin, pout, nout,
+                                                                              kappa);
+        else
+            dslash_half_c2_kernel<HT, false, BC><<<grid, TM::THREADS, 0, st>>>(g, (const h2 *)U, pin, nin, pout,
+                                                                               nout, kappa);
+    } else {
+        if (dagger)
+            dslash_half_kernel<HT, true, BC, NR><<<grid, TM::THREADS, 0, st>>>(g, (const h2 *)U, pin, nin, pout,
+                                                                               nout, kappa);
+        else
+            dslash_half_kernel<HT, false, BC, NR><<<grid, TM::THREADS, 0, st>>>(g, (const h2 *)U, pin, nin, pout,
+                                                                                nout, kappa);
+    }
+}
+
+// A half-format field of B columns is one buffer: the V * 12 * B components
+// (tile layout) followed by the V * B norms.
+template <typename HT>
+static void dslash_half_t(const Geom &g, const void *U, const void *in, void *out, int B, int dagger, double kappa,
+                          cudaStream_t st) {
+    switch (half_tile(B)) {
+    case 16: dslash_half_bc<HT, 16, SMPQ_HALF_NR>(g, U, in, out, B, dagger, (float)kappa, st); break;
+    default: dslash_half_bc<HT, 1, 1>(g, U, in, out, B, dagger, (float)kappa, st); break;
+    }
+}
+
+void launch_dslash_half(int prec, const Geom &g, const void *U, const void *in, void *out, int B, int dagger,
+                        double kappa, cudaStream_t st) {
+    if (prec == SMPQ_BF16N) dslash_half_t<B16>(g, U, in, out, B, dagger, kappa, st);
+    else dslash_half_t<H16>(g, U, in, out, B, dagger, kappa, st);
+}
+
+void launch_to_half(int prec, const double *in, void *out, int V, int B, cudaStream_t st) {
+    const long n = (long)V * B;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const int BC = half_tile(B);
+    const size_t ncomp = (size_t)V * 12 * B;
+    if (prec == SMPQ_BF16N) {
+        __nv_bfloat162 *o = (__nv_bfloat162 *)out;
+        to_half_kernel<B16><<<nb, 256, 0, st>>>((const double2 *)in, o, (float *)(o + ncomp), V, B, BC);
+    } else {
+        __half2 *o = (__half2 *)out;
+        to_half_kernel<H16><<<nb, 256, 0, st>>>((const double2 *)in, o, (float *)(o + ncomp), V, B, BC);
+    }
+}
+
+void launch_from_half(int prec, const void *in, double *out, int V, int B, cudaStream_t st) {
+    const long n = (long)V * B;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const int BC = half_tile(B);
+    const size_t ncomp = (size_t)V * 12 * B;
+    if (prec == SMPQ_BF16N) {
+        const __nv_bfloat162 *p = (const __nv_bfloat162 *)in;
+        from_half_kernel<B16><<<nb, 256, 0, st>>>(p, (const float *)(p + ncomp), (double2 *)out, V, B, BC);
+    } else {
+        const __half2 *p = (const __half2 *)in;
+        from_half_kernel<H16><<<nb, 256, 0, st>>>(p, (const float *)(p + ncomp), (double2 *)out, V, B, BC);
+    }
+}

@@ -39,6 +39,7 @@ struct smpq_ctx {
     int dims[4] = {0, 0, 0, 0};
     int V = 0;
     Buf U64, U32, Udf; // FP64, FP32 and float-float copies of the links
+    Buf Uh16, Ub16;    // rows 0 and 1 of the links in FP16 and BF16 (reconstruct-12)
 
     // spectrum / rational
     bool have_spec = false;
@@ -105,6 +106,17 @@ template <typename T> void launch_from_tiled(const void *in, double *out, int V,
 // out = D_W in (or D_W^dag), tiled layout, no reductions
 template <typename T> void launch_dslash(const Geom &g, const void *U, const void *in, void *out, int B, int BC,
                                          int dagger, double kappa, cudaStream_t st);
+
+// half.cu : SMPQ_FP16N / SMPQ_BF16N storage for the stand-alone D_W.  A half
+// field of B columns is one buffer of half_field_bytes(V, B): the components
+// [j / BC][V][12][BC] (BC = half_tile(B)) followed by the norms [j / BC][V][BC].
+void launch_pack_links12(const double *U_aos, void *Uh, void *Ub, int V, cudaStream_t st);
+int half_tile(int B);
+size_t half_field_bytes(int V, int B);
+void launch_to_half(int prec, const double *in, void *out, int V, int B, cudaStream_t st);
+void launch_from_half(int prec, const void *in, double *out, int V, int B, cudaStream_t st);
+void launch_dslash_half(int prec, const Geom &g, const void *U, const void *in, void *out, int B, int dagger,
+                        double kappa, cudaStream_t st);
 
 // msolve.cu : multi-shift CG over a batch (see msolve.cu for the contract)
 struct SolveSpec {

@@ -27,6 +27,8 @@ SMPQ_ESTATE = -8
 SMPQ_FP64 = 0
 SMPQ_FP32 = 1
 SMPQ_MIXED = 2
+SMPQ_FP16N = 3
+SMPQ_BF16N = 4
 
 _NAMES = {v: k for k, v in globals().items() if k.startswith("SMPQ_E") or k == "SMPQ_OK"}
 
@@ -91,7 +93,7 @@ EXPORTS = [
     "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
     "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv", "smpq_compute_qx_batch",
-    "smpq_low_modes", "smpq_get_low_modes", "smpq_clear_low_modes",
+    "smpq_low_modes", "smpq_get_low_modes", "smpq_clear_low_modes", "smpq_time_dslash",
 ]
 
 _lib = None
@@ -127,6 +129,7 @@ def load(build_if_missing=True):
         "smpq_colour_sites": [PI, I, I, P, PI],
         "smpq_dslash": [P, P, P, I, I, I, I],
         "smpq_dslash_noalloc": [P, P, P, I, I, I],
+        "smpq_time_dslash": [P, I, I, I, I, PD, PD],
         "smpq_apply_dov": [P, P, P, I, I],
         "smpq_compute_qx": [P, P, P, I, PD, ctypes.POINTER(smpq_stats)],
         "smpq_compute_qx_classes": [P, PI, I, P, P, I, ctypes.POINTER(smpq_stats)],
@@ -271,6 +274,15 @@ def smpq_dslash(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
     if di != do:
         raise ValueError("in and out must both be host or both be device buffers")
     _check(load().smpq_dslash(ctx, pi, po, B, int(dagger), precision, di), ctx)
+
+
+def smpq_time_dslash(ctx, B, dagger=False, precision=SMPQ_FP32, reps=10):
+    """Average ms of one stand-alone D_W launch on B scratch columns, and the
+    algorithmic bytes of that launch: returns (ms, bytes)."""
+    ms, nbytes = ctypes.c_double(), ctypes.c_double()
+    _check(load().smpq_time_dslash(ctx, B, int(dagger), precision, reps, ctypes.byref(ms), ctypes.byref(nbytes)),
+           ctx)
+    return ms.value, nbytes.value
 
 
 def smpq_dslash_noalloc(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):

@@ -79,6 +79,96 @@ def test_dslash_fp32(S):
     assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
+# Half-precision storage (SMPQ_FP16N / SMPQ_BF16N): FP16 or BF16 components
+# scaled by one FP32 norm per site and right-hand side, links as FP16/BF16 rows
+# 0 and 1 with row 2 = conj(row 0 x row 1), FP32 arithmetic.
+# Largest rounding error of a stored value in [-1, 1]: half the spacing below 1.
+HALF_UNIT = {"fp16": 2.0 ** -12, "bf16": 2.0 ** -9}
+
+
+def _round_half(x, fmt):
+    """float32 array -> nearest FP16 (numpy) or BF16 (torch on the CPU), as float64."""
+    x = np.asarray(x, dtype=np.float32)
+    if fmt == "fp16":
+        return x.astype(np.float16).astype(np.float64)
+    import torch
+    return torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _quantise_spinor(psi, fmt):
+    """The field the half format holds for psi [V, 4, 3, B]: per (site, rhs) the
+    FP32 norm n = max |re|, |im| of the 12 components, values n * half(v / n)."""
+    V, B = psi.shape[0], psi.shape[-1]
+    p = psi.reshape(V, 12, B)
+    n = np.maximum(np.abs(p.real), np.abs(p.imag)).max(axis=1).astype(np.float32).astype(np.float64)
+    d = np.where(n > 0, n, 1.0)[:, None, :]
+    q = _round_half(p.real / d, fmt) + 1j * _round_half(p.imag / d, fmt)
+    return (q * n[:, None, :]).reshape(psi.shape)
+
+
+def _quantise_links(U, fmt):
+    """Rows 0 and 1 rounded (FP32, then the half format), row 2 rebuilt as
+    conj(row 0 x row 1) in FP64 (the unitary third row of an SU(3) matrix)."""
+    Uq = np.empty_like(U)
+    Uq[..., :2, :] = _round_half(U[..., :2, :].real, fmt) + 1j * _round_half(U[..., :2, :].imag, fmt)
+    Uq[..., 2, :] = np.conj(np.cross(Uq[..., 0, :], Uq[..., 1, :]))
+    return Uq
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+@pytest.mark.parametrize("name,B,bc", [("flux4x8", 3, (1, 1, 1, -1)), ("flux8x16", 32, (1, 1, 1, 1)),
+                                       ("flux8x16", 48, (1, 1, 1, -1))])
+def test_dslash_half(S, fmt, name, B, bc):
+    """D_W in the half format against the FP64 oracle D_W on the quantised field
+    and links: the result differs only by its own rounding to the half format
+    (<= HALF_UNIT of its (site, rhs) norm in every real and imaginary part) and
+    FP32 arithmetic (< 1e-5 of that norm).
+    B = 3 runs one-column tiles, B = 32 and 48 the 16-column tiles."""
+    prec = S.SMPQ_FP16N if fmt == "fp16" else S.SMPQ_BF16N
+    cfg = make_config(name)
+    V = int(np.prod(cfg["dims"]))
+    psi = random_spinor(np.random.default_rng(7), V, B)
+    psi_q = _quantise_spinor(psi, fmt)
+    U_q = _quantise_links(cfg["U"], fmt)
+    with _session(S, bc=bc) as s:
+        s.load_gauge(cfg["dims"], cfg["U"])
+        for dag in (False, True):
+            got = s.dslash(psi_q, dagger=dag, precision=prec)
+            ref = native.apply_dw(U_q, dirac.apply_g5(psi_q) if dag else psi_q, cfg["dims"], KAPPA, bc)
+            if dag:
+                ref = dirac.apply_g5(ref)
+            r12 = ref.reshape(V, 12, B)
+            norm = np.maximum(np.abs(r12.real), np.abs(r12.imag)).max(axis=1)[:, None, :]
+            d = got.reshape(V, 12, B) - r12
+            err = np.maximum(np.abs(d.real), np.abs(d.imag)) / norm  # each real part is rounded on its own
+            assert err.max() <= HALF_UNIT[fmt] * 1.001 + 1e-5, err.max()
+            # against the unrounded field and links (the format's own error)
+            full = native.apply_dw(cfg["U"], dirac.apply_g5(psi) if dag else psi, cfg["dims"], KAPPA, bc)
+            if dag:
+                full = dirac.apply_g5(full)
+            rel = np.abs(got - full).max() / np.abs(full).max()
+            print("\nD_W %s %s B=%d dagger=%d: max |err| / max |D_W psi| = %.3e (vs quantised inputs %.3e)"
+                  % (fmt, name, B, dag, rel, err.max()))
+            assert rel <= 16 * HALF_UNIT[fmt]
+
+
+def test_time_dslash_every_format(S):
+    cfg = make_config("flux4x8")
+    V = int(np.prod(cfg["dims"]))
+    with _session(S) as s:
+        s.load_gauge(cfg["dims"], cfg["U"])
+        for prec, spinor, link in ((S.SMPQ_FP64, 192, 144), (S.SMPQ_FP32, 96, 72), (S.SMPQ_FP16N, 52, 24),
+                                   (S.SMPQ_BF16N, 52, 24)):
+            for B in (12, 48):
+                ms, nbytes = S.smpq_time_dslash(s.ctx, B, False, prec, 3)
+                assert ms > 0
+                assert nbytes == V * B * 2 * spinor + V * 4 * link
+        with pytest.raises(S.SmpqError):
+            S.smpq_time_dslash(s.ctx, 12, False, S.SMPQ_MIXED, 3)
+        with pytest.raises(S.SmpqError):
+            s.dslash(random_spinor(np.random.default_rng(1), V, 2), precision=S.SMPQ_MIXED)
+
+
 # ----------------------------------------------------------------------------- D_ov, spectrum
 
 

@@ -84,3 +84,11 @@ def test_stout_c_matches_numpy():
                 p += np.einsum("saa->s", P).real.mean() / 3
         return p / 6
     assert plaq(b) > plaq(U) + 0.1
+
+
+def test_third_link_row_is_conj_cross_of_the_first_two():
+    """SU(3) rows: row 2 = conj(row 0 x row 1), the identity behind storing two
+    rows of every link (reconstruct-12) in the half-precision D_W."""
+    for name in ("flux4", "flux4x8"):
+        U = make_config(name)["U"]
+        assert np.abs(np.conj(np.cross(U[..., 0, :], U[..., 1, :])) - U[..., 2, :]).max() < 1e-13
