@@ -249,6 +249,13 @@ def run_gpu(args):
     cfg = config_for_rank(rank, args.config)
     U, dims = cfg["U"], cfg["dims"]
     V = int(np.prod(dims))
+    if args.dslash_only:  # profiling entry: the stand-alone D_W formats alone, no solve
+        s = Session(device=dev, stream=stream)
+        s.load_gauge(dims, U)
+        print(json.dumps({"workload": "%dx%dx%dx%d %s, stand-alone D_W" % (tuple(dims) + (args.config,)),
+                          "dslash": _dslash_formats(s, V, args.dslash_columns)}), flush=True)
+        s.close()
+        return
     spectrum_note = "oracle ARPACK (tests/golden/spectra.json), widened 0.98/1.02"
     try:
         a, b = _spectrum(args.config)
@@ -260,14 +267,6 @@ def run_gpu(args):
         a, b = 0.98 * lo, 1.02 * hi
         spectrum_note = "GPU Lanczos (smpq_measure_spectrum, 300 steps), widened 0.98/1.02"
     prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
-
-    if args.dslash_only:  # profiling entry: the stand-alone D_W formats alone, no solve
-        s = Session(device=dev, stream=stream)
-        s.load_gauge(dims, U)
-        print(json.dumps({"workload": "%dx%dx%dx%d stand-alone D_W" % tuple(dims),
-                          "dslash": _dslash_formats(s, V, args.dslash_columns)}), flush=True)
-        s.close()
-        return
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
                 use_graphs=1, profile=1, switch_residual=args.switch, autotune=0 if args.no_autotune else 1)
