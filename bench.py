@@ -266,7 +266,8 @@ def run_gpu(args):
         probe.close()
         a, b = 0.98 * lo, 1.02 * hi
         spectrum_note = "GPU Lanczos (smpq_measure_spectrum, 300 steps), widened 0.98/1.02"
-    prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
+    prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED, "fp16n": smpq.SMPQ_FP16N,
+            "bf16n": smpq.SMPQ_BF16N}[args.precision]
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
                 use_graphs=1, profile=1, switch_residual=args.switch, autotune=0 if args.no_autotune else 1)
@@ -313,14 +314,22 @@ def run_gpu(args):
     link32, link64 = 4 * 9 * 8, 4 * 9 * 16
     b_vecs = 6 if prec == smpq.SMPQ_FP32 else 4  # t, p, r (+ x_lo) read, r (+ x_lo) written
     kern = {}
+    half = prec in (smpq.SMPQ_FP16N, smpq.SMPQ_BF16N)
+    lo = {smpq.SMPQ_FP16N: "fp16n", smpq.SMPQ_BF16N: "bf16n"}.get(prec, "fp32")
     for key, ms_k, n_k, esz_k, nvec in (
-            ("k_apply_a[fp32]", "dslash_ms", "dslash_launches", 8, 2),
-            ("k_apply_b[fp32]", "update_ms", "update_launches", 8, b_vecs),
+            ("k_apply_a[%s]" % lo, "dslash_ms", "dslash_launches", 8, 2),
+            ("k_apply_b[%s]" % lo, "update_ms", "update_launches", 8, b_vecs),
             ("k_apply_a[fp64-accurate]", "dslash_hi_ms", "dslash_hi_launches", 16, 2),
             ("k_apply_b[fp64-accurate]", "update_hi_ms", "update_hi_launches", 16, 4)):
         tot = sum(x[ms_k] for x in stats)
         n = sum(x[n_k] for x in stats)
-        if n:
+        if n and half and esz_k == 8:
+            # half-format p and t (52 bytes per site and source with the norm),
+            # FP32 r and x_lo (96 bytes each, read and written in k_apply_b),
+            # reconstruct-12 links (96 bytes per site)
+            nbytes = V * B * (2 * 52 if key.startswith("k_apply_a") else 2 * 52 + 4 * 96) + V * 96
+            kern[key] = dict(ms=tot / n, n=n, share_ms=tot, bytes=nbytes)
+        elif n:
             kern[key] = dict(ms=tot / n, n=n, share_ms=tot,
                              bytes=V * B * nvec * 12 * esz_k + V * (link32 if esz_k == 8 else link64))
     dom = max(kern, key=lambda k: kern[k]["share_ms"])
@@ -332,7 +341,7 @@ def run_gpu(args):
     # the FP64 units (1.25 TFLOP/s nominal).  Algorithmic operation counts per
     # site and source are the DF64_OPS_* and FP64_FLOP_* constants above.
     for key, k in kern.items():
-        if "fp32" in key:
+        if "fp32" in key or "16n" in key:
             k.update(bound="hbm", unit="GB/s", peak=peak_hbm, peak_source=peak_kind,
                      achieved=k["bytes"] / (k["ms"] / 1000.0) / 1e9, algorithmic=k["bytes"])
         elif prec == smpq.SMPQ_MIXED:  # float-float
@@ -539,7 +548,8 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
         # ablation of the star support: the shifted directions on every site
         # (14 full-lattice vectors per source) against the restricted path, on
         # the same sample of classes and in the same precision
-        prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED}[args.precision]
+        prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED, "fp16n": smpq.SMPQ_FP16N,
+            "bf16n": smpq.SMPQ_BF16N}[args.precision]
         cls = list(range(0, n_classes, max(1, n_classes // 16)))[:16]
         res = {}
         for full in (0, 1):
@@ -591,10 +601,15 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
         line = {
             "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {smpq.SMPQ_FP32: "f32", smpq.SMPQ_FP64: "f64", smpq.SMPQ_MIXED: "f64+f32"}[prec],
+            "vs_baseline": None, "dtype": {smpq.SMPQ_FP32: "f32", smpq.SMPQ_FP64: "f64", smpq.SMPQ_MIXED: "f64+f32",
+                                      smpq.SMPQ_FP16N: "f16+f32", smpq.SMPQ_BF16N: "bf16+f32"}[prec],
             "data": "synthetic",
             "config": {"workload": _workload_name(args),
                        "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
+                                     smpq.SMPQ_FP16N: "FP16 p, t with per-site norms, reconstruct-12 links, FP32 "
+                                                      "r and arithmetic, FP64 reliable updates",
+                                     smpq.SMPQ_BF16N: "BF16 p, t with per-site norms, reconstruct-12 links, FP32 "
+                                                      "r and arithmetic, FP64 reliable updates",
                                      smpq.SMPQ_FP64: "FP64",
                                      smpq.SMPQ_MIXED: "FP64-accurate until ||r|| < %g ||b||, then FP32 (shifted vectors too)"
                                      % args.switch}[prec],
@@ -630,7 +645,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="smpq", choices=["smpq", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "fp64", "mixed", "fp16n", "bf16n"])
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

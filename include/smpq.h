@@ -59,11 +59,15 @@ typedef enum {
                        until ||r|| <= switch_residual ||b||, then FP32 without residual
                        replacement; shifted directions in FP64 in the first phase and
                        FP32 in the second, y in FP64 throughout */
-    SMPQ_FP16N = 3, /* stand-alone D_W only (smpq_dslash, smpq_time_dslash): spinor components
-                       stored in FP16 and scaled by one FP32 norm per site and right-hand
-                       side, links stored as FP16 rows 0 and 1 (reconstruct-12), FP32
-                       arithmetic.  The solver options reject it (SMPQ_EINVAL). */
-    SMPQ_BF16N = 4  /* as SMPQ_FP16N with BF16 storage */
+    SMPQ_FP16N = 3, /* spinor components stored in FP16 and scaled by one FP32 norm per site
+                       and right-hand side, links stored as FP16 rows 0 and 1
+                       (reconstruct-12), FP32 arithmetic.  smpq_dslash / smpq_time_dslash:
+                       the stand-alone D_W in that format.  As a solver precision: the
+                       SMPQ_FP32 iterations (FP64 reliable updates, FP32 residual and
+                       shifted directions) with D_W's input p and output t in that
+                       format; the shifted systems then keep an error floor near the
+                       format's rounding (about 1e-4 relative), far above FP32's. */
+    SMPQ_BF16N = 4  /* as SMPQ_FP16N with BF16 storage (floor near 1e-3 relative) */
 } smpq_precision;
 
 typedef struct {

@@ -92,7 +92,8 @@ int validate_options(smpq_ctx *ctx, const smpq_options *o) {
     if (o->npoles < 1 || o->npoles > SMPQ_MAX_POLES) return set_err(ctx, SMPQ_EINVAL, "npoles must be in 1..32");
     if (!(o->tol > 0) || !(o->tol < 1)) return set_err(ctx, SMPQ_EINVAL, "tol must be in (0, 1)");
     if (o->max_iter < 1) return set_err(ctx, SMPQ_EINVAL, "max_iter must be positive");
-    if (o->precision != SMPQ_FP64 && o->precision != SMPQ_FP32 && o->precision != SMPQ_MIXED)
+    if (o->precision != SMPQ_FP64 && o->precision != SMPQ_FP32 && o->precision != SMPQ_MIXED &&
+        o->precision != SMPQ_FP16N && o->precision != SMPQ_BF16N)
         return set_err(ctx, SMPQ_EINVAL, "bad precision");
     if (o->precision == SMPQ_MIXED && (!(o->switch_residual > 0) || !(o->switch_residual < 1)))
         return set_err(ctx, SMPQ_EINVAL, "switch_residual must be in (0, 1)");
@@ -128,7 +129,8 @@ int tune_bc(smpq_ctx *ctx, int B, int prec) {
     for (int bc : {12, 24, 48})
         if (B % bc == 0) cand.push_back(bc);
     if (cand.empty()) return 1;
-    if (!ctx->opt.autotune || cand.size() == 1) return cand.back();
+    // (the half-storage iterations are not timed: widest tile)
+    if (!ctx->opt.autotune || cand.size() == 1 || prec == SMPQ_FP16N || prec == SMPQ_BF16N) return cand.back();
     for (auto &e : ctx->tuned)
         if (e[0] == ctx->V && e[1] == B && e[2] == prec) return e[3];
     const size_t nf = (size_t)B * 12 * ctx->V;
@@ -157,9 +159,12 @@ int tune_bc(smpq_ctx *ctx, int B, int prec) {
 
 // device bytes one right-hand side costs in the solver (full-lattice vectors)
 size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
-    size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16) : (prec == SMPQ_MIXED ? 3 * 16 + 3 * 8 : 3 * 16);
+    const bool half = prec == SMPQ_FP16N || prec == SMPQ_BF16N;
+    size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16)
+                 : half            ? (2 * 5 + 2 * 8 + 2 * 16) // p, t: 4 B + a 12th of the 4-byte norm
+                                   : (prec == SMPQ_MIXED ? 3 * 16 + 3 * 8 : 3 * 16);
     size_t full = (size_t)ctx->V * 12 * per;
-    size_t eb = prec == SMPQ_FP32 ? 8 : (prec == SMPQ_MIXED ? 16 + 8 : 16); // MIXED: FP64 and FP32 copies
+    size_t eb = (prec == SMPQ_FP32 || half) ? 8 : (prec == SMPQ_MIXED ? 16 + 8 : 16); // MIXED: FP64 and FP32 copies
     size_t sup = (size_t)n_sup * 12 * (npoles * eb + 16);
     return full + sup;
 }

@@ -7,163 +7,16 @@
 //     the third row is the complex conjugate of the cross product of the
 //     first two, recomputed in FP32 at every use;
 //   - arithmetic and accumulation in FP32.
-// These formats serve smpq_dslash and smpq_time_dslash only: the multi-shift
-// solver does not iterate in them (a half-precision Krylov basis would leave
-// every shifted system with an error floor near the format's unit roundoff).
+// This file holds the stand-alone D_W of smpq_dslash and smpq_time_dslash; the
+// solver's half-storage iterations (msolve.cu) share the device code in
+// half.cuh.
 //
 // Layouts (RHS tiles of BC columns, as the FP32 and FP64 fields):
 //   components [j / BC][V][12][BC] of H2 (one complex number as two halves)
 //   norms      [j / BC][V][BC] float; component value = norm * stored value
 //   links      [(mu * V + s) * 6 + row * 3 + col], rows 0 and 1
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <string.h>
-
 #include "smpq_internal.cuh"
-#include "wilson.cuh"
-
-struct H16 {
-    typedef __half2 h2;
-    static __device__ __forceinline__ float2 f2(h2 v) { return __half22float2(v); }
-    static __device__ __forceinline__ h2 pack(float2 v) { return __float22half2_rn(v); }
-};
-struct B16 {
-    typedef __nv_bfloat162 h2;
-    static __device__ __forceinline__ float2 f2(h2 v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ h2 pack(float2 v) { return __float22bfloat162_rn(v); }
-};
-
-template <typename HT> __device__ __forceinline__ float2 f2_bits(unsigned w) {
-    typename HT::h2 v;
-    memcpy(&v, &w, 4);
-    return HT::f2(v);
-}
-template <typename HT> __device__ __forceinline__ unsigned bits_f2(float2 v) {
-    typename HT::h2 h = HT::pack(v);
-    unsigned w;
-    memcpy(&w, &h, 4);
-    return w;
-}
-
-// NR adjacent columns of one component (NR = 2: one 8-byte access)
-template <typename HT, int NR>
-__device__ __forceinline__ void ld_cols(const typename HT::h2 *__restrict__ p, float2 v[NR]) {
-    if constexpr (NR == 2) {
-        const uint2 q = *reinterpret_cast<const uint2 *>(p);
-        v[0] = f2_bits<HT>(q.x);
-        v[1] = f2_bits<HT>(q.y);
-    } else {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = HT::f2(p[r]);
-    }
-}
-template <typename HT, int NR> __device__ __forceinline__ void st_cols(typename HT::h2 *p, const float2 v[NR]) {
-    if constexpr (NR == 2) {
-        *reinterpret_cast<uint2 *>(p) = make_uint2(bits_f2<HT>(v[0]), bits_f2<HT>(v[1]));
-    } else {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) p[r] = HT::pack(v[r]);
-    }
-}
-template <int NR> __device__ __forceinline__ void ld_norms(const float *__restrict__ p, float v[NR]) {
-    if constexpr (NR == 2) {
-        const float2 q = *reinterpret_cast<const float2 *>(p);
-        v[0] = q.x;
-        v[1] = q.y;
-    } else {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = p[r];
-    }
-}
-
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-
-// The link of (mu, s) as a full 3x3 matrix: rows 0 and 1 from memory (24 bytes,
-// three 8-byte loads), row 2 = conj(row 0 x row 1).
-template <typename HT>
-__device__ __forceinline__ void load_link12(const typename HT::h2 *__restrict__ U, size_t idx, float2 m[3][3]) {
-    const uint2 *p = reinterpret_cast<const uint2 *>(U + idx * 6);
-    const uint2 a = p[0], b = p[1], c = p[2];
-    m[0][0] = f2_bits<HT>(a.x);
-    m[0][1] = f2_bits<HT>(a.y);
-    m[0][2] = f2_bits<HT>(b.x);
-    m[1][0] = f2_bits<HT>(b.y);
-    m[1][1] = f2_bits<HT>(c.x);
-    m[1][2] = f2_bits<HT>(c.y);
-    m[2][0] = conjf2(csub(cmul(m[0][1], m[1][2]), cmul(m[0][2], m[1][1])));
-    m[2][1] = conjf2(csub(cmul(m[0][2], m[1][0]), cmul(m[0][0], m[1][2])));
-    m[2][2] = conjf2(csub(cmul(m[0][0], m[1][1]), cmul(m[0][1], m[1][0])));
-}
-
-// One hop, acc += f (1 + SG g_mu) W psi(nb) for NR columns, W = U(ls) or
-// U(ls)^dag (BACK); f = the neighbour's norm, negated across an antiperiodic
-// boundary (flip).  Same projection as the FP32 hop (S_mu on the lower half).
-template <typename HT, int MU, int SG, bool BACK, int BC, int NR>
-__device__ __forceinline__ void hop_half(const typename HT::h2 *__restrict__ U, const typename HT::h2 *__restrict__ in,
-                                         const float *__restrict__ nrm, int Vl, int nb, int ls, bool flip,
-                                         float2 acc[12][NR]) {
-    const typename HT::h2 *q = in + (size_t)nb * (12 * BC);
-    float f[NR];
-    ld_norms<NR>(nrm + (size_t)nb * BC, f);
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-        if (flip) f[r] = -f[r];
-    float2 h[2][3][NR];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float2 p0[NR], p1[NR], p2[NR], p3[NR];
-        ld_cols<HT, NR>(q + a * BC, p0);
-        ld_cols<HT, NR>(q + (3 + a) * BC, p1);
-        ld_cols<HT, NR>(q + (6 + a) * BC, p2);
-        ld_cols<HT, NR>(q + (9 + a) * BC, p3);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            float2 s0, s1;
-            s_apply<MU>(p2[r], p3[r], s0, s1);
-            if (SG > 0) { h[0][a][r] = cadd(p0[r], s0); h[1][a][r] = cadd(p1[r], s1); }
-            else { h[0][a][r] = csub(p0[r], s0); h[1][a][r] = csub(p1[r], s1); }
-        }
-    }
-    float2 m[3][3];
-    load_link12<HT>(U, (size_t)MU * Vl + ls, m);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (BACK) { // (U^dag)_{ab} = conj(U_{ba})
-                    w0 = cfmac(m[b][a], h[0][b][r], w0);
-                    w1 = cfmac(m[b][a], h[1][b][r], w1);
-                } else {
-                    w0 = cfma(m[a][b], h[0][b][r], w0);
-                    w1 = cfma(m[a][b], h[1][b][r], w1);
-                }
-            }
-            w0 = cscale(f[r], w0);
-            w1 = cscale(f[r], w1);
-            acc[a][r] = cadd(acc[a][r], w0);
-            acc[3 + a][r] = cadd(acc[3 + a][r], w1);
-            float2 l0, l1;
-            sdag_apply<MU>(w0, w1, l0, l1);
-            if (SG > 0) { acc[6 + a][r] = cadd(acc[6 + a][r], l0); acc[9 + a][r] = cadd(acc[9 + a][r], l1); }
-            else { acc[6 + a][r] = csub(acc[6 + a][r], l0); acc[9 + a][r] = csub(acc[9 + a][r], l1); }
-        }
-    }
-}
-
-template <typename HT, int MU, bool DAG, int BC, int NR>
-__device__ __forceinline__ void hop_dir_half(const Geom &g, const SiteCoords &xc, const typename HT::h2 *U,
-                                             const typename HT::h2 *in, const float *nrm, int s,
-                                             float2 acc[12][NR]) {
-    const int n = g.n[MU], st = g.stride[MU], c = xc.x[MU];
-    const bool top = c == n - 1, bot = c == 0;
-    const int nf = top ? s - (n - 1) * st : s + st;
-    const int nbk = bot ? s + (n - 1) * st : s - st;
-    hop_half<HT, MU, DAG ? +1 : -1, false, BC, NR>(U, in, nrm, g.V, nf, s, top && g.bcf[MU] < 0, acc);
-    hop_half<HT, MU, DAG ? -1 : +1, true, BC, NR>(U, in, nrm, g.V, nbk, nbk, bot && g.bcf[MU] < 0, acc);
-}
+#include "half.cuh"
 
 // out = D_W in (DAG: D_W^dag), both in the half format; the output norm is
 // taken from the FP32 result before it is rounded to the half format.
@@ -211,7 +64,11 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, NR == 1 ? 3 : 2)
     }
     float inv[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) inv[r] = mx[r] > 0.f ? 1.f / mx[r] : 0.f;
+    for (int r = 0; r < NR; ++r) { // below the smallest normal FP32 number: stored as zero
+        const bool tiny = !(mx[r] >= 1.17549435e-38f);
+        inv[r] = tiny ? 0.f : 1.f / mx[r];
+        if (tiny) mx[r] = 0.f;
+    }
     typename HT::h2 *po = out + fb + (size_t)s * 12 * BC;
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
@@ -349,6 +206,9 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
         mx0 = fmaxf(mx0, fmaxf(fabsf(acc[c].r.x), fabsf(acc[c].i.x)));
         mx1 = fmaxf(mx1, fmaxf(fabsf(acc[c].r.y), fabsf(acc[c].i.y)));
     }
+    // below the smallest normal FP32 number the reciprocal would overflow: stored as zero
+    if (!(mx0 >= 1.17549435e-38f)) mx0 = 0.f;
+    if (!(mx1 >= 1.17549435e-38f)) mx1 = 0.f;
     const float2 inv = make_float2(mx0 > 0.f ? 1.f / mx0 : 0.f, mx1 > 0.f ? 1.f / mx1 : 0.f);
     typename HT::h2 *po = out + fb + (size_t)s * 12 * BC;
 #pragma unroll

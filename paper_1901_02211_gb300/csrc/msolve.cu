@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "half.cuh"
 #include "smpq_internal.cuh"
 #include "wilson.cuh"
 
@@ -297,6 +298,161 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             pv.y = rv.y + b * pv.y;
             p[o] = pv;
         }
+    }
+}
+
+// ------------------------------------------------------------------ half-storage iterations
+// SMPQ_FP16N / SMPQ_BF16N: the FP32 path (FP64 reliable updates, FP32 r, x_lo
+// and shifted directions) with p and t -- the input and output of D_W --
+// stored in the half format of half.cuh and the links in reconstruct-12 form.
+// One thread per site and column (TileMap<BC>), FP32 arithmetic.
+template <typename HT> struct HF {
+    typename HT::h2 *v; // components, tiled like the FP32 fields
+    float *n;           // norms [j / BC][V][BC]
+};
+template <typename HT> struct HLinks;
+template <> struct HLinks<H16> { static const void *get(const smpq_ctx *c) { return c->Uh16.p; } };
+template <> struct HLinks<B16> { static const void *get(const smpq_ctx *c) { return c->Ub16.p; } };
+
+// r = p = b (p in the half format), x_lo = x_hi = 0; partial |b|^2
+template <typename HT, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+    k_init_h(Geom g, Source src, float2 *r, HF<HT> p, float2 *xlo, double2 *xhi, double *part, int G) {
+    __shared__ double sm[TileMap<BC>::THREADS];
+    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+    double acc = 0;
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        if (s >= g.V) continue;
+        float2 v[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = base + ((size_t)s * 12 + c) * BC;
+            const double2 b = source_at<BC>(src, g.V, s, c, j, o);
+            v[c] = make_float2((float)b.x, (float)b.y);
+            r[o] = v[c];
+            xlo[o] = make_float2(0.f, 0.f);
+            xhi[o] = make_double2(0, 0);
+            acc += b.x * b.x + b.y * b.y;
+        }
+        st_site_half<HT, BC>(p.v + base + (size_t)s * 12 * BC, p.n + nbase + (size_t)s * BC, v);
+    }
+    const double t = block_sum<BC>(acc, sm);
+    if (threadIdx.x < BC) part[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = t;
+}
+
+// t = D_W p in the half format; partials |t|^2 (before rounding) and |p|^2
+template <typename HT, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
+    k_apply_a_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
+                double *part_p, int G) {
+    __shared__ double sm[TileMap<BC>::THREADS];
+    const int jj = threadIdx.x % BC, chunk = blockIdx.y;
+    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+    double at = 0, ap = 0;
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        if (s >= g.V) continue;
+        float2 acc[12][1];
+        wilson_hop_half<HT, false, BC>(g, U, p.v + base, p.n + nbase, s, acc);
+        const typename HT::h2 *ps = p.v + base + (size_t)s * 12 * BC;
+        const float n = p.n[nbase + (size_t)s * BC];
+        float sp = 0.f, st = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const float2 f = HT::f2(ps[c * BC]);
+            const float2 v = make_float2(n * f.x, n * f.y);
+            sp += v.x * v.x + v.y * v.y;
+            acc[c][0] = make_float2(fmaf(-kappa, acc[c][0].x, v.x), fmaf(-kappa, acc[c][0].y, v.y));
+            st += acc[c][0].x * acc[c][0].x + acc[c][0].y * acc[c][0].y;
+        }
+        float2 w[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) w[c] = acc[c][0];
+        st_site_half<HT, BC>(t.v + base + (size_t)s * 12 * BC, t.n + nbase + (size_t)s * BC, w);
+        at += (double)st;
+        ap += (double)sp;
+    }
+    const double s1 = block_sum<BC>(at, sm);
+    const double s2 = block_sum<BC>(ap, sm);
+    if (threadIdx.x < BC) {
+        part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
+    }
+}
+
+// r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2
+template <typename HT, int BC, bool REL>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
+    k_apply_b_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
+                float2 *__restrict__ xlo, const double *__restrict__ alpha, double s0, float kappa, double *part_r,
+                int G) {
+    __shared__ double sm[TileMap<BC>::THREADS];
+    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+    const float a = (float)alpha[j], sh = (float)s0;
+    double ar = 0;
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        if (s >= g.V) continue;
+        float2 acc[12][1];
+        wilson_hop_half<HT, true, BC>(g, U, t.v + base, t.n + nbase, s, acc);
+        const typename HT::h2 *ts = t.v + base + (size_t)s * 12 * BC, *pq = p.v + base + (size_t)s * 12 * BC;
+        const float nt = t.n[nbase + (size_t)s * BC], np = p.n[nbase + (size_t)s * BC];
+        float sr = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = base + ((size_t)s * 12 + c) * BC;
+            const float2 tf = HT::f2(ts[c * BC]), pf = HT::f2(pq[c * BC]);
+            const float2 pv = make_float2(np * pf.x, np * pf.y);
+            float2 apv;
+            apv.x = fmaf(sh, pv.x, fmaf(-kappa, acc[c][0].x, nt * tf.x));
+            apv.y = fmaf(sh, pv.y, fmaf(-kappa, acc[c][0].y, nt * tf.y));
+            float2 rv = r[o];
+            rv.x = fmaf(-a, apv.x, rv.x);
+            rv.y = fmaf(-a, apv.y, rv.y);
+            r[o] = rv;
+            sr += rv.x * rv.x + rv.y * rv.y;
+            if (REL) {
+                float2 xv = xlo[o];
+                xv.x = fmaf(a, pv.x, xv.x);
+                xv.y = fmaf(a, pv.y, xv.y);
+                xlo[o] = xv;
+            }
+        }
+        ar += (double)sr;
+    }
+    const double s1 = block_sum<BC>(ar, sm);
+    if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+}
+
+// p = r + beta p, p in the half format
+template <typename HT, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+    k_update_p_h(int V, const float2 *__restrict__ r, HF<HT> p, const double *__restrict__ beta,
+                 const int *__restrict__ upd_rhs, int G) {
+    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    if (!upd_rhs[j]) return;
+    const size_t base = (size_t)chunk * 12 * V * BC + jj, nbase = (size_t)chunk * V * BC + jj;
+    const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+    const float b = (float)beta[j];
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        if (s >= V) continue;
+        typename HT::h2 *ps = p.v + base + (size_t)s * 12 * BC;
+        float *pn = p.n + nbase + (size_t)s * BC;
+        const float n = *pn;
+        float2 v[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const float2 f = HT::f2(ps[c * BC]), rv = r[base + ((size_t)s * 12 + c) * BC];
+            v[c] = make_float2(fmaf(b * n, f.x, rv.x), fmaf(b * n, f.y, rv.y));
+        }
+        st_site_half<HT, BC>(ps, pn, v);
     }
 }
 
@@ -614,6 +770,8 @@ constexpr bool ps32_phase2 = true;
 // solve runs in one or two phases:
 //   SMPQ_FP64  : FP64 iterations (vectors, D_W, shifted directions);
 //   SMPQ_FP32  : FP32 iterations with FP64 reliable updates of the base system;
+//   SMPQ_FP16N / SMPQ_BF16N : the same with p and t stored in FP16 / BF16 with
+//                per-site norms and reconstruct-12 links;
 //   SMPQ_MIXED : FP64 iterations until every right-hand side has
 //                ||r|| <= theta ||b||, then FP32 iterations without residual
 //                replacement; the shifted directions are FP64 in the first
@@ -723,18 +881,32 @@ template <int BC> struct Solve {
     // rel: FP64 reliable updates (needs xlo, xhi, t64).  theta2 > 0: return once
     // every active right-hand side has ||r||^2 <= theta2 ||b||^2.
     // fixed > 0: exactly `fixed` iterations, no checks (Lanczos).
-    template <typename T, typename TS>
+    // a half-format field of this solve passed through a float2 pointer
+    template <typename HT> HF<HT> hfield(void *f) const {
+        typename HT::h2 *v = (typename HT::h2 *)f;
+        return HF<HT>{v, (float *)(v + nfield)};
+    }
+
+    // HT (H16 or B16, T = float): p and t are half-format fields (components,
+    // then norms) passed through the float2 pointers.
+    template <typename T, typename TS, typename HT = void>
     int phase(typename cplx_t<T>::type *p, typename cplx_t<T>::type *t, typename cplx_t<T>::type *r,
               typename cplx_t<T>::type *xlo, double2 *xhi, double2 *t64, typename cplx_t<TS>::type *ps, bool init,
               bool rel, double theta2, int fixed, int max_iter) {
         typedef typename cplx_t<T>::type C;
+        constexpr bool half = !std::is_void<HT>::value;
         constexpr int NR = NRSel<T, BC>::value;
         const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
         const int GN = (ntiles_n + TPB - 1) / TPB;
         const dim3 grid(G, nchunk), gsup(Gs, nchunk), gridn(GN, nchunk);
         const int TH = TileMap<BC>::THREADS, THN = TileMap<BC, NR>::THREADS;
         const int sblocks = B;
-        const double delta2 = rel ? ctx->opt.reliable_delta * ctx->opt.reliable_delta : 0.0;
+        // Half-storage iterations replace the residual at least every 10x drop:
+        // their iterated residual drifts from the true one by about the format's
+        // rounding times the condition number per iteration, so a 1000x drop
+        // (the FP32 default) would outlast its meaning.
+        const double delta = half ? std::max(ctx->opt.reliable_delta, 0.1) : ctx->opt.reliable_delta;
+        const double delta2 = rel ? delta * delta : 0.0;
         const Geom g = ctx->geom;
         const T kappa = (T)ctx->opt.kappa;
         const C *U = (const C *)Links<T>::get(ctx);
@@ -742,14 +914,45 @@ template <int BC> struct Solve {
         const int per_iter = 5 + (shifts ? 1 : 0);
         const bool hi = sizeof(T) != sizeof(float); // FP64 or float-float iterations
         if (init) {
-            k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
+            if constexpr (half)
+                k_init_h<HT, BC><<<grid, TH, 0, st>>>(g, src, (float2 *)r, hfield<HT>(p), (float2 *)xlo, xhi, part0, G);
+            else
+                k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
             s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, sqrt(tol2));
             if (shifts)
                 k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r,
                                                         ps, y, sc, sp, Gs, 1);
             ctx->launches += 2 + (shifts ? 1 : 0);
         }
+        auto iteration_half = [&](int k) {
+            if constexpr (half) {
+                typedef typename HT::h2 H2;
+                const H2 *Uh = (const H2 *)HLinks<HT>::get(ctx);
+                const HF<HT> hp = hfield<HT>(p), ht = hfield<HT>(t);
+                if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
+                k_apply_a_h<HT, BC><<<grid, TH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, G);
+                if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
+                s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, part1, sc, sp);
+                if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
+                if (rel)
+                    k_apply_b_h<HT, BC, true><<<grid, TH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo, sc.alpha,
+                                                                   sp.s0, (float)kappa, part2, G);
+                else
+                    k_apply_b_h<HT, BC, false><<<grid, TH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo,
+                                                                    sc.alpha, sp.s0, (float)kappa, part2, G);
+                if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+                s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, delta2, theta2);
+                if (shifts)
+                    k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class,
+                                                            r, ps, y, sc, sp, Gs, 0);
+                k_update_p_h<HT, BC><<<grid, TH, 0, st>>>(V, (const float2 *)r, hp, sc.beta, sc.upd_rhs, G);
+            }
+        };
         auto iteration = [&](int k) {
+            if constexpr (half) {
+                iteration_half(k);
+                return;
+            }
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
             k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(g, U, p, t, kappa, part0, part1, GN);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
@@ -930,6 +1133,28 @@ template <int BC> struct Solve {
                                                      max_iter);
                 if (rc) return rc;
             }
+        } else if (spec.prec == SMPQ_FP16N || spec.prec == SMPQ_BF16N) {
+            // p and t in the half format, the rest as in the FP32 path
+            const size_t hb = (half_field_bytes(S.V, S.B) + 255) / 256 * 256;
+            if ((rc = ensure(ctx, ws[W_P], hb))) return rc;
+            if ((rc = ensure(ctx, ws[W_T], hb))) return rc;
+            if ((rc = ensure(ctx, ws[W_R], nf * sizeof(float2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XLO], nf * sizeof(float2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(double2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T64], nf * sizeof(double2)))) return rc;
+            if (shifts) {
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(float2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
+            }
+            S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            float2 *pp = (float2 *)ws[W_P].p, *tt = (float2 *)ws[W_T].p, *rr = (float2 *)ws[W_R].p;
+            float2 *xl = (float2 *)ws[W_XLO].p, *ps = shifts ? (float2 *)ws[W_PS].p : nullptr;
+            double2 *xh = (double2 *)ws[W_XHI].p, *t64 = (double2 *)ws[W_T64].p;
+            if (spec.prec == SMPQ_BF16N)
+                rc = S.template phase<float, float, B16>(pp, tt, rr, xl, xh, t64, ps, true, true, 0.0, fixed, max_iter);
+            else
+                rc = S.template phase<float, float, H16>(pp, tt, rr, xl, xh, t64, ps, true, true, 0.0, fixed, max_iter);
+            if (rc) return rc;
         } else {
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(float2)))) return rc;
             if ((rc = ensure(ctx, ws[W_T], nf * sizeof(float2)))) return rc;

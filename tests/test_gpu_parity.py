@@ -84,6 +84,7 @@ def test_dslash_fp32(S):
 # 0 and 1 with row 2 = conj(row 0 x row 1), FP32 arithmetic.
 # Largest rounding error of a stored value in [-1, 1]: half the spacing below 1.
 HALF_UNIT = {"fp16": 2.0 ** -12, "bf16": 2.0 ** -9}
+HALF_PREC = ("fp16n", "bf16n")
 
 
 def _round_half(x, fmt):
@@ -255,7 +256,7 @@ def test_unit_links_give_zero(S):
 
 
 @pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed7e-3", "mixed1e-2", "mixed3e-2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed7e-3", "mixed1e-2", "mixed3e-2", "fp16n", "bf16n"])
 def test_qx_8x16_sampled(S, r, classes, prec):
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
@@ -263,7 +264,8 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     zolo, delta = _zolo(a, b)
     colour, n = probing.color_sites(dims, r, 0)
     ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=classes, batch_colours=len(classes))
-    precision = S.SMPQ_MIXED if prec.startswith("mixed") else {"fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32}[prec]
+    precision = S.SMPQ_MIXED if prec.startswith("mixed") else {
+        "fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32, "fp16n": S.SMPQ_FP16N, "bf16n": S.SMPQ_BF16N}[prec]
     switch = float(prec[5:]) if prec.startswith("mixed") else 7e-3
     with _session(S, precision=precision, switch_residual=switch) as s:
         s.load_gauge(dims, U)
@@ -280,6 +282,15 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     # 1e-8 theta); the sum over the 1024 sites of r = 2 meets the 1e-9 bar on Q
     # at the default 7e-3 with a wide margin, but only at the edge at 1e-2 and
     # not at 3e-2, so those two are informational here
+    # The half-storage paths (FP16 / BF16 D_W input and output with per-site
+    # norms, FP64 reliable updates) have the same kind of floor at the format's
+    # rounding u (2^-12, 2^-9): held to 2 u per site, Q not checked.
+    if prec in HALF_PREC:
+        u = HALF_UNIT[prec[:4]]
+        print("    |Q - Q_oracle| = %.3e (%d sites), per-site bound 2 u = %.2e" % (
+            abs(Q - ref.real[mask].sum()), mask.sum(), 2 * u))
+        assert err <= 2 * u
+        return
     tol = 1e-5 if prec == "fp32" else 1e-8
     assert err <= tol
     qtol = {"fp32": 1e-4, "mixed1e-2": 3e-9, "mixed3e-2": 1e-7}.get(prec, 1e-9)
