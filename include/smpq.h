@@ -76,7 +76,8 @@ typedef struct {
     double tol;            /* per-shift relative residual |zeta_i| ||r|| / ||b|| */
     int max_iter;          /* CG iteration cap */
     int precision;         /* smpq_precision */
-    double reliable_delta; /* FP32 path: replace the residual when ||r|| < delta * max ||r|| */
+    double reliable_delta; /* FP32 path: replace the residual when ||r|| < delta * max ||r||
+                              (SMPQ_FP16N / SMPQ_BF16N use at least 0.1) */
     int bc[4];             /* fermion boundary factors per direction */
     int rhs_block;         /* right-hand sides per solve batch (multiple of 12; 0 = automatic) */
     int iters_per_check;   /* CG iterations launched between host convergence checks */
