@@ -74,3 +74,13 @@ def test_colouring_point_sources():
     assert n == 256
     with pytest.raises(S.SmpqError):
         S.smpq_colour_sites(dims, 8, 0)  # 8 does not divide 4
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/smpq.h (status codes, precisions) has the same
+    value in the Python binding."""
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(SMPQ_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt))
+    assert {"SMPQ_FP64", "SMPQ_FP32", "SMPQ_MIXED", "SMPQ_FP16N", "SMPQ_BF16N", "SMPQ_OK", "SMPQ_EINVAL"} <= set(enums)
+    for name, value in enums.items():
+        assert getattr(S, name) == value, name
