@@ -195,3 +195,126 @@ __device__ __forceinline__ float st_site_half(typename HT::h2 *__restrict__ q, f
     *nrm = tiny ? 0.f : mx;
     return mx;
 }
+
+// ---------------------------------------------------------------- two columns in packed lanes
+// Two adjacent right-hand-side columns per thread, held as the two lanes of
+// packed FP32 instructions (FFMA2, FADD2, FMUL2 on sm_100 and later): every
+// complex value is a pair of float2, .r = (re col 0, re col 1) and .i = (im
+// col 0, im col 1).  Each arithmetic instruction then serves both columns, and
+// a link (loaded and reconstructed once) serves both.
+struct c2 {
+    float2 r, i;
+};
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+template <typename HT> __device__ __forceinline__ c2 ld_c2(const typename HT::h2 *__restrict__ p) {
+    const uint2 q = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = f2_bits<HT>(q.x), b = f2_bits<HT>(q.y);
+    return {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+}
+template <typename HT> __device__ __forceinline__ void st_c2(typename HT::h2 *p, float2 r, float2 i) {
+    *reinterpret_cast<uint2 *>(p) =
+        make_uint2(bits_f2<HT>(make_float2(r.x, i.x)), bits_f2<HT>(make_float2(r.y, i.y)));
+}
+
+// a + g * u * v for a unit u: K = 0: 1, 1: -1, 2: i, 3: -i
+template <int K> __device__ __forceinline__ c2 fma_unit(float g, c2 v, c2 a) {
+    if (K == 0) return {__ffma2_rn(bc2(g), v.r, a.r), __ffma2_rn(bc2(g), v.i, a.i)};
+    if (K == 1) return {__ffma2_rn(bc2(-g), v.r, a.r), __ffma2_rn(bc2(-g), v.i, a.i)};
+    if (K == 2) return {__ffma2_rn(bc2(-g), v.i, a.r), __ffma2_rn(bc2(g), v.r, a.i)};
+    return {__ffma2_rn(bc2(g), v.i, a.r), __ffma2_rn(bc2(-g), v.r, a.i)};
+}
+// S_mu (l0, l1) = (u0 l_{J0}, u1 l_{J1}) and S_mu^dag (w0, w1) = (v0 w_{D0}, v1 w_{D1});
+// unit codes as in fma_unit
+template <int MU> struct SPerm {
+    static constexpr int J0 = (MU == 0 || MU == 1) ? 1 : 0, J1 = 1 - J0;
+    static constexpr int U0 = MU == 0 ? 3 : MU == 1 ? 1 : MU == 2 ? 3 : 0;
+    static constexpr int U1 = MU == 0 ? 3 : MU == 1 ? 0 : MU == 2 ? 2 : 0;
+    static constexpr int D0 = J0, D1 = J1;
+    static constexpr int V0 = MU == 0 ? 2 : MU == 1 ? 0 : MU == 2 ? 2 : 0;
+    static constexpr int V1 = MU == 0 ? 2 : MU == 1 ? 1 : MU == 2 ? 3 : 0;
+};
+
+template <typename HT, int MU, int SG, bool BACK, int BC>
+__device__ __forceinline__ void hop_half_c2(const typename HT::h2 *__restrict__ U, const typename HT::h2 *__restrict__ in,
+                                            const float *__restrict__ nrm, int Vl, int nb, int ls, bool flip,
+                                            c2 acc[12]) {
+    typedef SPerm<MU> P;
+    const typename HT::h2 *q = in + (size_t)nb * (12 * BC);
+    float2 f = *reinterpret_cast<const float2 *>(nrm + (size_t)nb * BC);
+    if (flip) f = make_float2(-f.x, -f.y);
+    const float g = (float)SG;
+    c2 h0[3], h1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const c2 p0 = ld_c2<HT>(q + a * BC), p1 = ld_c2<HT>(q + (3 + a) * BC);
+        const c2 p2 = ld_c2<HT>(q + (6 + a) * BC), p3 = ld_c2<HT>(q + (9 + a) * BC);
+        h0[a] = fma_unit<P::U0>(g, P::J0 ? p3 : p2, p0);
+        h1[a] = fma_unit<P::U1>(g, P::J1 ? p3 : p2, p1);
+    }
+    float2 m[3][3];
+    load_link12<HT>(U, (size_t)MU * Vl + ls, m);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c2 w0 = {bc2(0.f), bc2(0.f)}, w1 = w0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 e = BACK ? m[b][a] : m[a][b]; // W_ab = conj(U_ba) for BACK
+            const float2 ex = bc2(e.x), ey = bc2(BACK ? -e.y : e.y), ney = bc2(BACK ? e.y : -e.y);
+            w0.r = __ffma2_rn(ex, h0[b].r, __ffma2_rn(ney, h0[b].i, w0.r));
+            w0.i = __ffma2_rn(ex, h0[b].i, __ffma2_rn(ey, h0[b].r, w0.i));
+            w1.r = __ffma2_rn(ex, h1[b].r, __ffma2_rn(ney, h1[b].i, w1.r));
+            w1.i = __ffma2_rn(ex, h1[b].i, __ffma2_rn(ey, h1[b].r, w1.i));
+        }
+        w0 = {__fmul2_rn(f, w0.r), __fmul2_rn(f, w0.i)};
+        w1 = {__fmul2_rn(f, w1.r), __fmul2_rn(f, w1.i)};
+        acc[a] = {__fadd2_rn(acc[a].r, w0.r), __fadd2_rn(acc[a].i, w0.i)};
+        acc[3 + a] = {__fadd2_rn(acc[3 + a].r, w1.r), __fadd2_rn(acc[3 + a].i, w1.i)};
+        acc[6 + a] = fma_unit<P::V0>(g, P::D0 ? w1 : w0, acc[6 + a]);
+        acc[9 + a] = fma_unit<P::V1>(g, P::D1 ? w1 : w0, acc[9 + a]);
+    }
+}
+
+template <typename HT, int MU, bool DAG, int BC>
+__device__ __forceinline__ void hop_dir_half_c2(const Geom &g, const SiteCoords &xc, const typename HT::h2 *U,
+                                                const typename HT::h2 *in, const float *nrm, int s, c2 acc[12]) {
+    const int n = g.n[MU], st = g.stride[MU], c = xc.x[MU];
+    const bool top = c == n - 1, bot = c == 0;
+    const int nf = top ? s - (n - 1) * st : s + st;
+    const int nbk = bot ? s + (n - 1) * st : s - st;
+    hop_half_c2<HT, MU, DAG ? +1 : -1, false, BC>(U, in, nrm, g.V, nf, s, top && g.bcf[MU] < 0, acc);
+    hop_half_c2<HT, MU, DAG ? -1 : +1, true, BC>(U, in, nrm, g.V, nbk, nbk, bot && g.bcf[MU] < 0, acc);
+}
+
+// acc = hop(s) for two columns (packed lanes) of a half-format field
+template <typename HT, bool DAG, int BC>
+__device__ __forceinline__ void wilson_hop_half_c2(const Geom &g, const typename HT::h2 *__restrict__ U,
+                                                   const typename HT::h2 *__restrict__ in,
+                                                   const float *__restrict__ nrm, int s, c2 acc[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = {bc2(0.f), bc2(0.f)};
+    const SiteCoords xc(g, s);
+    hop_dir_half_c2<HT, 0, DAG, BC>(g, xc, U, in, nrm, s, acc);
+    hop_dir_half_c2<HT, 1, DAG, BC>(g, xc, U, in, nrm, s, acc);
+    hop_dir_half_c2<HT, 2, DAG, BC>(g, xc, U, in, nrm, s, acc);
+    hop_dir_half_c2<HT, 3, DAG, BC>(g, xc, U, in, nrm, s, acc);
+}
+
+// store the 12 components of two columns at one site (packed lanes) with
+// their norms; sites below the smallest normal FP32 number are stored as zero
+template <typename HT, int BC>
+__device__ __forceinline__ void st_site_half_c2(typename HT::h2 *__restrict__ q, float *__restrict__ nrm,
+                                                const c2 v[12]) {
+    float mx0 = 0.f, mx1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        mx0 = fmaxf(mx0, fmaxf(fabsf(v[c].r.x), fabsf(v[c].i.x)));
+        mx1 = fmaxf(mx1, fmaxf(fabsf(v[c].r.y), fabsf(v[c].i.y)));
+    }
+    if (!(mx0 >= 1.17549435e-38f)) mx0 = 0.f;
+    if (!(mx1 >= 1.17549435e-38f)) mx1 = 0.f;
+    const float2 inv = make_float2(mx0 > 0.f ? 1.f / mx0 : 0.f, mx1 > 0.f ? 1.f / mx1 : 0.f);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) st_c2<HT>(q + c * BC, __fmul2_rn(inv, v[c].r), __fmul2_rn(inv, v[c].i));
+    *reinterpret_cast<float2 *>(nrm) = make_float2(mx0, mx1);
+}

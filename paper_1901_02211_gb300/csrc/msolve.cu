@@ -456,6 +456,109 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     }
 }
 
+// Two columns per thread (the packed lanes of half.cuh) forms of k_apply_a_h
+// and k_apply_b_h, used for even tile widths: half the FP32 instructions and
+// one link reconstruction per two columns; r and x_lo move as 16-byte pairs.
+template <int BC> __device__ __forceinline__ void ld_rx2(const float2 *p, float2 &re, float2 &im) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    re = make_float2(q.x, q.z);
+    im = make_float2(q.y, q.w);
+}
+template <int BC> __device__ __forceinline__ void st_rx2(float2 *p, float2 re, float2 im) {
+    *reinterpret_cast<float4 *>(p) = make_float4(re.x, im.x, re.y, im.y);
+}
+
+template <typename HT, int BC>
+__global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
+    k_apply_a_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
+                 double *part_p, int G) {
+    typedef TileMap<BC, 2> TM;
+    __shared__ double sm[SmemCols<BC, 2>::N];
+    const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y;
+    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    double at[2] = {0, 0}, ap[2] = {0, 0};
+    const float2 nk = bc2(-kappa);
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        const int s = tile * TM::SPB + threadIdx.x / TM::TPS;
+        if (s >= g.V) continue;
+        c2 acc[12];
+        wilson_hop_half_c2<HT, false, BC>(g, U, p.v + base, p.n + nbase, s, acc);
+        const typename HT::h2 *ps = p.v + base + (size_t)s * 12 * BC;
+        const float2 np = *reinterpret_cast<const float2 *>(p.n + nbase + (size_t)s * BC);
+        float2 sp = bc2(0.f), st = bc2(0.f);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const c2 f = ld_c2<HT>(ps + c * BC);
+            const float2 vr = __fmul2_rn(np, f.r), vi = __fmul2_rn(np, f.i);
+            sp = __ffma2_rn(vr, vr, __ffma2_rn(vi, vi, sp));
+            acc[c].r = __ffma2_rn(nk, acc[c].r, vr);
+            acc[c].i = __ffma2_rn(nk, acc[c].i, vi);
+            st = __ffma2_rn(acc[c].r, acc[c].r, __ffma2_rn(acc[c].i, acc[c].i, st));
+        }
+        st_site_half_c2<HT, BC>(t.v + base + (size_t)s * 12 * BC, t.n + nbase + (size_t)s * BC, acc);
+        at[0] += (double)st.x;
+        at[1] += (double)st.y;
+        ap[0] += (double)sp.x;
+        ap[1] += (double)sp.y;
+    }
+    const double s1 = block_total<BC, 2>(at, sm);
+    const double s2 = block_total<BC, 2>(ap, sm);
+    if (threadIdx.x < BC) {
+        part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
+    }
+}
+
+template <typename HT, int BC, bool REL>
+__global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
+    k_apply_b_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
+                 float2 *__restrict__ xlo, const double *__restrict__ alpha, double s0, float kappa, double *part_r,
+                 int G) {
+    typedef TileMap<BC, 2> TM;
+    __shared__ double sm[SmemCols<BC, 2>::N];
+    const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y, j = chunk * BC + jj;
+    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    const float2 a = make_float2((float)alpha[j], (float)alpha[j + 1]), na = make_float2(-a.x, -a.y);
+    const float2 sh = bc2((float)s0), nk = bc2(-kappa);
+    double ar[2] = {0, 0};
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        const int s = tile * TM::SPB + threadIdx.x / TM::TPS;
+        if (s >= g.V) continue;
+        c2 acc[12];
+        wilson_hop_half_c2<HT, true, BC>(g, U, t.v + base, t.n + nbase, s, acc);
+        const typename HT::h2 *ts = t.v + base + (size_t)s * 12 * BC, *pq = p.v + base + (size_t)s * 12 * BC;
+        const float2 nt = *reinterpret_cast<const float2 *>(t.n + nbase + (size_t)s * BC);
+        const float2 np = *reinterpret_cast<const float2 *>(p.n + nbase + (size_t)s * BC);
+        float2 sr = bc2(0.f);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = base + ((size_t)s * 12 + c) * BC;
+            const c2 tf = ld_c2<HT>(ts + c * BC), pf = ld_c2<HT>(pq + c * BC);
+            const float2 pr = __fmul2_rn(np, pf.r), pi = __fmul2_rn(np, pf.i);
+            // A p = D_W^dag t + s0 p
+            const float2 apr = __ffma2_rn(sh, pr, __ffma2_rn(nk, acc[c].r, __fmul2_rn(nt, tf.r)));
+            const float2 api = __ffma2_rn(sh, pi, __ffma2_rn(nk, acc[c].i, __fmul2_rn(nt, tf.i)));
+            float2 rr, ri;
+            ld_rx2<BC>(r + o, rr, ri);
+            rr = __ffma2_rn(na, apr, rr);
+            ri = __ffma2_rn(na, api, ri);
+            st_rx2<BC>(r + o, rr, ri);
+            sr = __ffma2_rn(rr, rr, __ffma2_rn(ri, ri, sr));
+            if (REL) {
+                float2 xr, xi;
+                ld_rx2<BC>(xlo + o, xr, xi);
+                st_rx2<BC>(xlo + o, __ffma2_rn(a, pr, xr), __ffma2_rn(a, pi, xi));
+            }
+        }
+        ar[0] += (double)sr.x;
+        ar[1] += (double)sr.y;
+    }
+    const double s1 = block_total<BC, 2>(ar, sm);
+    if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+}
+
 // Shifted updates on the support: y += c_i alpha_i p_i ; p_i = zeta_new_i r + beta_i p_i.
 // Support entry k of rhs j sits on lattice site supsite[rhs_class[j] * n_sup + k]
 // (identity when supsite == nullptr).  r is read in the iteration precision T,
@@ -924,24 +1027,37 @@ template <int BC> struct Solve {
                                                         ps, y, sc, sp, Gs, 1);
             ctx->launches += 2 + (shifts ? 1 : 0);
         }
+        // two columns per thread for even tiles (SMPQ_HALF_SOLVE_NR=1: one)
+#ifndef SMPQ_HALF_SOLVE_NR
+#define SMPQ_HALF_SOLVE_NR 2
+#endif
+        constexpr bool h2cols = SMPQ_HALF_SOLVE_NR == 2 && BC % 2 == 0;
+        typedef TileMap<BC, h2cols ? 2 : 1> TMH;
+        const int GH = h2cols ? ((V + TMH::SPB - 1) / TMH::SPB + TPB - 1) / TPB : G;
+        const dim3 gridh(GH, nchunk);
         auto iteration_half = [&](int k) {
             if constexpr (half) {
                 typedef typename HT::h2 H2;
                 const H2 *Uh = (const H2 *)HLinks<HT>::get(ctx);
                 const HF<HT> hp = hfield<HT>(p), ht = hfield<HT>(t);
+                constexpr int THH = TMH::THREADS;
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-                k_apply_a_h<HT, BC><<<grid, TH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, G);
+                if constexpr (h2cols)
+                    k_apply_a_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH);
+                else
+                    k_apply_a_h<HT, BC><<<grid, TH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, G);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-                s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, part1, sc, sp);
+                s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GH, part0, part1, sc, sp);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
-                if (rel)
+                // (half-storage solves always run with reliable updates)
+                if constexpr (h2cols)
+                    k_apply_b_h2<HT, BC, true><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo,
+                                                                      sc.alpha, sp.s0, (float)kappa, part2, GH);
+                else
                     k_apply_b_h<HT, BC, true><<<grid, TH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo, sc.alpha,
                                                                    sp.s0, (float)kappa, part2, G);
-                else
-                    k_apply_b_h<HT, BC, false><<<grid, TH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo,
-                                                                    sc.alpha, sp.s0, (float)kappa, part2, G);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-                s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, delta2, theta2);
+                s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GH, part2, sc, sp, tol2, delta2, theta2);
                 if (shifts)
                     k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class,
                                                             r, ps, y, sc, sp, Gs, 0);
