@@ -19,8 +19,16 @@ Metric: q(x) sites/s = sites of the lattice / step time.
           its shifted systems keep an FP32 error floor);
   fp64_plain / fp64_batched : the FP64 path one source at a time / batched,
           timed on a sample of classes and scaled to all classes;
-  roofline : the dominant solver kernel's algorithmic bytes / CUDA-event time;
+  roofline : the dominant solver kernel's algorithmic bytes / CUDA-event time
+          against the measured HBM bandwidth; its arithmetic rate against the
+          measured FP32 (or FP64) peak as the secondary `alu` entry;
   cpu_baseline : the FP64 oracle on the host cores on one class (12 sources).
+
+The timed steps run as a user runs them (CUDA graphs on, no per-launch
+events); one further step with per-launch CUDA events gives the kernel times
+of the roofline, and one with the true_residual option the FP64 true residual.
+The Zolotarev interval comes from the GPU Lanczos estimate
+(smpq_measure_spectrum), timed as setup.
 
 Multi-GPU (torchrun, N ranks): every rank evaluates its own configuration
 (independent problems, no collective on the data path) -> weak scaling.
@@ -53,12 +61,6 @@ FP64_FLOP_A = 1320 + 48
 FP64_FLOP_B = 1320 + 96
 R_MIN, MODE = 4, 0
 KAPPA = 0.21
-
-
-def _spectrum(name):
-    with open(os.path.join(ROOT, "tests", "golden", "spectra.json")) as f:
-        sp = json.load(f)[name]
-    return 0.98 * sp["lmin2"], 1.02 * sp["lmax2"]
 
 
 def _peaks():
@@ -193,7 +195,25 @@ def cpu_oracle_sample(U, dims, a, b, n_classes=1, tol=1e-10, rmin=R_MIN):
     return sites / dt, sites, dt, native.threads()
 
 
+def _oracle_interval(name, U, dims):
+    """Zolotarev interval for the CPU legs: the oracle's ARPACK spectrum, stored
+    by tests/golden/make_spectra.py when there is one, else computed here."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "spectra.json")) as f:
+            sp = json.load(f)[name]
+        return 0.98 * sp["lmin2"], 1.02 * sp["lmax2"]
+    except KeyError:
+        from oracle import spectrum
+        lo, hi = spectrum.h2_extremes(U, dims, KAPPA, tol=1e-8)
+        return 0.98 * lo, 1.02 * hi
+
+
 def run_reference(args):
+    """The oracle (plain FP64 CPU code) as the reference arm: each step is one
+    colour class (12 sources and its sites) of the workload, on all host cores.
+    value = the sites of that sample per second it took; ms_per_step = the
+    measured time of one sample step (a whole-lattice step would take
+    N_p times as long: that extrapolation is labelled, not reported as the step)."""
     ws, rank, local = _dist()
     if rank != 0:
         return
@@ -202,35 +222,88 @@ def run_reference(args):
     native.build()
     cfg = make_config(args.config)
     U, dims = cfg["U"], cfg["dims"]
-    try:
-        a, b = _spectrum(args.config)
-    except KeyError:  # no stored spectrum for this workload: ARPACK in the oracle
-        from oracle import spectrum
-        lo, hi = spectrum.h2_extremes(U, dims, KAPPA, tol=1e-8)
-        a, b = 0.98 * lo, 1.02 * hi
+    a, b = _oracle_interval(args.config, U, dims)
     V = int(np.prod(dims))
     n_cls = args.rmin ** 4
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; bounded steps only
-    vals = []
-    t_all = 0.0
+    vals, secs = [], []
     for _ in range(args.steps):
         v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1, rmin=args.rmin)
         vals.append(v)
-        t_all += dt
+        secs.append(dt)
     value = float(np.median(vals))
     line = {
         "impl": "reference", "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * V / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.median(secs)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": _workload_name(args),
-                   "sample": "1 colour class (12 sources, %d sites) per step" % sites},
+                   "sample": "each step: 1 colour class (12 sources, %d of %d sites)" % (sites, V),
+                   "whole_lattice_step_ms_extrapolated": 1000.0 * V / value},
         "cpu_baseline": {"value": value, "unit": "sites/s", "cores": thr, "kind": "oracle",
                          "sample": "1 of %d colour classes per step (12 sources, %d sites), FP64, tol 1e-10"
                                    % (n_cls, sites)},
         "e2e": {"value": value, "unit": "sites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _alu_peaks(dev):
+    """Measured FP32 (packed two-lane, the form the float-float kernels issue)
+    and FP64 multiply-add lane rates of this GPU (smpq_alu_peak)."""
+    from paper_1901_02211_gb300 import smpq
+    try:
+        return {"fp32_lane_ops_per_s": smpq.smpq_alu_peak(dev, smpq.ALU_FP32X2),
+                "fp32_scalar_lane_ops_per_s": smpq.smpq_alu_peak(dev, smpq.ALU_FP32),
+                "fp64_fma_per_s": smpq.smpq_alu_peak(dev, smpq.ALU_FP64)}
+    except Exception as e:  # reported, never invented
+        return {"error": str(e)}
+
+
+def _kernel_table(prec, stats, V, B, peak_hbm, peak_kind, alu):
+    """Per solver kernel: average CUDA-event time per launch (profiled step),
+    algorithmic bytes per launch (spinor fields read and written + links, as in
+    the module docstring of msolve.cu) against the measured HBM bandwidth, and
+    for the FP64-accurate kernels their arithmetic against the measured ALU peak."""
+    from paper_1901_02211_gb300 import smpq
+    link32, link64 = 4 * 9 * 8, 4 * 9 * 16
+    b_vecs = 6 if prec == smpq.SMPQ_FP32 else 4  # t, p, r (+ x_lo) read, r (+ x_lo) written
+    half = prec in (smpq.SMPQ_FP16N, smpq.SMPQ_BF16N)
+    lo = {smpq.SMPQ_FP16N: "fp16n", smpq.SMPQ_BF16N: "bf16n"}.get(prec, "fp32")
+    kern = {}
+    for key, ms_k, n_k, esz_k, nvec in (
+            ("k_apply_a[%s]" % lo, "dslash_ms", "dslash_launches", 8, 2),
+            ("k_apply_b[%s]" % lo, "update_ms", "update_launches", 8, b_vecs),
+            ("k_apply_a[fp64-accurate]", "dslash_hi_ms", "dslash_hi_launches", 16, 2),
+            ("k_apply_b[fp64-accurate]", "update_hi_ms", "update_hi_launches", 16, 4)):
+        tot = sum(x[ms_k] for x in stats)
+        n = sum(x[n_k] for x in stats)
+        if not n or tot <= 0:
+            continue
+        if half and esz_k == 8:
+            # half-format p and t (52 bytes per site and source with the norm),
+            # FP32 r and x_lo (96 bytes each, read and written in k_apply_b),
+            # reconstruct-12 links (96 bytes per site)
+            nbytes = V * B * (2 * 52 if key.startswith("k_apply_a") else 2 * 52 + 4 * 96) + V * 96
+        else:
+            nbytes = V * B * nvec * 12 * esz_k + V * (link32 if esz_k == 8 else link64)
+        ms = tot / n
+        k = dict(ms=ms, n=n, share_ms=tot / len(stats), bytes=nbytes, bound="hbm", unit="GB/s", peak=peak_hbm,
+                 peak_source=peak_kind, achieved=nbytes / (ms / 1000.0) / 1e9)
+        if esz_k == 16 and prec == smpq.SMPQ_MIXED and "fp32_lane_ops_per_s" in alu:  # float-float
+            ops = V * B * (DF64_OPS_A if key.startswith("k_apply_a") else DF64_OPS_B)
+            pk = alu["fp32_lane_ops_per_s"] / 1e12
+            k["alu"] = dict(achieved=ops / (ms / 1000.0) / 1e12, peak=pk, unit="T FP32 lane-ops/s",
+                            frac=ops / (ms / 1000.0) / 1e12 / pk, algorithmic=ops,
+                            peak_source="measured (smpq_alu_peak, packed FFMA2 probe)")
+        elif esz_k == 16 and "fp64_fma_per_s" in alu:  # native FP64
+            fl = V * B * (FP64_FLOP_A if key.startswith("k_apply_a") else FP64_FLOP_B)
+            pk = 2 * alu["fp64_fma_per_s"] / 1e12
+            k["alu"] = dict(achieved=fl / (ms / 1000.0) / 1e12, peak=pk, unit="TFLOP/s (FP64)",
+                            frac=fl / (ms / 1000.0) / 1e12 / pk, algorithmic=fl,
+                            peak_source="measured (smpq_alu_peak, DFMA probe, 2 flop each)")
+        kern[key] = k
+    return kern
 
 
 def run_gpu(args):
@@ -256,22 +329,18 @@ def run_gpu(args):
                           "dslash": _dslash_formats(s, V, args.dslash_columns)}), flush=True)
         s.close()
         return
-    spectrum_note = "oracle ARPACK (tests/golden/spectra.json), widened 0.98/1.02"
-    try:
-        a, b = _spectrum(args.config)
-    except KeyError:  # no oracle spectrum for this workload: Lanczos on the GPU (the production setup step)
-        probe = Session(device=dev, stream=stream)
-        probe.load_gauge(dims, U)
-        lo, hi = probe.measure_spectrum(300)
-        probe.close()
-        a, b = 0.98 * lo, 1.02 * hi
-        spectrum_note = "GPU Lanczos (smpq_measure_spectrum, 300 steps), widened 0.98/1.02"
     prec = {"fp32": smpq.SMPQ_FP32, "fp64": smpq.SMPQ_FP64, "mixed": smpq.SMPQ_MIXED, "fp16n": smpq.SMPQ_FP16N,
             "bf16n": smpq.SMPQ_BF16N}[args.precision]
 
     s = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
-                use_graphs=1, profile=1, switch_residual=args.switch, autotune=0 if args.no_autotune else 1)
+                use_graphs=1, profile=0, switch_residual=args.switch, autotune=0 if args.no_autotune else 1)
     s.load_gauge(dims, U)
+    # setup, timed on its own: the Zolotarev interval from the GPU Lanczos estimate
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lo, hi = s.measure_spectrum(args.lanczos)
+    spectrum_s = time.perf_counter() - t0
+    a, b = 0.98 * lo, 1.02 * hi
     s.set_spectrum(a, b)
     n_classes = s.build_sources(args.rmin, MODE)
     q_re = torch.zeros(V, dtype=torch.float64, device="cuda")
@@ -307,56 +376,22 @@ def run_gpu(args):
         ms = max_over_ranks(ms, "cuda")
     value = ws * V_step / (ms / 1000.0)
     clocks = clk.summary()
-
-    # dominant kernel: average CUDA-event duration per launch over the timed steps,
-    # FP32 iterations and FP64-accurate (FP64 or float-float) iterations separately
-    B = stats[-1]["n_rhs"] // max(1, stats[-1]["n_batches"])
-    link32, link64 = 4 * 9 * 8, 4 * 9 * 16
-    b_vecs = 6 if prec == smpq.SMPQ_FP32 else 4  # t, p, r (+ x_lo) read, r (+ x_lo) written
-    kern = {}
-    half = prec in (smpq.SMPQ_FP16N, smpq.SMPQ_BF16N)
-    lo = {smpq.SMPQ_FP16N: "fp16n", smpq.SMPQ_BF16N: "bf16n"}.get(prec, "fp32")
-    for key, ms_k, n_k, esz_k, nvec in (
-            ("k_apply_a[%s]" % lo, "dslash_ms", "dslash_launches", 8, 2),
-            ("k_apply_b[%s]" % lo, "update_ms", "update_launches", 8, b_vecs),
-            ("k_apply_a[fp64-accurate]", "dslash_hi_ms", "dslash_hi_launches", 16, 2),
-            ("k_apply_b[fp64-accurate]", "update_hi_ms", "update_hi_launches", 16, 4)):
-        tot = sum(x[ms_k] for x in stats)
-        n = sum(x[n_k] for x in stats)
-        if n and half and esz_k == 8:
-            # half-format p and t (52 bytes per site and source with the norm),
-            # FP32 r and x_lo (96 bytes each, read and written in k_apply_b),
-            # reconstruct-12 links (96 bytes per site)
-            nbytes = V * B * (2 * 52 if key.startswith("k_apply_a") else 2 * 52 + 4 * 96) + V * 96
-            kern[key] = dict(ms=tot / n, n=n, share_ms=tot, bytes=nbytes)
-        elif n:
-            kern[key] = dict(ms=tot / n, n=n, share_ms=tot,
-                             bytes=V * B * nvec * 12 * esz_k + V * (link32 if esz_k == 8 else link64))
-    dom = max(kern, key=lambda k: kern[k]["share_ms"])
-    esz = 8 if prec == smpq.SMPQ_FP32 else 16
-    peak_hbm, peak_kind = _peaks()
-    # Rooflines: the FP32 kernels are bounded by HBM bandwidth; the FP64-accurate
-    # ones by arithmetic -- float-float runs on the FP32 pipes (152 SMs x 128
-    # lanes x clock, one lane-operation per FP32 instruction), native FP64 on
-    # the FP64 units (1.25 TFLOP/s nominal).  Algorithmic operation counts per
-    # site and source are the DF64_OPS_* and FP64_FLOP_* constants above.
-    for key, k in kern.items():
-        if "fp32" in key or "16n" in key:
-            k.update(bound="hbm", unit="GB/s", peak=peak_hbm, peak_source=peak_kind,
-                     achieved=k["bytes"] / (k["ms"] / 1000.0) / 1e9, algorithmic=k["bytes"])
-        elif prec == smpq.SMPQ_MIXED:  # float-float
-            ops = V * B * (DF64_OPS_A if key.startswith("k_apply_a") else DF64_OPS_B)
-            clk = (clocks.get("sm_mhz") or 2070.0) * 1e6
-            k.update(bound="alu", unit="T FP32 lane-ops/s", peak=152 * 128 * clk / 1e12,
-                     peak_source="152 SMs x 128 FP32 lanes x median SM clock under load",
-                     achieved=ops / (k["ms"] / 1000.0) / 1e12, algorithmic=ops)
-        else:  # native FP64
-            fl = V * B * (FP64_FLOP_A if key.startswith("k_apply_a") else FP64_FLOP_B)
-            k.update(bound="alu", unit="TFLOP/s (FP64)", peak=1.25, peak_source="nominal GB300 FP64 rate",
-                     achieved=fl / (k["ms"] / 1000.0) / 1e12, algorithmic=fl)
-    peak, ach = kern[dom]["peak"], kern[dom]["achieved"]
-    traffic = _traffic(dom, B)
     launches = sum(x["kernel_launches"] for x in stats)
+
+    # one more step with CUDA events around every D_W launch (graphs off): the
+    # kernel times of the roofline; then one with the FP64 true residual
+    s.set_options(profile=1)
+    Qp, stp = step()
+    s.set_options(profile=0, true_residual=1)
+    Qt, stt = step()
+    s.set_options(true_residual=0)
+    B = stats[-1]["n_rhs"] // max(1, stats[-1]["n_batches"])
+    peak_hbm, peak_kind = _peaks()
+    alu = _alu_peaks(dev)
+    kern = _kernel_table(prec, [stp], V, B, peak_hbm, peak_kind, alu)
+    dom = max(kern, key=lambda k: kern[k]["share_ms"])
+    traffic = _traffic(dom, B)
+    esz = 8 if prec == smpq.SMPQ_FP32 else 16
 
     e2e_val = None
     if args.no_e2e:
@@ -369,12 +404,15 @@ def run_gpu(args):
     if rank == 0 and not args.no_baselines and args.low_modes > 0 and sub is None:
         q_ref = (q_re + 1j * q_im).cpu().numpy()
         out["low_mode_projection"] = _low_modes(args, dims, U, V, a, b, prec, dev, stream, q_ref)
-    out["spectrum"] = {"lmin2": a, "lmax2": b, "source": spectrum_note}
+    out["spectrum"] = {"lmin2": a, "lmax2": b, "lanczos_lmin2": lo, "lanczos_lmax2": hi, "setup_s": spectrum_s,
+                       "source": "GPU Lanczos (smpq_measure_spectrum, %d steps), widened 0.98/1.02" % args.lanczos}
+    out["alu_peaks"] = alu
+    out["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
     if rank == 0 and not args.no_dslash:
         out["dslash"] = _dslash_formats(s, V, B)
     if rank == 0:
-        _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak,
-                peak_kind, traffic, stats, out, sub)
+        _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, traffic, stats, stp,
+                stt, out, sub)
     s.close()
     if ws > 1:
         dist.destroy_process_group()
@@ -573,7 +611,8 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
                 len(cls), n_classes, 12 * len(cls), res[0][2], res[1][2]),
             "max_abs_dq": float(np.abs(res[0][1][mask] - res[1][1][mask]).max())}
         if not args.no_cpu:
-            v, sites, dt, thr = cpu_oracle_sample(U, dims, a, b, 1, rmin=args.rmin)
+            oa, ob = _oracle_interval(args.config, U, dims)
+            v, sites, dt, thr = cpu_oracle_sample(U, dims, oa, ob, 1, rmin=args.rmin)
             out["cpu_baseline"] = {"value": v, "unit": "sites/s", "cores": thr, "kind": "oracle",
                                    "sample": "1 of %d colour classes (12 sources, %d sites), FP64 tol 1e-10, %.1f s"
                                              % (n_classes, sites, dt)}
@@ -593,50 +632,62 @@ def _workload_name(args):
             % (d[0], d[1], d[2], d[3], links, args.rmin, n_cls, 12 * n_cls))
 
 
-def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, ach, peak, peak_kind,
-            traffic, stats, out, sub):
+def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, dom, kern, traffic, stats, stp,
+            stt, out, sub):
     from paper_1901_02211_gb300 import smpq
-    if True:
-        st = stats[-1]
-        line = {
-            "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {smpq.SMPQ_FP32: "f32", smpq.SMPQ_FP64: "f64", smpq.SMPQ_MIXED: "f64+f32",
-                                      smpq.SMPQ_FP16N: "f16+f32", smpq.SMPQ_BF16N: "bf16+f32"}[prec],
-            "data": "synthetic",
-            "config": {"workload": _workload_name(args),
-                       "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
-                                     smpq.SMPQ_FP16N: "FP16 p, t with per-site norms, reconstruct-12 links, FP32 "
-                                                      "r and arithmetic, FP64 reliable updates",
-                                     smpq.SMPQ_BF16N: "BF16 p, t with per-site norms, reconstruct-12 links, FP32 "
-                                                      "r and arithmetic, FP64 reliable updates",
-                                     smpq.SMPQ_FP64: "FP64",
-                                     smpq.SMPQ_MIXED: "FP64-accurate until ||r|| < %g ||b||, then FP32 (shifted vectors too)"
-                                     % args.switch}[prec],
-                       "batch": B, "rhs_tile": int(st.get("rhs_tile", 0)), "l2": "inputs larger than L2 (each solver vector %.1f GB)"
-                       % (V * 12 * B * esz / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
-            "clocks": clocks,
-            "e2e": None if e2e_val is None else {
-                "value": e2e_val, "unit": "sites/s", "h2d_bytes_per_step": int(U.nbytes),
-                "d2h_bytes_per_step": int(2 * V * 8 + 16)},
-            "gpu_launches": int(launches),
-            "roofline": {"bound": kern[dom]["bound"], "kernel": dom, "achieved": ach, "peak": peak,
-                         "unit": kern[dom]["unit"], "frac": ach / peak, "peak_source": kern[dom]["peak_source"],
-                         "traffic": traffic, "algorithmic_per_launch": kern[dom]["algorithmic"],
-                         "avg_launch_ms": kern[dom]["ms"], "launches": kern[dom]["n"]},
-            "roofline_all": {k: {"bound": v["bound"], "achieved": v["achieved"], "peak": v["peak"], "unit": v["unit"],
-                                 "frac": v["achieved"] / v["peak"], "avg_launch_ms": v["ms"], "launches": v["n"]}
-                             for k, v in kern.items()},
-            "solver": {"iterations": st["max_iterations"], "reliable_updates": st["reliable_updates"],
-                       "max_resid": st["max_resid"], "Q": st["Q"], "abs_Q_minus_round": st["q_round_dev"],
-                       "max_im_q": st["max_im_q"],
-                       "kernel_ms": {k: v["share_ms"] / args.steps for k, v in kern.items()},
-                       "kernel_avg_launch_ms": {k: v["ms"] for k, v in kern.items()}},
-        }
-        if sub is not None:
-            line["config"]["workload"] += " (profiling subset: first %d classes)" % len(sub)
-        line.update(out)
-        print(json.dumps(line), flush=True)
+    st = stats[-1]
+    k = kern[dom]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": k["achieved"], "peak": k["peak"], "unit": "GB/s",
+            "frac": k["achieved"] / k["peak"], "peak_source": k["peak_source"], "traffic": traffic,
+            "traffic_over_algorithmic": None if traffic is None else traffic / k["bytes"],
+            "algorithmic_per_launch": k["bytes"], "avg_launch_ms": k["ms"], "launches": k["n"],
+            "timing": "CUDA events around every launch of one profiled step (graphs off), on the launch stream"}
+    if "alu" in k:
+        roof["alu"] = k["alu"]
+    n_iter = max(1, stp["max_iterations"])
+    line = {
+        "metric": "q(x) sites/s", "value": value, "unit": "sites/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {smpq.SMPQ_FP32: "f32", smpq.SMPQ_FP64: "f64", smpq.SMPQ_MIXED: "f64+f32",
+                                  smpq.SMPQ_FP16N: "f16+f32", smpq.SMPQ_BF16N: "bf16+f32"}[prec],
+        "data": "synthetic",
+        "config": {"workload": _workload_name(args),
+                   "precision": {smpq.SMPQ_FP32: "FP32 dslash/vectors + FP64 reliable updates",
+                                 smpq.SMPQ_FP16N: "FP16 p, t with per-site norms, reconstruct-12 links, FP32 "
+                                                  "r and arithmetic, FP64 reliable updates",
+                                 smpq.SMPQ_BF16N: "BF16 p, t with per-site norms, reconstruct-12 links, FP32 "
+                                                  "r and arithmetic, FP64 reliable updates",
+                                 smpq.SMPQ_FP64: "FP64",
+                                 smpq.SMPQ_MIXED: "FP64-accurate until ||r|| < %g ||b||, then FP32 (shifted vectors too)"
+                                 % args.switch}[prec],
+                   "batch": B, "rhs_tile": int(st.get("rhs_tile", 0)),
+                   "l2": "inputs larger than L2 (each solver vector %.1f GB)" % (V * 12 * B * esz / 1e9),
+                   "graphs": "CUDA graphs, %d iterations per host check" % 10,
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "clocks": clocks,
+        "e2e": None if e2e_val is None else {
+            "value": e2e_val, "unit": "sites/s", "h2d_bytes_per_step": int(U.nbytes),
+            "d2h_bytes_per_step": int(2 * V * 8 + 16)},
+        "gpu_launches": int(launches),
+        "launches_per_iteration": (stp["kernel_launches"] / n_iter) if n_iter else None,
+        "roofline": roof,
+        "roofline_all": {kk: {"bound": v["bound"], "achieved": v["achieved"], "peak": v["peak"], "unit": v["unit"],
+                              "frac": v["achieved"] / v["peak"], "avg_launch_ms": v["ms"], "launches": v["n"],
+                              **({"alu_frac": v["alu"]["frac"]} if "alu" in v else {})}
+                         for kk, v in kern.items()},
+        "solver": {"iterations": st["max_iterations"], "reliable_updates": st["reliable_updates"],
+                   "max_resid": st["max_resid"], "true_resid_base": stt["true_resid"],
+                   "true_resid_note": "FP64 |b - (H^2 + s0) x| / |b| of the smallest shift after the solve "
+                                      "(x accumulated in FP64 in a verification step)",
+                   "Q": st["Q"], "abs_Q_minus_round": st["q_round_dev"], "max_im_q": st["max_im_q"],
+                   "profiled_step_ms": stp["total_ms"], "timed_step_ms": ms,
+                   "kernel_ms_per_step": {kk: v["share_ms"] for kk, v in kern.items()},
+                   "kernel_avg_launch_ms": {kk: v["ms"] for kk, v in kern.items()}},
+    }
+    if sub is not None:
+        line["config"]["workload"] += " (profiling subset: first %d classes)" % len(sub)
+    line.update(out)
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -662,6 +713,7 @@ def main():
                     help="also time the variant with this many low modes of H_W exact (0: skip)")
     ap.add_argument("--uneven", action="store_true",
                     help="also time the uneven batch of three lattices (8^3x16, 12^3x24, 16^3x32) in one call")
+    ap.add_argument("--lanczos", type=int, default=300, help="Lanczos steps of the spectrum setup")
     ap.add_argument("--no-autotune", action="store_true",
                     help="widest RHS tile that divides the batch, without timing the candidates")
     args = ap.parse_args()

@@ -25,6 +25,11 @@
  *
  * Errors: every call returns an smpq_status; nothing throws across the ABI.  On
  * error smpq_last_error(ctx) gives a message valid until the next call on ctx.
+ * Device buffers: a buffer passed as device memory (on_device = 1, and both
+ * buffers of smpq_dslash_noalloc) must be device or managed memory of the
+ * context's GPU; anything else returns SMPQ_EINVAL before any launch.  Sizes
+ * cannot be checked through a plain pointer: each call states what it reads
+ * and writes, and a shorter buffer is the caller's error.
  * Ownership: caller buffers are only read or written during the call (device
  * buffers are used in stream order on the context's stream and the call
  * synchronises that stream before returning); the library never frees caller
@@ -88,6 +93,10 @@ typedef struct {
     int full_support;       /* q(x): keep the shifted directions on every site instead of only where
                                z = D_W y is read (the ablation of that restriction; same result,
                                14 full-lattice vectors per source) */
+    int true_residual;      /* SMPQ_FP64 / SMPQ_MIXED: also accumulate the base system's solution x
+                               (FP64, whole lattice: two more FP64 fields per source) and report
+                               max |b - (H^2 + s0) x| / |b| in smpq_stats.true_resid.  The FP32 and
+                               half paths report it from their last reliable update at no cost. */
 } smpq_options;
 
 typedef struct {
@@ -115,12 +124,15 @@ typedef struct {
     long long update_hi_launches;
     int rhs_tile;           /* RHS tile width the solves used (autotuned or fixed) */
     double q_round_dev;     /* |Q - round(Q)| of the processed sites (the charge is an integer) */
+    double true_resid;      /* largest true relative residual |b - (H^2 + s0) x| / |b| of the base
+                               (smallest) shift, recomputed in FP64 after the solve; -1 when not
+                               computed (SMPQ_FP64 / SMPQ_MIXED without the true_residual option) */
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
  * 10 iterations per check, graphs on, profiling off, switch_residual 7e-3,
- * autotuning on. */
+ * autotuning on, no true-residual accumulation. */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.
@@ -129,6 +141,12 @@ int smpq_options_default(smpq_options *opt);
 int smpq_create(smpq_ctx **out, int device, void *stream, const smpq_options *opt);
 int smpq_destroy(smpq_ctx *ctx);
 const char *smpq_last_error(const smpq_ctx *ctx);
+
+/* The context's lattice and GPU: dims (nullable) receives {nx, ny, nz, nt} of
+ * the loaded gauge field (zeros before smpq_load_gauge), *device (nullable)
+ * the CUDA device index.  Not in the paper: callers use it to size and place
+ * the buffers of the calls below. */
+int smpq_context_info(const smpq_ctx *ctx, int dims[4], int *device);
 
 /* Change the options of an existing context (kappa/bc changes take effect on
  * the next call; the gauge field and spectrum stay loaded). */
@@ -269,6 +287,17 @@ int smpq_compute_qx_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, 
  * context's precision.  Needs a gauge field and a colouring scheme (no
  * spectrum).  t_re, t_im: double[V], host or device. */
 int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, double *T, smpq_stats *stats);
+
+/* Measured arithmetic peak of GPU `device` (not part of the paper's method: the
+ * denominator of the ALU rooflines the solver's FP64-accurate kernels are
+ * reported against).  kind 0: FP32 fused multiply-adds as scalar instructions,
+ * 1: FP32 in packed two-lane instructions (sm_100 and later), 2: FP64 fused
+ * multiply-adds.  *ops_per_s = lane operations (one multiply-add each) per
+ * second, best of three launches of 8 independent chains per thread on 8
+ * blocks of 256 threads per SM.  Runs on a stream of its own; allocates and
+ * frees one small device buffer.  SMPQ_EINVAL for an unknown kind,
+ * SMPQ_ECUDA for a bad device or a CUDA error. */
+int smpq_alu_peak(int device, int kind, double *ops_per_s);
 
 #ifdef __cplusplus
 }

@@ -42,6 +42,22 @@ void release(Buf &b) {
     b.bytes = 0;
 }
 
+int check_device_ptr(smpq_ctx *ctx, const void *p, const char *what) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, SMPQ_EINVAL, std::string(what) + ": not a pointer CUDA knows");
+    }
+    if (a.type == cudaMemoryTypeManaged) return SMPQ_OK;
+    if (a.type != cudaMemoryTypeDevice)
+        return set_err(ctx, SMPQ_EINVAL, std::string(what) + ": a device buffer was expected, got host memory");
+    if (a.device != ctx->device)
+        return set_err(ctx, SMPQ_EINVAL, std::string(what) + ": device memory of GPU " + std::to_string(a.device) +
+                                             ", the context runs on GPU " + std::to_string(ctx->device));
+    return SMPQ_OK;
+}
+
 namespace {
 
 struct DeviceGuard {
@@ -163,6 +179,7 @@ size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
     size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16)
                  : half            ? (2 * 5 + 2 * 8 + 2 * 16) // p, t: 4 B + a 12th of the 4-byte norm
                                    : (prec == SMPQ_MIXED ? 3 * 16 + 3 * 8 : 3 * 16);
+    if (ctx->opt.true_residual && (prec == SMPQ_FP64 || prec == SMPQ_MIXED)) per += 2 * 16; // x64, t64
     size_t full = (size_t)ctx->V * 12 * per;
     size_t eb = (prec == SMPQ_FP32 || half) ? 8 : (prec == SMPQ_MIXED ? 16 + 8 : 16); // MIXED: FP64 and FP32 copies
     size_t sup = (size_t)n_sup * 12 * (npoles * eb + 16);
@@ -173,6 +190,11 @@ size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
 int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re, double *q_im, int on_device,
                     smpq_stats *stats, bool full, int kind = 0) {
     cudaStream_t st = ctx->stream;
+    if (on_device) {
+        int rc0;
+        if ((rc0 = check_device_ptr(ctx, q_re, "output (real parts)")) || (rc0 = check_device_ptr(ctx, q_im, "output (imaginary parts)")))
+            return rc0;
+    }
     ctx->launches = 0;
     ctx->prof_a_ms = ctx->prof_b_ms = ctx->prof_a_hi_ms = ctx->prof_b_hi_ms = 0;
     ctx->prof_a_n = ctx->prof_b_n = ctx->prof_a_hi_n = ctx->prof_b_hi_n = 0;
@@ -253,7 +275,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
 
     int maxit = 0, nrel = 0, nb = 0;
     long long totit = 0;
-    double worst = 0, solve_ms = 0;
+    double worst = 0, solve_ms = 0, true_res = -1;
     for (int j0 = 0; j0 < nrhs_total; j0 += B) {
         for (int j = 0; j < B; ++j) {
             int g = j0 + j;
@@ -301,6 +323,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         totit += out.iterations;
         nrel += out.reliable_updates;
         worst = std::max(worst, out.max_resid);
+        if (out.true_resid >= 0) true_res = std::max(true_res, out.true_resid);
         solve_ms += out.solve_ms;
         ++nb;
     }
@@ -365,6 +388,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->max_im_q = tot[1];
         stats->Q = tot[0];
         stats->q_round_dev = std::fabs(tot[0] - std::nearbyint(tot[0]));
+        stats->true_resid = true_res;
         stats->solve_ms = solve_ms;
         stats->total_ms = tms;
         stats->kernel_launches = ctx->launches;
@@ -469,6 +493,14 @@ int smpq_destroy(smpq_ctx *ctx) {
 
 const char *smpq_last_error(const smpq_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+int smpq_context_info(const smpq_ctx *ctx, int dims[4], int *device) {
+    if (!ctx) return SMPQ_EINVAL;
+    if (dims)
+        for (int mu = 0; mu < 4; ++mu) dims[mu] = ctx->have_gauge ? ctx->dims[mu] : 0;
+    if (device) *device = ctx->device;
+    return SMPQ_OK;
+}
+
 int smpq_set_options(smpq_ctx *ctx, const smpq_options *opt) {
     if (!ctx || !opt) return SMPQ_EINVAL;
     int rc = validate_options(ctx, opt);
@@ -499,6 +531,7 @@ int smpq_load_gauge(smpq_ctx *ctx, const int dims[4], const double *links, int o
     if ((rc = ensure(ctx, ctx->Uh16, (size_t)V * 24 * 4))) return rc;
     if ((rc = ensure(ctx, ctx->Ub16, (size_t)V * 24 * 4))) return rc;
     const double *src = links;
+    if (on_device && (rc = check_device_ptr(ctx, links, "load_gauge links"))) return rc;
     if (!on_device) {
         if ((rc = ensure(ctx, ctx->ws[W_MISC], (size_t)V * 36 * sizeof(double2)))) return rc;
         cudaMemcpyAsync(ctx->ws[W_MISC].p, links, (size_t)V * 36 * sizeof(double2), cudaMemcpyHostToDevice,
@@ -687,6 +720,8 @@ int smpq_dslash(smpq_ctx *ctx, const double *in, double *out, int B, int dagger,
     if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad dslash arguments");
     if (precision != SMPQ_FP64 && precision != SMPQ_FP32 && !is_half(precision))
         return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    if (on_device && ((rc = check_device_ptr(ctx, in, "dslash in")) || (rc = check_device_ptr(ctx, out, "dslash out"))))
+        return rc;
     DeviceGuard dg(ctx->device);
     StreamEntry se(ctx, ctx->user_stream);
     cudaStream_t st = ctx->stream;
@@ -766,6 +801,8 @@ int smpq_apply_dov(smpq_ctx *ctx, const double *in, double *out, int B, int on_d
     int rc = check_ctx(ctx, true, true, false);
     if (rc) return rc;
     if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad apply_dov arguments");
+    if (on_device && ((rc = check_device_ptr(ctx, in, "apply_dov in")) || (rc = check_device_ptr(ctx, out, "apply_dov out"))))
+        return rc;
     DeviceGuard dg(ctx->device);
     StreamEntry se(ctx, ctx->user_stream);
     cudaStream_t st = ctx->stream;

@@ -203,6 +203,11 @@ extern "C" int smpq_dslash_noalloc(smpq_ctx *ctx, const double *in, double *out,
     if (!ctx->have_gauge) return set_err(ctx, SMPQ_ESTATE, "no gauge field loaded");
     if (!in || !out || B < 1) return set_err(ctx, SMPQ_EINVAL, "bad dslash_noalloc arguments");
     if (precision != SMPQ_FP64 && precision != SMPQ_FP32) return set_err(ctx, SMPQ_EINVAL, "bad precision");
+    // in and out must be device memory of the context's GPU: a host pointer or
+    // another GPU's buffer would be dereferenced by the kernels
+    int rc0;
+    if ((rc0 = check_device_ptr(ctx, in, "dslash_noalloc in")) || (rc0 = check_device_ptr(ctx, out, "dslash_noalloc out")))
+        return rc0;
     const size_t n = (size_t)ctx->V * 12 * B;
     const size_t esz = precision == SMPQ_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t half = ((n * esz + 255) / 256) * 256; // input tile, then output tile

@@ -3,13 +3,18 @@
 // for a batch of B right-hand sides, accumulating y = sum_i c_i x_i (Eq. 4) on
 // the support the trace needs.
 //
-// Per iteration (one launch each, no host synchronisation):
-//   A  t = D_W p                                 + per-rhs partial |t|^2, |p|^2
-//   S1 alpha = <r,r> / (|t|^2 + s0 |p|^2); zeta_{k+1}, alpha_i for every shift
-//   B  r -= alpha (D_W^dag t + s0 p) [x_lo += alpha p]   + partial |r|^2
-//   S2 beta, beta_i, convergence |zeta_i| ||r|| <= tol ||b||, residual-replacement request
-//   Y  on the support: y += c_i alpha_i p_i ; p_i = zeta_{k+1} r + beta_i p_i
-//   P  p = r + beta p
+// One iteration is three launches, with no host synchronisation:
+//   A   t = D_W p, per-block partials |t|^2, |p|^2; the last block to finish
+//       an RHS tile sums the tile's partials and runs the first scalar step of
+//       its columns: alpha = <r,r> / (|t|^2 + s0 |p|^2), zeta_{k+1} and
+//       alpha_i of every shift
+//   B   r -= alpha (D_W^dag t + s0 p) [x_lo += alpha p], partials |r|^2; the
+//       last block of a tile runs the second scalar step: beta, beta_i,
+//       convergence |zeta_i| ||r|| <= tol ||b||, residual-replacement request
+//   YP  on the support: y += c_i alpha_i p_i, p_i = zeta_{k+1} r + beta_i p_i;
+//       on the lattice: p = r + beta p [x += alpha p for the true residual]
+// The "last block" is found with one atomic counter per RHS tile (the CUDA
+// threadfence-reduction pattern): no block ever waits for another.
 // Base vectors (p, t, r) live on the whole lattice in the iteration precision T.
 // Shifted directions p_i are pointwise in x (the matrix never touches them),
 // so they are kept only where y is read later: the 9-site star around every
@@ -19,7 +24,7 @@
 // Vorst 1996); scalars, reductions and y stay FP64 throughout.
 //
 // Reductions are deterministic: per-block partial sums in a fixed tree/sequence,
-// then a fixed-order sum over blocks in the scalar kernels.
+// then a fixed-order sum over the blocks of a tile in the tile's last block.
 #include <algorithm>
 #include <cmath>
 
@@ -105,6 +110,156 @@ __device__ __forceinline__ double2 source_at(const Source &src, int V, int s, in
     return make_double2((cl >= 0 && src.colour[s] == cl && c == src.src_comp[j]) ? 1.0 : 0.0, 0.0);
 }
 
+// ------------------------------------------------------------------ scalar steps (one thread per column)
+// First scalar step of column j: alpha and the shift recurrences zeta_{k+1},
+// alpha_i (tt = |D_W p|^2, pp = |p|^2, so <p, A p> = tt + s0 pp).
+__device__ void s1_column(int j, double tt, double pp, const Scal &sc, const ShiftParams &sp, int B) {
+    if (j == 0) {
+        sc.flags[0] = 0;
+        sc.flags[3] = 0;
+        if (sc.hist) {
+            int it = sc.iter_counter[0];
+            if (it < sc.hist_len) sc.hist[it] = 0; // filled below when rhs 0 is active
+        }
+    }
+    if (!sc.act_rhs[j]) {
+        sc.alpha[j] = 0;
+        sc.upd_rhs[j] = 0;
+        for (int i = 0; i < sp.n; ++i) { sc.upd[i * B + j] = 0; sc.alpha_s[i * B + j] = 0; }
+        return;
+    }
+    double pAp = tt + sp.s0 * pp;
+    if (!(pAp > 0) || !isfinite(pAp)) {
+        atomicOr(&sc.flags[2], 1);
+        sc.alpha[j] = 0;
+        sc.upd_rhs[j] = 0;
+        sc.act_rhs[j] = 0;
+        for (int i = 0; i < sp.n; ++i) { sc.upd[i * B + j] = 0; sc.alpha_s[i * B + j] = 0; }
+        return;
+    }
+    double a = sc.rr[j] / pAp;
+    sc.alpha[j] = a;
+    sc.upd_rhs[j] = 1;
+    if (sc.hist && j == 0) {
+        int it = sc.iter_counter[0];
+        if (it < sc.hist_len) sc.hist[it] = a;
+    }
+    double ap = sc.alpha_prev[j], bp = sc.beta_prev[j];
+    for (int i = 0; i < sp.n; ++i) {
+        int ix = i * B + j;
+        if (!sc.act[ix]) { sc.upd[ix] = 0; sc.alpha_s[ix] = 0; continue; }
+        double z = sc.zeta[ix], zp = sc.zeta_prev[ix];
+        double den = a * bp * (zp - z) + zp * ap * (1.0 + sp.sig[i] * a);
+        double zn = z * zp * ap / den;
+        sc.zeta_new[ix] = zn;
+        sc.alpha_s[ix] = a * zn / z;
+        sc.upd[ix] = 1;
+    }
+}
+
+// Second scalar step of column j (rrn = |r_{k+1}|^2): beta, beta_i, the
+// convergence of every shift, the residual-replacement request and the count
+// of columns still above the precision-switch residual.
+__device__ void s2_column(int j, double rrn, const Scal &sc, const ShiftParams &sp, int B, double tol2,
+                          double delta2, double theta2) {
+    if (j == 0) {
+        if (sc.hist) {
+            int it = sc.iter_counter[0];
+            if (it < sc.hist_len) sc.hist[sc.hist_len + it] = sc.upd_rhs[0] ? rrn / sc.rr[0] : 0.0;
+        }
+        sc.iter_counter[0] += 1;
+    }
+    if (!sc.upd_rhs[j]) return;
+    double b = rrn / sc.rr[j];
+    sc.beta[j] = b;
+    int any = 0;
+    double bb = sc.bb[j];
+    for (int i = 0; i < sp.n; ++i) {
+        int ix = i * B + j;
+        if (!sc.upd[ix]) { any |= sc.act[ix]; continue; }
+        double z = sc.zeta[ix], zn = sc.zeta_new[ix];
+        double q = zn / z;
+        sc.beta_s[ix] = b * q * q;
+        sc.zeta_prev[ix] = z;
+        sc.zeta[ix] = zn;
+        int a = zn * zn * rrn > tol2 * bb;
+        sc.act[ix] = a;
+        any |= a;
+    }
+    sc.alpha_prev[j] = sc.alpha[j];
+    sc.beta_prev[j] = b;
+    sc.rr[j] = rrn;
+    sc.iters[j] += 1;
+    sc.act_rhs[j] = any;
+    if (any) atomicAdd(&sc.flags[0], 1);
+    if (delta2 > 0 && rrn < delta2 * sc.rr_ref[j]) atomicOr(&sc.flags[1], 1);
+    if (any && rrn > theta2 * bb) atomicAdd(&sc.flags[3], 1); // still above the precision switch
+}
+
+// What the lattice kernels A and B need for the scalar step of an RHS tile.
+// count == nullptr: no scalar step (the autotuner's timing launches).
+struct Fuse {
+    int *count; // [tiles] blocks of the tile that have stored their partials; back to 0 after each launch
+    Scal sc;
+    ShiftParams sp;
+    int B;
+    double tol2, delta2, theta2; // (second step only)
+};
+
+// Called by every thread of a block after its partial sums are stored: true
+// in every thread of the block that arrives last among the G blocks of RHS
+// tile blockIdx.y.  The partial stores are fenced before the arrival count,
+// so the last block sees every partial of its tile.
+__device__ __forceinline__ bool last_block_of_tile(int *count, int G) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int ticket = atomicAdd(&count[blockIdx.y], 1);
+        last = ticket == G - 1;
+        if (last) count[blockIdx.y] = 0; // every block of the tile has arrived: reset for the next launch
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Sum over the G blocks of RHS tile `chunk` of the partials of each column, in
+// a fixed order (NT / BC lanes per column, then the lanes in order); every
+// thread of the block calls it, threads < BC receive their column's total.
+template <int BC, int NT> __device__ double tile_sum(const double *part, int chunk, int G, double *sm) {
+    constexpr int K = NT / BC;
+    const int t = threadIdx.x, jj = t % BC, k = t / BC;
+    double v = 0;
+    if (k < K)
+        for (int b = k; b < G; b += K) v += __ldcg(part + ((size_t)chunk * G + b) * BC + jj);
+    if (k < K) sm[t] = v;
+    __syncthreads();
+    double tot = 0;
+    if (t < BC)
+        for (int q = 0; q < K; ++q) tot += sm[q * BC + t];
+    __syncthreads();
+    return tot;
+}
+
+// end of lattice kernel A: the tile's last block runs the first scalar step
+template <int BC, int NT>
+__device__ __forceinline__ void fuse_step1(const Fuse &f, const double *part_t, const double *part_p, int G,
+                                           double *sm) {
+    if (!f.count || !last_block_of_tile(f.count, G)) return;
+    const double tt = tile_sum<BC, NT>(part_t, blockIdx.y, G, sm);
+    const double pp = tile_sum<BC, NT>(part_p, blockIdx.y, G, sm);
+    if (threadIdx.x < BC) s1_column(blockIdx.y * BC + threadIdx.x, tt, pp, f.sc, f.sp, f.B);
+}
+// end of lattice kernel B: the tile's last block runs the second scalar step
+template <int BC, int NT>
+__device__ __forceinline__ void fuse_step2(const Fuse &f, const double *part_r, int G, double *sm) {
+    if (!f.count || !last_block_of_tile(f.count, G)) return;
+    const double rr = tile_sum<BC, NT>(part_r, blockIdx.y, G, sm);
+    if (threadIdx.x < BC)
+        s2_column(blockIdx.y * BC + threadIdx.x, rr, f.sc, f.sp, f.B, f.tol2, f.delta2, f.theta2);
+}
+
 // ------------------------------------------------------------------ lattice kernels
 template <typename T, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
@@ -167,7 +322,7 @@ template <int BC, int NR> struct SmemCols {
 template <typename T, int BC, int NR>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_a(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ p,
-              typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G) {
+              typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
     __shared__ double sm[SmemCols<BC, NR>::N];
@@ -211,6 +366,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
         part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
         part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
     }
+    fuse_step1<BC, TM::THREADS>(f, part_t, part_p, G, sm);
 }
 
 // r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2 (NR columns per thread)
@@ -219,7 +375,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_b(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ t,
               const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ r,
               typename cplx_t<T>::type *__restrict__ xlo, const double *__restrict__ alpha, double s0, T kappa,
-              double *part_r, int G) {
+              double *part_r, int G, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
     __shared__ double sm[SmemCols<BC, NR>::N];
@@ -274,26 +430,35 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     }
     double s1 = block_total<BC, NR>(ar, sm);
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TM::THREADS>(f, part_r, G, sm);
 }
 
-// p = r + beta p
+// p = r + beta p on the lattice tiles of tile group bx; with x64, first
+// x += alpha p (FP64, the base system's solution for the true residual)
 template <typename T, int BC>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_update_p(int V, const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<T>::type *__restrict__ p,
-               const double *__restrict__ beta, const int *__restrict__ upd_rhs, int G) {
+__device__ __forceinline__ void update_p_tiles(int bx, int V, const typename cplx_t<T>::type *__restrict__ r,
+                                               typename cplx_t<T>::type *__restrict__ p, const Scal &sc,
+                                               double2 *__restrict__ x64) {
     typedef typename cplx_t<T>::type C;
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
-    if (!upd_rhs[j]) return;
+    if (!sc.upd_rhs[j]) return;
     const size_t base = (size_t)chunk * 12 * V * BC + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    const T b = (T)beta[j];
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    const T b = (T)sc.beta[j];
+    const double a = sc.alpha[j];
+    for (int tile = bx * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= V) continue;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             size_t o = base + ((size_t)s * 12 + c) * BC;
             C rv = r[o], pv = p[o];
+            if (x64) {
+                double2 xv = x64[o];
+                xv.x += a * to_d(pv.x);
+                xv.y += a * to_d(pv.y);
+                x64[o] = xv;
+            }
             pv.x = rv.x + b * pv.x;
             pv.y = rv.y + b * pv.y;
             p[o] = pv;
@@ -347,7 +512,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     k_apply_a_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
-                double *part_p, int G) {
+                double *part_p, int G, Fuse f) {
     __shared__ double sm[TileMap<BC>::THREADS];
     const int jj = threadIdx.x % BC, chunk = blockIdx.y;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
@@ -382,6 +547,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
         part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
         part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
     }
+    fuse_step1<BC, TileMap<BC>::THREADS>(f, part_t, part_p, G, sm);
 }
 
 // r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2
@@ -389,7 +555,7 @@ template <typename HT, int BC, bool REL>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     k_apply_b_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
                 float2 *__restrict__ xlo, const double *__restrict__ alpha, double s0, float kappa, double *part_r,
-                int G) {
+                int G, Fuse f) {
     __shared__ double sm[TileMap<BC>::THREADS];
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
@@ -428,19 +594,19 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     }
     const double s1 = block_sum<BC>(ar, sm);
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TileMap<BC>::THREADS>(f, part_r, G, sm);
 }
 
-// p = r + beta p, p in the half format
+// p = r + beta p on the lattice tiles of tile group bx, p in the half format
 template <typename HT, int BC>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_update_p_h(int V, const float2 *__restrict__ r, HF<HT> p, const double *__restrict__ beta,
-                 const int *__restrict__ upd_rhs, int G) {
+__device__ __forceinline__ void update_p_h_tiles(int bx, int V, const float2 *__restrict__ r, HF<HT> p,
+                                                 const Scal &sc) {
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
-    if (!upd_rhs[j]) return;
+    if (!sc.upd_rhs[j]) return;
     const size_t base = (size_t)chunk * 12 * V * BC + jj, nbase = (size_t)chunk * V * BC + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    const float b = (float)beta[j];
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    const float b = (float)sc.beta[j];
+    for (int tile = bx * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= V) continue;
         typename HT::h2 *ps = p.v + base + (size_t)s * 12 * BC;
@@ -471,7 +637,7 @@ template <int BC> __device__ __forceinline__ void st_rx2(float2 *p, float2 re, f
 template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     k_apply_a_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
-                 double *part_p, int G) {
+                 double *part_p, int G, Fuse f) {
     typedef TileMap<BC, 2> TM;
     __shared__ double sm[SmemCols<BC, 2>::N];
     const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y;
@@ -508,13 +674,14 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
         part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
         part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
     }
+    fuse_step1<BC, TM::THREADS>(f, part_t, part_p, G, sm);
 }
 
 template <typename HT, int BC, bool REL>
 __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     k_apply_b_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
                  float2 *__restrict__ xlo, const double *__restrict__ alpha, double s0, float kappa, double *part_r,
-                 int G) {
+                 int G, Fuse f) {
     typedef TileMap<BC, 2> TM;
     __shared__ double sm[SmemCols<BC, 2>::N];
     const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y, j = chunk * BC + jj;
@@ -557,6 +724,7 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     }
     const double s1 = block_total<BC, 2>(ar, sm);
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TM::THREADS>(f, part_r, G, sm);
 }
 
 // Shifted updates on the support: y += c_i alpha_i p_i ; p_i = zeta_new_i r + beta_i p_i.
@@ -564,10 +732,11 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
 // (identity when supsite == nullptr).  r is read in the iteration precision T,
 // ps ([shift][chunk][n_sup][12][BC]) is kept in TS, y ([chunk][n_sup][12][BC]) in FP64.
 template <typename T, typename TS, int BC>
-__global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_shift(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
-            const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<TS>::type *__restrict__ ps,
-            double2 *__restrict__ y, Scal sc, ShiftParams sp, int G, int init) {
+__device__ __forceinline__ void shift_tiles(int bx, int V, int n_sup, int nshift, int B,
+                                            const int *__restrict__ supsite, const int *__restrict__ rhs_class,
+                                            const typename cplx_t<T>::type *__restrict__ r,
+                                            typename cplx_t<TS>::type *__restrict__ ps, double2 *__restrict__ y,
+                                            const Scal &sc, const ShiftParams &sp, int init) {
     typedef typename cplx_t<T>::type CR;
     typedef typename cplx_t<TS>::type C;
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
@@ -577,7 +746,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     const size_t sbase = (size_t)chunk * 12 * n_sup * BC + jj;
     const size_t sstride = (size_t)B * 12 * n_sup; // one shift
     const int ntiles = (n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = bx * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         int k = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (k >= n_sup) continue;
         int site = supsite ? supsite[(size_t)cls * n_sup + k] : k;
@@ -618,6 +787,41 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 #pragma unroll
         for (int c = 0; c < 12; ++c) y[sbase + ((size_t)k * 12 + c) * BC] = yv[c];
     }
+}
+
+// shifted directions at the start of a solve: p_i = b (= r), y = 0
+template <typename T, typename TS, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+    k_shift_init(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite,
+                 const int *__restrict__ rhs_class, const typename cplx_t<T>::type *__restrict__ r,
+                 typename cplx_t<TS>::type *__restrict__ ps, double2 *__restrict__ y, Scal sc, ShiftParams sp) {
+    shift_tiles<T, TS, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 1);
+}
+
+// Launch YP of an iteration: blocks x < Gs update y and the shifted directions
+// on the support, the others p (and x64) on the lattice.
+template <typename T, typename TS, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+    k_yp(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
+         const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<TS>::type *__restrict__ ps,
+         double2 *__restrict__ y, Scal sc, ShiftParams sp, int Gs, typename cplx_t<T>::type *__restrict__ p,
+         double2 *__restrict__ x64) {
+    if ((int)blockIdx.x < Gs)
+        shift_tiles<T, TS, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 0);
+    else
+        update_p_tiles<T, BC>(blockIdx.x - Gs, V, r, p, sc, x64);
+}
+
+// Launch YP of a half-storage iteration (p in the half format)
+template <typename HT, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS)
+    k_yp_h(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
+           const float2 *__restrict__ r, float2 *__restrict__ ps, double2 *__restrict__ y, Scal sc, ShiftParams sp,
+           int Gs, HF<HT> p) {
+    if ((int)blockIdx.x < Gs)
+        shift_tiles<float, float, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 0);
+    else
+        update_p_h_tiles<HT, BC>(blockIdx.x - Gs, V, r, p, sc);
 }
 
 // x_hi += x_lo ; x_lo = 0
@@ -728,94 +932,11 @@ __global__ void __launch_bounds__(SCAL_THREADS)
     if (any) atomicAdd(&sc.flags[0], 1);
 }
 
-__global__ void __launch_bounds__(SCAL_THREADS)
-    s1_kernel(int B, int BC, int G, const double *part_t, const double *part_p, Scal sc, ShiftParams sp) {
+// out[j] = sum over the blocks of the partials of rhs j (one block per rhs)
+__global__ void __launch_bounds__(SCAL_THREADS) s_sum_rhs(int BC, int G, const double *part, double *out) {
     __shared__ double sm[SCAL_THREADS];
-    const int j = blockIdx.x;
-    double tt = part_sum(part_t, j, BC, G, sm), pp = part_sum(part_p, j, BC, G, sm);
-    if (threadIdx.x) return;
-    if (j == 0) {
-        sc.flags[0] = 0;
-        sc.flags[3] = 0;
-        if (sc.hist) {
-            int it = sc.iter_counter[0];
-            if (it < sc.hist_len) sc.hist[it] = 0; // filled below when rhs 0 is active
-        }
-    }
-    if (!sc.act_rhs[j]) {
-        sc.alpha[j] = 0;
-        sc.upd_rhs[j] = 0;
-        for (int i = 0; i < sp.n; ++i) { sc.upd[i * B + j] = 0; sc.alpha_s[i * B + j] = 0; }
-        return;
-    }
-    double pAp = tt + sp.s0 * pp;
-    if (!(pAp > 0) || !isfinite(pAp)) {
-        atomicOr(&sc.flags[2], 1);
-        sc.alpha[j] = 0;
-        sc.upd_rhs[j] = 0;
-        sc.act_rhs[j] = 0;
-        for (int i = 0; i < sp.n; ++i) { sc.upd[i * B + j] = 0; sc.alpha_s[i * B + j] = 0; }
-        return;
-    }
-    double a = sc.rr[j] / pAp;
-    sc.alpha[j] = a;
-    sc.upd_rhs[j] = 1;
-    if (sc.hist && j == 0) {
-        int it = sc.iter_counter[0];
-        if (it < sc.hist_len) sc.hist[it] = a;
-    }
-    double ap = sc.alpha_prev[j], bp = sc.beta_prev[j];
-    for (int i = 0; i < sp.n; ++i) {
-        int ix = i * B + j;
-        if (!sc.act[ix]) { sc.upd[ix] = 0; sc.alpha_s[ix] = 0; continue; }
-        double z = sc.zeta[ix], zp = sc.zeta_prev[ix];
-        double den = a * bp * (zp - z) + zp * ap * (1.0 + sp.sig[i] * a);
-        double zn = z * zp * ap / den;
-        sc.zeta_new[ix] = zn;
-        sc.alpha_s[ix] = a * zn / z;
-        sc.upd[ix] = 1;
-    }
-}
-
-__global__ void __launch_bounds__(SCAL_THREADS)
-    s2_kernel(int B, int BC, int G, const double *part_r, Scal sc, ShiftParams sp, double tol2, double delta2,
-              double theta2) {
-    __shared__ double sm[SCAL_THREADS];
-    const int j = blockIdx.x;
-    double rrn = part_sum(part_r, j, BC, G, sm);
-    if (threadIdx.x) return;
-    if (j == 0) {
-        if (sc.hist) {
-            int it = sc.iter_counter[0];
-            if (it < sc.hist_len) sc.hist[sc.hist_len + it] = sc.upd_rhs[0] ? rrn / sc.rr[0] : 0.0;
-        }
-        sc.iter_counter[0] += 1;
-    }
-    if (!sc.upd_rhs[j]) return;
-    double b = rrn / sc.rr[j];
-    sc.beta[j] = b;
-    int any = 0;
-    double bb = sc.bb[j];
-    for (int i = 0; i < sp.n; ++i) {
-        int ix = i * B + j;
-        if (!sc.upd[ix]) { any |= sc.act[ix]; continue; }
-        double z = sc.zeta[ix], zn = sc.zeta_new[ix];
-        double q = zn / z;
-        sc.beta_s[ix] = b * q * q;
-        sc.zeta_prev[ix] = z;
-        sc.zeta[ix] = zn;
-        int a = zn * zn * rrn > tol2 * bb;
-        sc.act[ix] = a;
-        any |= a;
-    }
-    sc.alpha_prev[j] = sc.alpha[j];
-    sc.beta_prev[j] = b;
-    sc.rr[j] = rrn;
-    sc.iters[j] += 1;
-    sc.act_rhs[j] = any;
-    if (any) atomicAdd(&sc.flags[0], 1);
-    if (delta2 > 0 && rrn < delta2 * sc.rr_ref[j]) atomicOr(&sc.flags[1], 1);
-    if (any && rrn > theta2 * bb) atomicAdd(&sc.flags[3], 1); // still above the precision switch
+    const double v = part_sum(part, blockIdx.x, BC, G, sm);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
 // after a residual replacement: rr = |r_hi|^2, the base shift re-activates if
@@ -894,6 +1015,9 @@ template <int BC> struct Solve {
     double tol2;
     int base_shift;
     int *hflags = nullptr;
+    int *count = nullptr;     // [nchunk] arrival counters of the fused scalar steps
+    double2 *x64 = nullptr;   // base-system solution in FP64 (true residual), nullable
+    double *true_rr = nullptr; // [B] |b - (A + s0) x64|^2
     int iters = 0, nrel = 0;
     bool prof;
     int chk;
@@ -917,8 +1041,8 @@ template <int BC> struct Solve {
         if (ws.size() < W_COUNT) ws.resize(W_COUNT);
         int rc;
         if ((rc = ensure(ctx, ws[W_PART], 3 * npart * sizeof(double)))) return rc;
-        const size_t nscal = (size_t)B * 7 + (size_t)sp.n * B * 5;
-        const size_t nint = (size_t)B * 3 + (size_t)sp.n * B * 2 + 8;
+        const size_t nscal = (size_t)B * 8 + (size_t)sp.n * B * 5;
+        const size_t nint = (size_t)B * 3 + (size_t)sp.n * B * 2 + 8 + (size_t)nchunk;
         if ((rc = ensure(ctx, ws[W_SCAL], nscal * sizeof(double) + nint * sizeof(int)))) return rc;
         part0 = (double *)ws[W_PART].p;
         part1 = part0 + npart;
@@ -928,10 +1052,12 @@ template <int BC> struct Solve {
         sc.alpha_prev = d; d += B; sc.beta_prev = d; d += B; sc.rr_ref = d; d += B;
         sc.zeta = d; d += sp.n * B; sc.zeta_prev = d; d += sp.n * B; sc.zeta_new = d; d += sp.n * B;
         sc.alpha_s = d; d += sp.n * B; sc.beta_s = d; d += sp.n * B;
+        true_rr = d; d += B;
         int *ip = (int *)d;
         sc.act_rhs = ip; ip += B; sc.upd_rhs = ip; ip += B; sc.iters = ip; ip += B;
         sc.act = ip; ip += sp.n * B; sc.upd = ip; ip += sp.n * B;
-        sc.flags = ip; ip += 4; sc.iter_counter = ip;
+        sc.flags = ip; ip += 4; sc.iter_counter = ip; ip += 4;
+        count = ip;
         sc.hist = hist;
         sc.hist_len = hist_len;
         src.colour = spec.d_colour;
@@ -955,7 +1081,7 @@ template <int BC> struct Solve {
             cudaGetLastError();
             return set_err(ctx, SMPQ_ENOMEM, "pinned host flags");
         }
-        cudaMemsetAsync(sc.flags, 0, 5 * sizeof(int), st);
+        cudaMemsetAsync(sc.flags, 0, (8 + (size_t)nchunk) * sizeof(int), st); // flags, counter, arrivals
         return SMPQ_OK;
     }
 
@@ -1014,8 +1140,12 @@ template <int BC> struct Solve {
         const T kappa = (T)ctx->opt.kappa;
         const C *U = (const C *)Links<T>::get(ctx);
         const bool shifts = spec.n_sup > 0;
-        const int per_iter = 5 + (shifts ? 1 : 0);
+        const int per_iter = 3;
         const bool hi = sizeof(T) != sizeof(float); // FP64 or float-float iterations
+        if constexpr (half) {
+            if (!rel || !xlo || !xhi || !t64)
+                return set_err(ctx, SMPQ_EINVAL, "internal: half-storage iterations need FP64 reliable updates");
+        }
         if (init) {
             if constexpr (half)
                 k_init_h<HT, BC><<<grid, TH, 0, st>>>(g, src, (float2 *)r, hfield<HT>(p), (float2 *)xlo, xhi, part0, G);
@@ -1023,10 +1153,19 @@ template <int BC> struct Solve {
                 k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
             s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, sqrt(tol2));
             if (shifts)
-                k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r,
-                                                        ps, y, sc, sp, Gs, 1);
+                k_shift_init<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite,
+                                                             spec.d_rhs_class, r, ps, y, sc, sp);
             ctx->launches += 2 + (shifts ? 1 : 0);
         }
+        // the scalar steps ride on the last block of each RHS tile of launches A and B
+        const Fuse f1{count, sc, sp, B, 0.0, 0.0, 0.0};
+        const Fuse f2{count, sc, sp, B, tol2, delta2, theta2};
+        // launch YP: Gy support blocks, then the lattice blocks of the p update
+        const int Gy = shifts ? Gs : 0;
+        const dim3 gridyp(Gy + G, nchunk);
+        // x += alpha p in FP64 for the true residual (the FP32 and half paths
+        // keep x_hi for their reliable updates instead)
+        double2 *xacc = rel ? nullptr : x64;
         // two columns per thread for even tiles (SMPQ_HALF_SOLVE_NR=1: one)
 #ifndef SMPQ_HALF_SOLVE_NR
 #define SMPQ_HALF_SOLVE_NR 2
@@ -1043,25 +1182,21 @@ template <int BC> struct Solve {
                 constexpr int THH = TMH::THREADS;
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
                 if constexpr (h2cols)
-                    k_apply_a_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH);
+                    k_apply_a_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH, f1);
                 else
-                    k_apply_a_h<HT, BC><<<grid, TH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, G);
+                    k_apply_a_h<HT, BC><<<grid, TH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, G, f1);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-                s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GH, part0, part1, sc, sp);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
                 // (half-storage solves always run with reliable updates)
                 if constexpr (h2cols)
                     k_apply_b_h2<HT, BC, true><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo,
-                                                                      sc.alpha, sp.s0, (float)kappa, part2, GH);
+                                                                      sc.alpha, sp.s0, (float)kappa, part2, GH, f2);
                 else
                     k_apply_b_h<HT, BC, true><<<grid, TH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo, sc.alpha,
-                                                                   sp.s0, (float)kappa, part2, G);
+                                                                   sp.s0, (float)kappa, part2, G, f2);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-                s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GH, part2, sc, sp, tol2, delta2, theta2);
-                if (shifts)
-                    k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class,
-                                                            r, ps, y, sc, sp, Gs, 0);
-                k_update_p_h<HT, BC><<<grid, TH, 0, st>>>(V, (const float2 *)r, hp, sc.beta, sc.upd_rhs, G);
+                k_yp_h<HT, BC><<<gridyp, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class,
+                                                       (const float2 *)r, (float2 *)ps, y, sc, sp, Gy, hp);
             }
         };
         auto iteration = [&](int k) {
@@ -1070,22 +1205,18 @@ template <int BC> struct Solve {
                 return;
             }
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-            k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(g, U, p, t, kappa, part0, part1, GN);
+            k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(g, U, p, t, kappa, part0, part1, GN, f1);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-            s1_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GN, part0, part1, sc, sp);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
             if (rel)
                 k_apply_b<T, BC, NR, true><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
-                                                                   GN);
+                                                                   GN, f2);
             else
                 k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
-                                                                    GN);
+                                                                    GN, f2);
             if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-            s2_kernel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, GN, part2, sc, sp, tol2, delta2, theta2);
-            if (shifts)
-                k_shift<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r,
-                                                        ps, y, sc, sp, Gs, 0);
-            k_update_p<T, BC><<<grid, TH, 0, st>>>(V, r, p, sc.beta, sc.upd_rhs, G);
+            k_yp<T, TS, BC><<<gridyp, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps, y,
+                                                   sc, sp, Gy, p, xacc);
         };
         auto reliable = [&]() {
             ctx->launches += 4;
@@ -1157,10 +1288,29 @@ template <int BC> struct Solve {
         return status;
     }
 
-    int finish(SolveOut *out, int fixed) {
+    bool relpath = false; // FP32 / half paths: the last reliable update left |b - (A + s0) x_hi|^2 in sc.rr
+
+    // True residual of the base system from the FP64 solution x64 (FP64 and
+    // mixed paths): t64 = D_W x64, |b - (D_W^dag t64 + s0 x64)|^2 per rhs into
+    // rr_out (the FP32 copy of that residual goes to the scratch field rs).
+    template <typename T>
+    int true_residual(double2 *t64, typename cplx_t<T>::type *rs, double *rr_out) {
+        const dim3 grid(G, nchunk);
+        const int TH = TileMap<BC>::THREADS;
+        launch_dslash<double>(ctx->geom, ctx->U64.p, x64, t64, B, BC, 0, ctx->opt.kappa, st);
+        k_rel_resid<T, BC><<<grid, TH, 0, st>>>(ctx->geom, (const double2 *)ctx->U64.p, t64, x64, src, rs, sp.s0,
+                                                ctx->opt.kappa, part2, G);
+        s_sum_rhs<<<B, SCAL_THREADS, 0, st>>>(BC, G, part2, rr_out);
+        ctx->launches += 3;
+        return cuda_check(ctx, cudaGetLastError(), "true residual");
+    }
+
+    int finish(SolveOut *out, int fixed, const double *d_true_rr = nullptr) {
         cudaEventRecord(ctx->ev2, st);
         std::vector<double> hz((size_t)sp.n * B), hrr(B), hbb(B);
         std::vector<int> hit(B);
+        std::vector<double> htr(d_true_rr ? B : 0);
+        if (d_true_rr) cudaMemcpyAsync(htr.data(), d_true_rr, B * sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(hz.data(), sc.zeta, hz.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(hrr.data(), sc.rr, B * sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(hbb.data(), sc.bb, B * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1181,6 +1331,13 @@ template <int BC> struct Solve {
         out->iterations = fixed > 0 ? fixed : maxit;
         out->reliable_updates = nrel;
         out->max_resid = worst;
+        out->true_resid = -1;
+        if (relpath || d_true_rr) {
+            double tr = 0;
+            for (int j = 0; j < B; ++j)
+                if (hbb[j] > 0) tr = std::max(tr, std::sqrt((d_true_rr ? htr[j] : hrr[j]) / hbb[j]));
+            out->true_resid = tr;
+        }
         out->solve_ms = ms;
         return cuda_check(ctx, cudaGetLastError(), "multishift launch");
     }
@@ -1203,11 +1360,15 @@ template <int BC> struct Solve {
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            if ((rc = S.alloc_x64())) return rc;
             rc = S.template phase<double, double>((double2 *)ws[W_P].p, (double2 *)ws[W_T].p, (double2 *)ws[W_R].p,
                                                   nullptr, nullptr, nullptr,
                                                   shifts ? (double2 *)ws[W_PS].p : nullptr, true, false, 0.0, fixed,
                                                   max_iter);
             if (rc) return rc;
+            if (S.x64 && (rc = S.template true_residual<double>((double2 *)ws[W_T64].p, (double2 *)ws[W_R].p,
+                                                                 S.true_rr)))
+                return rc;
         } else if (spec.prec == SMPQ_MIXED) {
             // phase 1: float-float (FP64-accurate) vectors and D_W down to the switch residual
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(df64c)))) return rc;
@@ -1218,6 +1379,7 @@ template <int BC> struct Solve {
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            if ((rc = S.alloc_x64())) return rc;
             double2 *ps = shifts ? (double2 *)ws[W_PS].p : nullptr;
             df64c *p = (df64c *)ws[W_P].p, *t = (df64c *)ws[W_T].p, *r = (df64c *)ws[W_R].p;
             const double theta = ctx->opt.switch_residual;
@@ -1249,6 +1411,7 @@ template <int BC> struct Solve {
                                                      max_iter);
                 if (rc) return rc;
             }
+            if (S.x64 && (rc = S.template true_residual<float>((double2 *)ws[W_T64].p, r32, S.true_rr))) return rc;
         } else if (spec.prec == SMPQ_FP16N || spec.prec == SMPQ_BF16N) {
             // p and t in the half format, the rest as in the FP32 path
             const size_t hb = (half_field_bytes(S.V, S.B) + 255) / 256 * 256;
@@ -1266,6 +1429,7 @@ template <int BC> struct Solve {
             float2 *pp = (float2 *)ws[W_P].p, *tt = (float2 *)ws[W_T].p, *rr = (float2 *)ws[W_R].p;
             float2 *xl = (float2 *)ws[W_XLO].p, *ps = shifts ? (float2 *)ws[W_PS].p : nullptr;
             double2 *xh = (double2 *)ws[W_XHI].p, *t64 = (double2 *)ws[W_T64].p;
+            S.relpath = true;
             if (spec.prec == SMPQ_BF16N)
                 rc = S.template phase<float, float, B16>(pp, tt, rr, xl, xh, t64, ps, true, true, 0.0, fixed, max_iter);
             else
@@ -1283,13 +1447,27 @@ template <int BC> struct Solve {
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
+            S.relpath = true;
             rc = S.template phase<float, float>((float2 *)ws[W_P].p, (float2 *)ws[W_T].p, (float2 *)ws[W_R].p,
                                                 (float2 *)ws[W_XLO].p, (double2 *)ws[W_XHI].p,
                                                 (double2 *)ws[W_T64].p, shifts ? (float2 *)ws[W_PS].p : nullptr,
                                                 true, true, 0.0, fixed, max_iter);
             if (rc) return rc;
         }
-        return S.finish(out, fixed);
+        return S.finish(out, fixed, S.x64 ? S.true_rr : nullptr);
+    }
+
+    // FP64 and mixed paths with the true_residual option: x64 (and t64 for
+    // the final check) on the whole lattice, x64 starting at 0
+    int alloc_x64() {
+        if (!ctx->opt.true_residual || spec.n_sup == 0) return SMPQ_OK;
+        std::vector<Buf> &ws = ctx->ws;
+        int rc;
+        if ((rc = ensure(ctx, ws[W_XHI], nfield * sizeof(double2)))) return rc;
+        if ((rc = ensure(ctx, ws[W_T64], nfield * sizeof(double2)))) return rc;
+        x64 = (double2 *)ws[W_XHI].p;
+        cudaMemsetAsync(x64, 0, nfield * sizeof(double2), st);
+        return SMPQ_OK;
     }
 };
 
@@ -1404,11 +1582,13 @@ template <typename T, int BC> float time_pair(smpq_ctx *ctx, int B, int reps, vo
     cudaStream_t st = ctx->stream;
     const dim3 gridn(GN, nchunk);
     const int THN = TileMap<BC, NR>::THREADS;
+    Fuse none{};
+    none.count = nullptr; // timing only: no scalar step
     auto once = [&]() {
         k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(ctx->geom, U, p, t, kappa, part, part + (size_t)nchunk * GN * BC,
-                                                     GN);
+                                                     GN, none);
         k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(ctx->geom, U, t, p, r, nullptr, alpha, 0.0, kappa, part,
-                                                            GN);
+                                                            GN, none);
     };
     once(); // warm-up
     cudaEventRecord(ctx->ev1, st);

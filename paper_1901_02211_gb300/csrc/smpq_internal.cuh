@@ -86,6 +86,9 @@ int set_err(smpq_ctx *ctx, int code, const std::string &msg);
 int cuda_check(smpq_ctx *ctx, cudaError_t e, const char *what);
 int ensure(smpq_ctx *ctx, Buf &b, size_t bytes);
 void release(Buf &b);
+// SMPQ_EINVAL unless p is device (or managed) memory of the context's GPU;
+// `what` names the argument in the message
+int check_device_ptr(smpq_ctx *ctx, const void *p, const char *what);
 
 // zolotarev.cpp
 int zolotarev_coeffs(int n, double a, double b, double *c0, double *c, double *q, double *delta);
@@ -139,6 +142,7 @@ struct SolveOut {
     int iterations = 0;
     int reliable_updates = 0;
     double max_resid = 0;
+    double true_resid = -1; // max_j |b - (A + s0) x|/|b| of the base system (-1: not computed)
     float solve_ms = 0;
 };
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out);

@@ -15,7 +15,6 @@ Usage:  python -m paper_1901_02211_gb300.experiments rmin [config]
 """
 from __future__ import annotations
 
-import json
 import math
 import os
 import sys
@@ -121,13 +120,16 @@ def locality(dims, U, lmin2, lmax2, site=0, device=0):
     return out
 
 
-def _load(name):
+def _load(name, device=0, lanczos_steps=300):
+    """The synthetic configuration and its Zolotarev interval, measured on the
+    GPU (smpq_measure_spectrum: Lanczos on H_W^2, widened to 0.98 / 1.02)."""
     sys.path.insert(0, ROOT)
     from synth import make_config
     cfg = make_config(name)
-    with open(os.path.join(ROOT, "tests", "golden", "spectra.json")) as f:
-        sp = json.load(f)[name]
-    return cfg, 0.98 * sp["lmin2"], 1.02 * sp["lmax2"]
+    with Session(device=device) as s:
+        s.load_gauge(cfg["dims"], cfg["U"])
+        lo, hi = s.measure_spectrum(lanczos_steps)
+    return cfg, 0.98 * lo, 1.02 * hi
 
 
 def main(argv):

@@ -55,6 +55,7 @@ class smpq_options(ctypes.Structure):
         ("switch_residual", ctypes.c_double),
         ("autotune", ctypes.c_int),
         ("full_support", ctypes.c_int),
+        ("true_residual", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,7 @@ class smpq_stats(ctypes.Structure):
         ("update_hi_launches", ctypes.c_longlong),
         ("rhs_tile", ctypes.c_int),
         ("q_round_dev", ctypes.c_double),
+        ("true_resid", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -93,7 +95,8 @@ EXPORTS = [
     "smpq_load_gauge", "smpq_set_spectrum", "smpq_measure_spectrum", "smpq_zolotarev", "smpq_get_zolotarev",
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
     "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv", "smpq_compute_qx_batch",
-    "smpq_low_modes", "smpq_get_low_modes", "smpq_clear_low_modes", "smpq_time_dslash",
+    "smpq_low_modes", "smpq_get_low_modes", "smpq_clear_low_modes", "smpq_time_dslash", "smpq_context_info",
+    "smpq_alu_peak",
 ]
 
 _lib = None
@@ -138,6 +141,8 @@ def load(build_if_missing=True):
         "smpq_low_modes": [P, I, I, D, I, P, P, PI],
         "smpq_get_low_modes": [P, P, P, PI],
         "smpq_clear_low_modes": [P],
+        "smpq_context_info": [P, PI, PI],
+        "smpq_alu_peak": [I, I, PD],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -166,6 +171,56 @@ def _ptr(a):
             raise ValueError("tensor must be contiguous")
         return a.data_ptr(), 1 if a.is_cuda else 0
     raise TypeError("expected a numpy array or a torch tensor")
+
+
+def smpq_context_info(ctx):
+    """(dims, device) of a context; dims are zeros before a gauge field is loaded."""
+    d = (ctypes.c_int * 4)()
+    dev = ctypes.c_int()
+    _check(load().smpq_context_info(ctx, d, ctypes.byref(dev)), ctx)
+    return tuple(d), dev.value
+
+
+ALU_FP32, ALU_FP32X2, ALU_FP64 = 0, 1, 2
+
+
+def smpq_alu_peak(device=0, kind=ALU_FP32X2):
+    """Measured lane operations (multiply-adds) per second of the GPU: kind
+    ALU_FP32 (scalar FFMA), ALU_FP32X2 (packed two-lane FFMA2) or ALU_FP64."""
+    v = ctypes.c_double()
+    _check(load().smpq_alu_peak(device, kind, ctypes.byref(v)))
+    return v.value
+
+
+def _check_buf(ctx, a, count, kind, what):
+    """Refuse, before any launch, a buffer the kernels could overrun or could
+    not reach: it must hold `count` elements of `kind` ("complex128" or
+    "float64") and, as device memory, sit on the context's GPU."""
+    dims, dev = smpq_context_info(ctx)
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(kind):
+            raise ValueError("%s: dtype %s, expected %s" % (what, a.dtype, kind))
+        n = a.size
+    elif hasattr(a, "data_ptr"):
+        import torch
+        want = torch.complex128 if kind == "complex128" else torch.float64
+        if a.dtype != want:
+            raise ValueError("%s: dtype %s, expected %s" % (what, a.dtype, want))
+        if a.is_cuda and a.device.index != dev:
+            raise ValueError("%s: on cuda:%d, the context runs on cuda:%d" % (what, a.device.index, dev))
+        n = a.numel()
+    else:
+        raise TypeError("%s: expected a numpy array or a torch tensor" % what)
+    if n < count:
+        raise ValueError("%s: %d elements, the call reads or writes %d" % (what, n, count))
+
+
+def _volume(ctx):
+    dims, _ = smpq_context_info(ctx)
+    V = int(np.prod(dims))
+    if V == 0:
+        raise SmpqError(SMPQ_ESTATE, "no gauge field loaded")
+    return V
 
 
 # ----------------------------------------------------------------------------- thin wrappers (same names)
@@ -198,6 +253,7 @@ def smpq_set_options(ctx, options):
 
 def smpq_load_gauge(ctx, dims, links):
     d = (ctypes.c_int * 4)(*dims)
+    _check_buf(ctx, links, int(np.prod(dims)) * 36, "complex128", "links")
     p, dev = _ptr(links)
     _check(load().smpq_load_gauge(ctx, d, p, dev), ctx)
 
@@ -268,7 +324,20 @@ def smpq_colour_sites(dims, r, mode):
     return col, n.value
 
 
+def _check_fields(ctx, inp, out, B):
+    n = _volume(ctx) * 12 * B
+    _check_buf(ctx, inp, n, "complex128", "in")
+    _check_buf(ctx, out, n, "complex128", "out")
+
+
+def _check_sites(ctx, a, b, names):
+    V = _volume(ctx)
+    _check_buf(ctx, a, V, "float64", names[0])
+    _check_buf(ctx, b, V, "float64", names[1])
+
+
 def smpq_dslash(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
+    _check_fields(ctx, inp, out, B)
     pi, di = _ptr(inp)
     po, do = _ptr(out)
     if di != do:
@@ -288,6 +357,7 @@ def smpq_time_dslash(ctx, B, dagger=False, precision=SMPQ_FP32, reps=10):
 def smpq_dslash_noalloc(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
     """Allocation-free D_W for callers that cannot allocate device memory:
     `inp` and `out` must be device buffers (torch CUDA tensors)."""
+    _check_fields(ctx, inp, out, B)
     pi, di = _ptr(inp)
     po, do = _ptr(out)
     if not (di and do):
@@ -296,6 +366,7 @@ def smpq_dslash_noalloc(ctx, inp, out, B, dagger=False, precision=SMPQ_FP64):
 
 
 def smpq_apply_dov(ctx, inp, out, B):
+    _check_fields(ctx, inp, out, B)
     pi, di = _ptr(inp)
     po, do = _ptr(out)
     if di != do:
@@ -304,6 +375,7 @@ def smpq_apply_dov(ctx, inp, out, B):
 
 
 def smpq_compute_qx(ctx, q_re, q_im):
+    _check_sites(ctx, q_re, q_im, ("q_re", "q_im"))
     pr, dr = _ptr(q_re)
     pm, dm = _ptr(q_im)
     if dr != dm:
@@ -316,6 +388,7 @@ def smpq_compute_qx(ctx, q_re, q_im):
 
 def smpq_compute_qx_classes(ctx, classes, q_re, q_im):
     cl = np.ascontiguousarray(classes, dtype=np.int32)
+    _check_sites(ctx, q_re, q_im, ("q_re", "q_im"))
     pr, dr = _ptr(q_re)
     pm, dm = _ptr(q_im)
     st = smpq_stats()
@@ -325,6 +398,7 @@ def smpq_compute_qx_classes(ctx, classes, q_re, q_im):
 
 
 def smpq_trace_dwinv(ctx, t_re, t_im):
+    _check_sites(ctx, t_re, t_im, ("t_re", "t_im"))
     pr, dr = _ptr(t_re)
     pm, dm = _ptr(t_im)
     if dr != dm:
@@ -338,6 +412,8 @@ def smpq_trace_dwinv(ctx, t_re, t_im):
 def smpq_compute_qx_batch(ctxs, q_re, q_im):
     """Uneven batch over several contexts; q_re/q_im: lists of per-lattice buffers."""
     n = len(ctxs)
+    for c, a, b in zip(ctxs, q_re, q_im):
+        _check_sites(c, a, b, ("q_re", "q_im"))
     pr = [_ptr(a) for a in q_re]
     pm = [_ptr(a) for a in q_im]
     dev = {d for _, d in pr + pm}

@@ -84,3 +84,44 @@ def test_binding_constants_match_the_header():
     assert {"SMPQ_FP64", "SMPQ_FP32", "SMPQ_MIXED", "SMPQ_FP16N", "SMPQ_BF16N", "SMPQ_OK", "SMPQ_EINVAL"} <= set(enums)
     for name, value in enums.items():
         assert getattr(S, name) == value, name
+
+
+def _struct_members(name):
+    """Member names of `typedef struct { ... } name;` in include/smpq.h, in order."""
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", txt).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            out.extend(re.sub(r"\[.*?\]", "", v).split()[-1] for v in decl.split(","))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyclass", [("smpq_options", S.smpq_options), ("smpq_stats", S.smpq_stats)])
+def test_binding_structs_follow_the_header(cname, pyclass):
+    """The ctypes mirrors of the option and statistics structs have the header's
+    members in the header's order (a drift would shift every later field)."""
+    assert [f for f, _ in pyclass._fields_] == _struct_members(cname)
+
+
+def test_buffer_checks_refuse_before_any_launch(monkeypatch):
+    """The binding refuses a buffer of the wrong type or size before calling C
+    (a short or complex64 buffer would be overrun by the kernels).  The
+    context's lattice comes from a stand-in for smpq_context_info (no GPU here)."""
+    monkeypatch.setattr(S, "smpq_context_info", lambda ctx: ((4, 4, 4, 4), 0))
+    V, B = 256, 3
+    good = np.zeros((V, 4, 3, B), dtype=np.complex128)
+    S._check_fields(None, good, good, B)  # accepted
+    with pytest.raises(ValueError, match="dtype"):
+        S._check_fields(None, good.astype(np.complex64), good, B)
+    with pytest.raises(ValueError, match="elements"):
+        S._check_fields(None, good, good[:, :, :, :2].copy(), B)
+    S._check_sites(None, np.zeros(V), np.zeros(V), ("q_re", "q_im"))
+    with pytest.raises(ValueError, match="elements"):
+        S._check_sites(None, np.zeros(V - 1), np.zeros(V), ("q_re", "q_im"))
+    with pytest.raises(ValueError, match="dtype"):
+        S._check_sites(None, np.zeros(V, dtype=np.float32), np.zeros(V), ("q_re", "q_im"))
+    monkeypatch.setattr(S, "smpq_context_info", lambda ctx: ((0, 0, 0, 0), 0))
+    with pytest.raises(S.SmpqError):
+        S._volume(None)

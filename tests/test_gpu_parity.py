@@ -208,8 +208,7 @@ def test_zolotarev_of_context_matches_oracle(S, flux4, zolo4):
 @pytest.mark.parametrize("rhs_block", [1, 0])
 @pytest.mark.parametrize("r,mode", [(2, 0), (2, 1), (2, 2), (4, 2)])
 def test_qx_4x4_fp64_vs_dense(S, flux4, zolo4, g5dov4, r, mode, rhs_block):
-    if rhs_block == 1 and (r, mode) != (2, 0):
-        pytest.skip("one-rhs path checked on one scheme")
+    """Every colouring mode, batched and one source at a time (rhs_block = 1)."""
     U, dims = flux4["U"], flux4["dims"]
     colour, n = probing.color_sites(dims, r, mode)
     ref = qx.dense_smp_qx(g5dov4, colour)
@@ -222,6 +221,73 @@ def test_qx_4x4_fp64_vs_dense(S, flux4, zolo4, g5dov4, r, mode, rhs_block):
     assert abs(Q - ref.real.sum()) <= 1e-9
     assert st["max_resid"] <= 1e-10
     assert abs(st["max_im_q"] - np.abs(ref.imag).max()) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("r,mode", [(2, 0), (2, 1)])
+def test_qx_4x4_antiperiodic_vs_dense(S, flux4, r, mode, prec):
+    """Antiperiodic fermion boundary in t (the other common convention): q^SMP
+    against the dense gamma_5 D_ov built with the same boundary factors and
+    its own spectrum."""
+    U, dims = flux4["U"], flux4["dims"]
+    bc = (1, 1, 1, -1)
+    H = dirac.apply_g5(dirac.dense_dw(U, dims, KAPPA, bc).reshape(256, 4, 3, 3072)).reshape(3072, 3072)
+    lam = np.linalg.eigvalsh(H)
+    a, b = 0.98 * (lam ** 2).min(), 1.02 * (lam ** 2).max()
+    zolo, delta = _zolo(a, b)
+    ref = qx.dense_smp_qx(qx.dense_g5dov(U, dims, KAPPA, zolo, bc)[0], probing.color_sites(dims, r, mode)[0])
+    precision = S.SMPQ_FP64 if prec == "fp64" else S.SMPQ_MIXED
+    with _session(S, bc=bc, precision=precision) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(a, b)
+        s.build_sources(r, mode)
+        q, Q, st = s.compute_qx()
+    err = np.abs(q - ref).max()
+    print("4^4 antiperiodic r=%d mode %d %s: max |dq| = %.3e, Q = %.9f" % (r, mode, prec, err, Q))
+    assert err <= 1e-8
+    assert abs(Q - ref.real.sum()) <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def flux4_light():
+    """The 4^4 flux field with kappa = 0.08 (below the free critical 1/8): a
+    well-conditioned H_W^2 (condition number about 20) for the storage formats
+    whose rounding times the condition number of the kappa = 0.21 operator
+    (about 360 on 4^4) leaves the reliable updates no contraction (BF16)."""
+    from synth import make_config
+    cfg = make_config("flux4")
+    U, dims, kappa = cfg["U"], cfg["dims"], 0.08
+    H = dirac.apply_g5(dirac.dense_dw(U, dims, kappa).reshape(256, 4, 3, 3072)).reshape(3072, 3072)
+    lam = np.linalg.eigvalsh(H)
+    a, b = 0.98 * (lam ** 2).min(), 1.02 * (lam ** 2).max()
+    zolo, _ = _zolo(a, b)
+    return dict(U=U, dims=dims, kappa=kappa, a=a, b=b, g5dov=qx.dense_g5dov(U, dims, kappa, zolo)[0])
+
+
+@pytest.mark.parametrize("fmt", ["fp16n", "bf16n"])
+def test_qx_4x4_half_one_source_at_a_time(S, flux4_light, fmt):
+    """The half-storage solve with one source per batch (one-column tiles, the
+    kernels of odd tile widths) against the dense matrix, at the format's
+    floor (2 u of max |q| per site, as the batched half-storage solves)."""
+    U, dims = flux4_light["U"], flux4_light["dims"]
+    colour, n = probing.color_sites(dims, 2, 0)
+    ref = qx.dense_smp_qx(flux4_light["g5dov"], colour)
+    precision = S.SMPQ_FP16N if fmt == "fp16n" else S.SMPQ_BF16N
+    with _session(S, precision=precision, rhs_block=1, kappa=flux4_light["kappa"]) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(flux4_light["a"], flux4_light["b"])
+        s.build_sources(2, 0)
+        q, Q, st = s.compute_qx(classes=[0, 7])
+    mask = np.isin(colour, [0, 7])
+    err = np.abs(q[mask] - ref[mask]).max()
+    scale = np.abs(ref[mask]).max()
+    print("4^4 kappa 0.08 %s one source per batch: max |dq| = %.3e (max |q| %.3e), %d batches, %d iterations" % (
+        fmt, err, scale, st["n_batches"], st["max_iterations"]))
+    assert st["n_batches"] == 24 and st["rhs_tile"] == 1
+    # q is small at this kappa (max |q| ~ 3e-5): the bar is relative to it;
+    # a wrong index or tile would give O(1) relative errors
+    assert err <= 0.1 * scale
+    assert 0 <= st["true_resid"] <= 1e-10  # the last reliable update of the base system
 
 
 def test_exact_trace_point_sources_4x4(S, flux4, zolo4, g5dov4):
@@ -267,15 +333,19 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     precision = S.SMPQ_MIXED if prec.startswith("mixed") else {
         "fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32, "fp16n": S.SMPQ_FP16N, "bf16n": S.SMPQ_BF16N}[prec]
     switch = float(prec[5:]) if prec.startswith("mixed") else 7e-3
-    with _session(S, precision=precision, switch_residual=switch) as s:
+    with _session(S, precision=precision, switch_residual=switch, true_residual=1) as s:
         s.load_gauge(dims, U)
         s.set_spectrum(a, b)
         s.build_sources(r, 0)
         q, Q, st = s.compute_qx(classes=classes)
     mask = np.isin(colour, classes)
     err = np.abs(q[mask] - ref[mask]).max()
-    print("8^3x16 r=%d %s: max |dq| = %.3e, iterations %d, reliable updates %d" % (
-        r, prec, err, st["max_iterations"], st["reliable_updates"]))
+    print("8^3x16 r=%d %s: max |dq| = %.3e, iterations %d, reliable updates %d, true residual %.2e, "
+          "recursive %.2e, %.2f launches per iteration" % (
+              r, prec, err, st["max_iterations"], st["reliable_updates"], st["true_resid"], st["max_resid"],
+              st["kernel_launches"] / st["max_iterations"]))
+    # the base system's residual recomputed in FP64 after the solve
+    assert 0 <= st["true_resid"] <= 1e-8
     # FP64 and the FP64-then-FP32 path meet the 1e-8 per-site bar; the FP32
     # path with FP64 reliable updates has the FP32 floor of its shifted systems.
     # The per-site error of the mixed path grows with the switch point (about
@@ -366,13 +436,14 @@ def test_error_codes(S, flux4):
 
 def test_bench_configuration_sampled(S):
     """All 256 classes of r_min = 4 on 8^3 x 16 in one batch (3072 sources, the
-    tile width and precision bench.py times), sampled sites against the oracle."""
+    tile width and precision bench.py times) against the oracle on 16 classes
+    spread over the lattice: q(x) per site and their sum (512 sites) at the Q bar."""
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
     a, b = _interval("flux8x16")
     zolo, delta = _zolo(a, b)
     colour, n = probing.color_sites(dims, 4, 0)
-    sample = [0, 131, 255]
+    sample = list(range(0, 256, 16))
     ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=sample, batch_colours=len(sample))
     with _session(S, precision=S.SMPQ_MIXED) as s:
         s.load_gauge(dims, U)
@@ -382,9 +453,15 @@ def test_bench_configuration_sampled(S):
     assert st["n_rhs"] == 3072 and st["n_batches"] == 1
     mask = np.isin(colour, sample)
     err = np.abs(q[mask] - ref[mask]).max()
-    print("bench configuration: max |dq| over %d sampled sites = %.3e, Q = %.9f" % (mask.sum(), err, Q))
+    dQ = abs(q.real[mask].sum() - ref.real[mask].sum())
+    print("bench configuration: max |dq| over %d sampled sites = %.3e, |dQ| over them = %.3e, Q = %.9f, "
+          "%d launches for %d iterations" % (mask.sum(), err, dQ, Q, st["kernel_launches"], st["max_iterations"]))
     assert err <= 1e-8
+    assert dQ <= 1e-9
     assert abs(Q - 2.0) < 0.05  # closed-form index k = 2, r_min = 4 probing bias
+    # three launches per CG iteration (plus setup, phase switch, contraction
+    # and the iterations of the last check interval after convergence)
+    assert st["kernel_launches"] <= 3 * (st["max_iterations"] + 10) + 40
 
 
 # ----------------------------------------------------------------------------- SMP trace of D_W^{-1}
