@@ -401,6 +401,9 @@ def run_gpu(args):
     out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream) if rank == 0 else {}
     if rank == 0 and args.uneven:
         out["uneven_batch"] = _uneven(args, prec, dev, stream)
+    if rank == 0 and not args.no_extra:
+        out["c3_16x32"] = _c3_record(args, dev, stream)
+        out["c5_32x64"] = _c5_record(args, dev, stream)
     if rank == 0 and not args.no_baselines and args.low_modes > 0 and sub is None:
         q_ref = (q_re + 1j * q_im).cpu().numpy()
         out["low_mode_projection"] = _low_modes(args, dims, U, V, a, b, prec, dev, stream, q_ref)
@@ -502,6 +505,76 @@ def _low_modes(args, dims, U, V, a, b, prec, dev, stream, q_ref):
             "max_eig_residual": float(res.max()), "max_iterations": st["max_iterations"], "Q": Q,
             "max_abs_dq_vs_headline": float(np.abs(q - q_ref).max()),
             "note": "setup (the eigen-solve) is per gauge field and not in value"}
+
+
+def _one_step(name, dims, U, r, prec, dev, stream, switch, max_iter=5000, classes=None, lanczos=300):
+    """One untimed-setup, timed q(x) step of a configuration in one precision:
+    GPU Lanczos interval (setup), then compute_qx (all classes or a subset)."""
+    import torch
+
+    from paper_1901_02211_gb300 import Session, smpq
+    V = int(np.prod(dims))
+    with Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=0, iters_per_check=10,
+                 use_graphs=1, switch_residual=switch, max_iter=max_iter) as s:
+        s.load_gauge(dims, U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lo, hi = s.measure_spectrum(lanczos)
+        setup = time.perf_counter() - t0
+        s.set_spectrum(0.98 * lo, 1.02 * hi)
+        n_classes = s.build_sources(r, MODE)
+        t0 = time.perf_counter()
+        try:
+            q, Q, st = s.compute_qx(classes=classes)
+            err = None
+        except smpq.SmpqError as e:
+            err = str(e)
+        dt = time.perf_counter() - t0
+    if err is not None:
+        return {"error": err, "seconds": dt, "lambda2_min": lo, "lambda2_max": hi, "max_iter": max_iter}
+    nc = n_classes if classes is None else len(classes)
+    rec = {"value": V * nc / n_classes / dt, "unit": "sites/s", "seconds": dt, "setup_lanczos_s": setup,
+           "extrapolated": classes is not None and nc < n_classes,
+           "sources": 12 * nc, "batches": st["n_batches"], "rhs_tile": st["rhs_tile"],
+           "iterations": st["max_iterations"], "reliable_updates": st["reliable_updates"],
+           "true_resid_base": st["true_resid"], "max_resid": st["max_resid"], "Q": Q,
+           "abs_Q_minus_round": st["q_round_dev"], "max_im_q": st["max_im_q"],
+           "lambda2_min": lo, "lambda2_max": hi}
+    return rec
+
+
+def _c3_record(args, dev, stream):
+    """16^3 x 32 flux configuration (Q = -1, noise 0.15), r_min = 4: all 3072
+    sources, one step in the mixed (headline) precision and one with FP16
+    storage, per-site norms and reconstruct-12 links."""
+    from paper_1901_02211_gb300 import smpq
+    from synth import make_config
+    cfg = make_config("flux16x32")
+    out = {"workload": "16x16x16x32 flux Q=%d noise 0.15 + gauge transform, r_min=4, 256 classes x 12 = 3072 "
+                       "sources x 14 shifts, tol 1e-10" % cfg["Q_closed"]}
+    for key, prec in (("mixed", smpq.SMPQ_MIXED), ("fp16n", smpq.SMPQ_FP16N)):
+        out[key] = _one_step("flux16x32", cfg["dims"], cfg["U"], 4, prec, dev, stream, args.switch)
+    return out
+
+
+def _c5_record(args, dev, stream):
+    """32^3 x 64 stout-smoothed Haar configuration, r_min = 8: one colour class
+    (12 sources, the batch the configuration names) in FP32 with FP64
+    reliable updates; the throughput is that class's sites per second scaled
+    to the lattice, labelled extrapolated.  On this rough field H_W is barely
+    gapped, so the iteration cap is raised (bounded) and |Q - round Q| of the
+    class's sites is reported, not asserted."""
+    from paper_1901_02211_gb300 import smpq
+    from synth import make_config
+    t0 = time.perf_counter()
+    cfg = make_config("stout32x64")
+    gen = time.perf_counter() - t0
+    rec = _one_step("stout32x64", cfg["dims"], cfg["U"], 8, smpq.SMPQ_FP32, dev, stream, args.switch,
+                    max_iter=args.c5_max_iter, classes=[0])
+    rec["generation_s"] = gen
+    rec["workload"] = ("32x32x32x64 Haar seed 5001 + 20 stout steps rho 0.1, r_min=8, class 0 of 4096 "
+                       "(12 sources), FP32 + FP64 reliable updates, tol 1e-10, max_iter %d" % args.c5_max_iter)
+    return rec
 
 
 def _uneven(args, prec, dev, stream):
@@ -677,8 +750,9 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
                          for kk, v in kern.items()},
         "solver": {"iterations": st["max_iterations"], "reliable_updates": st["reliable_updates"],
                    "max_resid": st["max_resid"], "true_resid_base": stt["true_resid"],
-                   "true_resid_note": "FP64 |b - (H^2 + s0) x| / |b| of the smallest shift after the solve "
-                                      "(x accumulated in FP64 in a verification step)",
+                   "true_resid_note": "|b - (H^2 + s0) x| / |b| of the smallest shift recomputed with FP64 "
+                                      "accuracy after the solve (mixed, FP32, half: the last residual replacement; "
+                                      "FP64: x accumulated in a verification step)",
                    "Q": st["Q"], "abs_Q_minus_round": st["q_round_dev"], "max_im_q": st["max_im_q"],
                    "profiled_step_ms": stp["total_ms"], "timed_step_ms": ms,
                    "kernel_ms_per_step": {kk: v["share_ms"] for kk, v in kern.items()},
@@ -714,6 +788,9 @@ def main():
     ap.add_argument("--uneven", action="store_true",
                     help="also time the uneven batch of three lattices (8^3x16, 12^3x24, 16^3x32) in one call")
     ap.add_argument("--lanczos", type=int, default=300, help="Lanczos steps of the spectrum setup")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the one-step records of the 16^3x32 and 32^3x64 configurations")
+    ap.add_argument("--c5-max-iter", type=int, default=12000, help="iteration cap of the 32^3x64 record")
     ap.add_argument("--no-autotune", action="store_true",
                     help="widest RHS tile that divides the batch, without timing the candidates")
     args = ap.parse_args()

@@ -89,7 +89,9 @@ typedef struct {
     int use_graphs;        /* capture those iterations in a CUDA graph */
     int profile;           /* time every D_W / D_W^dag launch of the solver with CUDA events */
     double switch_residual; /* SMPQ_MIXED: relative residual at which FP64 iterations hand over to FP32 */
-    int autotune;           /* time the RHS tile widths (12, 24, 48) on the first solve of each shape */
+    int autotune;           /* time the D_W launch shapes (RHS tile 12, 24, 48; tiles per block 1, 2,
+                               4, 8; FP32 columns per thread 1, 2) on the first solve of each batch
+                               shape, and use the fastest */
     int full_support;       /* q(x): keep the shifted directions on every site instead of only where
                                z = D_W y is read (the ablation of that restriction; same result,
                                14 full-lattice vectors per source) */
@@ -97,6 +99,9 @@ typedef struct {
                                (FP64, whole lattice: two more FP64 fields per source) and report
                                max |b - (H^2 + s0) x| / |b| in smpq_stats.true_resid.  The FP32 and
                                half paths report it from their last reliable update at no cost. */
+    const char *tune_cache; /* path of a text file of tuned launch shapes (NULL: none): read before
+                               tuning a new shape, appended after (see smpq_tune_cache_lookup).  The
+                               context copies the path. */
 } smpq_options;
 
 typedef struct {
@@ -125,14 +130,18 @@ typedef struct {
     int rhs_tile;           /* RHS tile width the solves used (autotuned or fixed) */
     double q_round_dev;     /* |Q - round(Q)| of the processed sites (the charge is an integer) */
     double true_resid;      /* largest true relative residual |b - (H^2 + s0) x| / |b| of the base
-                               (smallest) shift, recomputed in FP64 after the solve; -1 when not
-                               computed (SMPQ_FP64 / SMPQ_MIXED without the true_residual option) */
+                               (smallest) shift, recomputed with FP64 accuracy after the solve; -1
+                               when not computed (SMPQ_FP64 without the true_residual option) */
+    int tiles_per_block_hi; /* launch shape of the D_W kernels (autotuned): tiles per block of the */
+    int tiles_per_block_lo; /*   FP64-accurate and of the FP32 / half-storage iterations, */
+    int cols_per_thread;    /*   FP32 columns per thread (1 or 2), */
+    int shape_from_cache;   /*   1 if the shape came from the tune_cache file */
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
  * 10 iterations per check, graphs on, profiling off, switch_residual 7e-3,
- * autotuning on, no true-residual accumulation. */
+ * autotuning on, no true-residual accumulation, no tuning cache file. */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.
@@ -287,6 +296,24 @@ int smpq_compute_qx_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, 
  * context's precision.  Needs a gauge field and a colouring scheme (no
  * spectrum).  t_re, t_im: double[V], host or device. */
 int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, double *T, smpq_stats *stats);
+
+/* The autotuner's cache file (host only; not part of the paper's method).
+ * A shape is {RHS tile width (1, 12, 24, 48), tiles per block of the
+ * FP64-accurate D_W launches, tiles per block of the FP32 / half-storage ones,
+ * FP32 columns per thread (1, 2)}, keyed by a device string (as the library
+ * writes it: "<name>/<SMs>sm"), the lattice dims, the batch B and the
+ * precision.  One line per entry:
+ *   smpq-tune-1|<device>|<nx> <ny> <nz> <nt>|<B>|<precision>|<bc> <tpb_hi> <tpb_lo> <nr>|<ms>
+ * lookup: SMPQ_OK and shape[4] filled from the last matching well-formed line,
+ * SMPQ_ESTATE if the file is missing or has no such line, SMPQ_EINVAL for
+ * NULL arguments.  store: appends one line (ms = the tuner's estimate per
+ * iteration pair); SMPQ_EINVAL if the file cannot be opened or the device
+ * string holds '|' or a newline.  Neither call takes a lock: processes that
+ * tune the same shape at once both append, and the last line wins. */
+int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[4], int B, int precision,
+                           int shape[4]);
+int smpq_tune_cache_store(const char *path, const char *device, const int dims[4], int B, int precision,
+                          const int shape[4], double ms);
 
 /* Measured arithmetic peak of GPU `device` (not part of the paper's method: the
  * denominator of the ALU rooflines the solver's FP64-accurate kernels are

@@ -1,6 +1,7 @@
 // C ABI of libsmpq (declared and documented in include/smpq.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -135,41 +136,119 @@ void set_geom(smpq_ctx *ctx) {
     g.V = ctx->V;
 }
 
-// RHS tile width: measured once per (V, B, precision) on the first solve of
-// that shape (the autotuner), among the widths that divide B; a fixed choice
-// when autotuning is off or B has a single candidate.  The workspace it times
-// on is the solver's own (allocated anyway for the solve).
-int tune_bc(smpq_ctx *ctx, int B, int prec) {
-    if (B == 1) return 1;
+// ---------------------------------------------------------------- autotuner
+// The shape of the solver's D_W launches: RHS tile width BC (12, 24 or 48,
+// shared by both phases of the mixed solve: its fields change precision in
+// place), tiles per block of the FP64-accurate and of the FP32 / half-storage
+// iterations (1, 2, 4 or 8), and columns per thread of the FP32 kernels (1 or
+// 2).  Chosen once per (device, lattice, B, precision) by timing the D_W pair
+// of every candidate on the solver's own workspace; kept in the context and,
+// with opt.tune_cache set, in a text file that later processes read first.
+struct Shape {
+    int bc, tpb_hi, tpb_lo, nr;
+};
+
+std::string device_key(int dev) {
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    return std::string(pr.name) + "/" + std::to_string(pr.multiProcessorCount) + "sm";
+}
+
+std::string cache_key(const char *device, const int dims[4], int B, int precision) {
+    return std::string("smpq-tune-1|") + device + "|" + std::to_string(dims[0]) + " " + std::to_string(dims[1]) +
+           " " + std::to_string(dims[2]) + " " + std::to_string(dims[3]) + "|" + std::to_string(B) + "|" +
+           std::to_string(precision) + "|";
+}
+
+int tune_kind_lo(int prec) {
+    return prec == SMPQ_FP64 ? 0 : prec == SMPQ_FP16N ? 3 : prec == SMPQ_BF16N ? 4 : 1;
+}
+
+Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
+    *cached = 0;
+    Shape def{1, 4, 4, 1};
+    if (B == 1) return def;
     std::vector<int> cand;
     for (int bc : {12, 24, 48})
         if (B % bc == 0) cand.push_back(bc);
-    if (cand.empty()) return 1;
-    // (the half-storage iterations are not timed: widest tile)
-    if (!ctx->opt.autotune || cand.size() == 1 || prec == SMPQ_FP16N || prec == SMPQ_BF16N) return cand.back();
+    if (cand.empty()) return def;
+    def.bc = cand.back();
+    if (!ctx->opt.autotune) return def;
     for (auto &e : ctx->tuned)
-        if (e[0] == ctx->V && e[1] == B && e[2] == prec) return e[3];
+        if (e.dims == std::array<int, 4>{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]} && e.B == B &&
+            e.prec == prec) {
+            *cached = e.from_file;
+            return Shape{e.shape[0], e.shape[1], e.shape[2], e.shape[3]};
+        }
+    const std::string dev = device_key(ctx->device);
+    int sh[4];
+    if (!ctx->tune_cache.empty() &&
+        smpq_tune_cache_lookup(ctx->tune_cache.c_str(), dev.c_str(), ctx->dims, B, prec, sh) == SMPQ_OK &&
+        B % sh[0] == 0) {
+        ctx->tuned.push_back({{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]}, B, prec, {sh[0], sh[1], sh[2], sh[3]}, 1});
+        *cached = 1;
+        return Shape{sh[0], sh[1], sh[2], sh[3]};
+    }
     const size_t nf = (size_t)B * 12 * ctx->V;
-    if (ensure(ctx, ctx->ws[W_P], 3 * nf * sizeof(df64c)) || ensure(ctx, ctx->ws[W_PART], (size_t)2 * nf / 12 * sizeof(double) + 64) ||
+    if (ensure(ctx, ctx->ws[W_P], 3 * nf * sizeof(df64c)) ||
+        ensure(ctx, ctx->ws[W_PART], (size_t)2 * nf / 12 * sizeof(double) + 64) ||
         ensure(ctx, ctx->ws[W_SCAL], (size_t)B * sizeof(double))) {
         cudaGetLastError();
-        return cand.back();
+        return def;
     }
     cudaMemsetAsync(ctx->ws[W_P].p, 0, 3 * nf * sizeof(df64c), ctx->stream);
     cudaMemsetAsync(ctx->ws[W_SCAL].p, 0, (size_t)B * sizeof(double), ctx->stream);
-    int best = cand.back();
+    void *buf = ctx->ws[W_P].p;
+    double *part = (double *)ctx->ws[W_PART].p, *alpha = (double *)ctx->ws[W_SCAL].p;
+    const int kind_lo = tune_kind_lo(prec);
+    const bool mixed = prec == SMPQ_MIXED, fp64 = prec == SMPQ_FP64;
+    Shape best = def;
     float tbest = 1e30f;
     for (int bc : cand) {
-        float t = time_dslash_pair(ctx, prec, B, bc, 3, ctx->ws[W_P].p, (double *)ctx->ws[W_PART].p,
-                                   (double *)ctx->ws[W_SCAL].p);
-        ctx->launches += 8 * (prec == SMPQ_MIXED ? 2 : 1);
-        if (t > 0 && t < tbest) {
-            tbest = t;
-            best = bc;
+        Shape s{bc, 4, 4, 1};
+        float tlo = 1e30f, thi = 0.f;
+        // the FP32 / half / FP64 iterations (FP64 runs with the tiles-per-block
+        // of the FP64-accurate iterations)
+        for (int tpb : {1, 2, 4, 8})
+            for (int nr : {1, 2}) {
+                if (nr == 2 && kind_lo != 1) continue;
+                const float t = time_dslash_pair(ctx, kind_lo, B, bc, tpb, nr, fp64 ? 2 : 3, buf, part, alpha);
+                ctx->launches += 2 * (1 + (fp64 ? 2 : 3));
+                if (t > 0 && t < tlo) {
+                    tlo = t;
+                    if (fp64) s.tpb_hi = tpb;
+                    else s.tpb_lo = tpb;
+                    s.nr = nr;
+                }
+            }
+        if (mixed) { // the float-float iterations: about a fifth of the solve
+            float th = 1e30f;
+            for (int tpb : {1, 2, 4, 8}) {
+                const float t = time_dslash_pair(ctx, 2, B, bc, tpb, 1, 2, buf, part, alpha);
+                ctx->launches += 6;
+                if (t > 0 && t < th) {
+                    th = t;
+                    s.tpb_hi = tpb;
+                }
+            }
+            thi = th;
+        }
+        const float est = mixed ? 0.2f * thi + 0.8f * tlo : tlo;
+        if (est < tbest) {
+            tbest = est;
+            best = s;
         }
     }
     cudaGetLastError();
-    ctx->tuned.push_back({ctx->V, B, prec, best});
+    ctx->tuned.push_back({{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]}, B, prec,
+                          {best.bc, best.tpb_hi, best.tpb_lo, best.nr}, 0});
+    if (!ctx->tune_cache.empty()) {
+        const int shape[4] = {best.bc, best.tpb_hi, best.tpb_lo, best.nr};
+        smpq_tune_cache_store(ctx->tune_cache.c_str(), dev.c_str(), ctx->dims, B, prec, shape, tbest);
+    }
     return best;
 }
 
@@ -178,8 +257,8 @@ size_t bytes_per_rhs(const smpq_ctx *ctx, int prec, int n_sup, int npoles) {
     const bool half = prec == SMPQ_FP16N || prec == SMPQ_BF16N;
     size_t per = prec == SMPQ_FP32 ? (4 * 8 + 2 * 16)
                  : half            ? (2 * 5 + 2 * 8 + 2 * 16) // p, t: 4 B + a 12th of the 4-byte norm
-                                   : (prec == SMPQ_MIXED ? 3 * 16 + 3 * 8 : 3 * 16);
-    if (ctx->opt.true_residual && (prec == SMPQ_FP64 || prec == SMPQ_MIXED)) per += 2 * 16; // x64, t64
+                                   : (prec == SMPQ_MIXED ? 4 * 16 + 4 * 8 : 3 * 16); // MIXED: p t r x_hi, p t r x_lo
+    if (ctx->opt.true_residual && prec == SMPQ_FP64) per += 2 * 16; // x64, t64
     size_t full = (size_t)ctx->V * 12 * per;
     size_t eb = (prec == SMPQ_FP32 || half) ? 8 : (prec == SMPQ_MIXED ? 16 + 8 : 16); // MIXED: FP64 and FP32 copies
     size_t sup = (size_t)n_sup * 12 * (npoles * eb + 16);
@@ -229,7 +308,9 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     }
     if (B > 1) B -= B % 12;
     if (B < 1) B = 1;
-    const int BC = tune_bc(ctx, B, prec);
+    int from_cache = 0;
+    const Shape shape = tune_shape(ctx, B, prec, &from_cache);
+    const int BC = shape.bc;
     ctx->last_bc = BC;
     // qterm + device q
     if ((rc = ensure(ctx, ctx->ws[W_QTERM], (size_t)ctx->n_classes * 12 * ctx->members * sizeof(double2)))) return rc;
@@ -255,6 +336,9 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     spec.d_src_comp = d_src_comp;
     spec.d_src_field = nullptr;
     spec.shifts = nullptr;
+    spec.tpb_hi = shape.tpb_hi;
+    spec.tpb_lo = shape.tpb_lo;
+    spec.nr = shape.nr;
     ShiftParams cg; // kind 1: one unshifted system D_W^dag D_W x = D_W^dag b, y = x
     if (kind == 1) {
         cg.n = 1;
@@ -389,6 +473,10 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->Q = tot[0];
         stats->q_round_dev = std::fabs(tot[0] - std::nearbyint(tot[0]));
         stats->true_resid = true_res;
+        stats->tiles_per_block_hi = shape.tpb_hi;
+        stats->tiles_per_block_lo = shape.tpb_lo;
+        stats->cols_per_thread = shape.nr;
+        stats->shape_from_cache = from_cache;
         stats->solve_ms = solve_ms;
         stats->total_ms = tms;
         stats->kernel_launches = ctx->launches;
@@ -430,6 +518,41 @@ int smpq_options_default(smpq_options *o) {
     return SMPQ_OK;
 }
 
+int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[4], int B, int precision,
+                           int shape[4]) {
+    if (!path || !device || !dims || !shape || B < 1) return SMPQ_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return SMPQ_ESTATE;
+    const std::string key = cache_key(device, dims, B, precision);
+    char line[1024];
+    int rc = SMPQ_ESTATE;
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::strncmp(line, key.c_str(), key.size()) != 0) continue;
+        int v[4];
+        double ms;
+        if (std::sscanf(line + key.size(), "%d %d %d %d|%lf", &v[0], &v[1], &v[2], &v[3], &ms) == 5 &&
+            (v[0] == 1 || v[0] == 12 || v[0] == 24 || v[0] == 48) && v[1] >= 1 && v[1] <= 64 && v[2] >= 1 &&
+            v[2] <= 64 && (v[3] == 1 || v[3] == 2)) {
+            std::copy(v, v + 4, shape); // the last matching line wins
+            rc = SMPQ_OK;
+        }
+    }
+    std::fclose(f);
+    return rc;
+}
+
+int smpq_tune_cache_store(const char *path, const char *device, const int dims[4], int B, int precision,
+                          const int shape[4], double ms) {
+    if (!path || !device || !dims || !shape || B < 1 || std::strchr(device, '|') || std::strchr(device, '\n'))
+        return SMPQ_EINVAL;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return SMPQ_EINVAL;
+    const std::string key = cache_key(device, dims, B, precision);
+    std::fprintf(f, "%s%d %d %d %d|%.6g\n", key.c_str(), shape[0], shape[1], shape[2], shape[3], ms);
+    std::fclose(f);
+    return SMPQ_OK;
+}
+
 int smpq_create(smpq_ctx **out, int device, void *stream, const smpq_options *opt) {
     if (!out) return SMPQ_EINVAL;
     *out = nullptr;
@@ -437,6 +560,8 @@ int smpq_create(smpq_ctx **out, int device, void *stream, const smpq_options *op
     if (!ctx) return SMPQ_ENOMEM;
     if (opt) ctx->opt = *opt;
     else smpq_options_default(&ctx->opt);
+    ctx->tune_cache = ctx->opt.tune_cache ? ctx->opt.tune_cache : "";
+    ctx->opt.tune_cache = nullptr; // the context keeps its own copy of the path
     int rc = validate_options(ctx, &ctx->opt);
     if (rc) { delete ctx; return rc; }
     int ndev = 0;
@@ -507,6 +632,8 @@ int smpq_set_options(smpq_ctx *ctx, const smpq_options *opt) {
     if (rc) return rc;
     bool respec = opt->npoles != ctx->opt.npoles;
     ctx->opt = *opt;
+    ctx->tune_cache = opt->tune_cache ? opt->tune_cache : "";
+    ctx->opt.tune_cache = nullptr;
     if (ctx->have_gauge) set_geom(ctx);
     if (respec && ctx->have_spec) return smpq_set_spectrum(ctx, ctx->lmin2, ctx->lmax2);
     return SMPQ_OK;

@@ -38,6 +38,7 @@ namespace {
 // tile, and blocks are numbered site-major inside an RHS tile, so the blocks
 // resident at any moment cover a narrow band of the lattice for few RHS tiles:
 // the +-t neighbours (V/n_t sites away) are still in L2 when they are read.
+// (The D_W kernels take the count as an argument, chosen by the autotuner.)
 constexpr int TPB = 4;
 
 // minimum resident blocks per SM requested from the register allocator for
@@ -208,11 +209,12 @@ struct Fuse {
 
 // Called by every thread of a block after its partial sums are stored: true
 // in every thread of the block that arrives last among the G blocks of RHS
-// tile blockIdx.y.  The partial stores are fenced before the arrival count,
-// so the last block sees every partial of its tile.
-__device__ __forceinline__ bool last_block_of_tile(int *count, int G) {
+// tile blockIdx.y.  The threads that stored partials (wrote) fence them before
+// the arrival count, so the last block sees every partial of its tile; the
+// other threads' stores need no fence (the next launch sees them).
+__device__ __forceinline__ bool last_block_of_tile(int *count, int G, bool wrote) {
     __shared__ int last;
-    __threadfence();
+    if (wrote) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const int ticket = atomicAdd(&count[blockIdx.y], 1);
@@ -246,7 +248,7 @@ template <int BC, int NT> __device__ double tile_sum(const double *part, int chu
 template <int BC, int NT>
 __device__ __forceinline__ void fuse_step1(const Fuse &f, const double *part_t, const double *part_p, int G,
                                            double *sm) {
-    if (!f.count || !last_block_of_tile(f.count, G)) return;
+    if (!f.count || !last_block_of_tile(f.count, G, threadIdx.x < BC)) return;
     const double tt = tile_sum<BC, NT>(part_t, blockIdx.y, G, sm);
     const double pp = tile_sum<BC, NT>(part_p, blockIdx.y, G, sm);
     if (threadIdx.x < BC) s1_column(blockIdx.y * BC + threadIdx.x, tt, pp, f.sc, f.sp, f.B);
@@ -254,7 +256,7 @@ __device__ __forceinline__ void fuse_step1(const Fuse &f, const double *part_t, 
 // end of lattice kernel B: the tile's last block runs the second scalar step
 template <int BC, int NT>
 __device__ __forceinline__ void fuse_step2(const Fuse &f, const double *part_r, int G, double *sm) {
-    if (!f.count || !last_block_of_tile(f.count, G)) return;
+    if (!f.count || !last_block_of_tile(f.count, G, threadIdx.x < BC)) return;
     const double rr = tile_sum<BC, NT>(part_r, blockIdx.y, G, sm);
     if (threadIdx.x < BC)
         s2_column(blockIdx.y * BC + threadIdx.x, rr, f.sc, f.sp, f.B, f.tol2, f.delta2, f.theta2);
@@ -264,7 +266,7 @@ __device__ __forceinline__ void fuse_step2(const Fuse &f, const double *part_r, 
 template <typename T, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     k_init(Geom g, Source src, typename cplx_t<T>::type *r, typename cplx_t<T>::type *p,
-           typename cplx_t<T>::type *xlo, double2 *xhi, double *part, int G) {
+           typename cplx_t<T>::type *xlo, df64c *xhi, double *part, int G) {
     typedef typename cplx_t<T>::type C;
     __shared__ double sm[TileMap<BC>::THREADS];
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             r[o] = v;
             p[o] = v;
             if (xlo) xlo[o] = mkc<C>(0, 0);
-            if (xhi) xhi[o] = make_double2(0, 0);
+            if (xhi) xhi[o] = df64c{df64(0.f), df64(0.f)};
             acc += b.x * b.x + b.y * b.y;
         }
     }
@@ -322,7 +324,7 @@ template <int BC, int NR> struct SmemCols {
 template <typename T, int BC, int NR>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_a(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ p,
-              typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G, Fuse f) {
+              typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G, int tpb, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
     __shared__ double sm[SmemCols<BC, NR>::N];
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     double at[NR], ap[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) at[r] = ap[r] = 0;
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
         int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
         C acc[12][NR];
@@ -369,13 +371,12 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     fuse_step1<BC, TM::THREADS>(f, part_t, part_p, G, sm);
 }
 
-// r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2 (NR columns per thread)
-template <typename T, int BC, int NR, bool REL>
+// r -= alpha (D_W^dag t + s0 p); partial |r|^2 (NR columns per thread)
+template <typename T, int BC, int NR>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_b(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ t,
               const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ r,
-              typename cplx_t<T>::type *__restrict__ xlo, const double *__restrict__ alpha, double s0, T kappa,
-              double *part_r, int G, Fuse f) {
+              const double *__restrict__ alpha, double s0, T kappa, double *part_r, int G, int tpb, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
     __shared__ double sm[SmemCols<BC, NR>::N];
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     double ar[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) ar[q] = 0;
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
         int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
         C acc[12][NR];
@@ -414,16 +415,6 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
                 sr[q] += rv[q].x * rv[q].x + rv[q].y * rv[q].y;
             }
             Cols<C, NR>::store(r + o, rv);
-            if (REL) {
-                C xv[NR];
-                Cols<C, NR>::load(xlo + o, xv);
-#pragma unroll
-                for (int q = 0; q < NR; ++q) {
-                    xv[q].x += a[q] * pv[q].x;
-                    xv[q].y += a[q] * pv[q].y;
-                }
-                Cols<C, NR>::store(xlo + o, xv);
-            }
         }
 #pragma unroll
         for (int q = 0; q < NR; ++q) ar[q] += (double)sr[q];
@@ -433,12 +424,21 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     fuse_step2<BC, TM::THREADS>(f, part_r, G, sm);
 }
 
+// The base system's solution x accumulated by the p update: FP64 for the FP64
+// iterations (the true-residual check), float-float for the FP64-accurate
+// first phase of the mixed solve (the x_hi its FP32 phase's reliable updates
+// continue from).
+template <typename T> struct XAcc { typedef double2 type; };
+template <> struct XAcc<df64> { typedef df64c type; };
+
 // p = r + beta p on the lattice tiles of tile group bx; with x64, first
-// x += alpha p (FP64, the base system's solution for the true residual)
+// x64 += alpha p, with xlo, first xlo += alpha p in T (the part of the base
+// solution that the next residual replacement folds into x_hi)
 template <typename T, int BC>
 __device__ __forceinline__ void update_p_tiles(int bx, int V, const typename cplx_t<T>::type *__restrict__ r,
                                                typename cplx_t<T>::type *__restrict__ p, const Scal &sc,
-                                               double2 *__restrict__ x64) {
+                                               typename XAcc<T>::type *__restrict__ x64,
+                                               typename cplx_t<T>::type *__restrict__ xlo) {
     typedef typename cplx_t<T>::type C;
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
     if (!sc.upd_rhs[j]) return;
@@ -453,11 +453,25 @@ __device__ __forceinline__ void update_p_tiles(int bx, int V, const typename cpl
         for (int c = 0; c < 12; ++c) {
             size_t o = base + ((size_t)s * 12 + c) * BC;
             C rv = r[o], pv = p[o];
+            if (xlo) {
+                C xv = xlo[o];
+                xv.x += (T)a * pv.x;
+                xv.y += (T)a * pv.y;
+                xlo[o] = xv;
+            }
             if (x64) {
-                double2 xv = x64[o];
-                xv.x += a * to_d(pv.x);
-                xv.y += a * to_d(pv.y);
-                x64[o] = xv;
+                if constexpr (std::is_same<T, df64>::value) {
+                    df64c xv = x64[o];
+                    const df64 ad(a);
+                    xv.x = fma_df(ad, pv.x, xv.x);
+                    xv.y = fma_df(ad, pv.y, xv.y);
+                    x64[o] = xv;
+                } else {
+                    double2 xv = x64[o];
+                    xv.x += a * to_d(pv.x);
+                    xv.y += a * to_d(pv.y);
+                    x64[o] = xv;
+                }
             }
             pv.x = rv.x + b * pv.x;
             pv.y = rv.y + b * pv.y;
@@ -482,7 +496,7 @@ template <> struct HLinks<B16> { static const void *get(const smpq_ctx *c) { ret
 // r = p = b (p in the half format), x_lo = x_hi = 0; partial |b|^2
 template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_init_h(Geom g, Source src, float2 *r, HF<HT> p, float2 *xlo, double2 *xhi, double *part, int G) {
+    k_init_h(Geom g, Source src, float2 *r, HF<HT> p, float2 *xlo, df64c *xhi, double *part, int G) {
     __shared__ double sm[TileMap<BC>::THREADS];
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
@@ -499,7 +513,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             v[c] = make_float2((float)b.x, (float)b.y);
             r[o] = v[c];
             xlo[o] = make_float2(0.f, 0.f);
-            xhi[o] = make_double2(0, 0);
+            xhi[o] = df64c{df64(0.f), df64(0.f)};
             acc += b.x * b.x + b.y * b.y;
         }
         st_site_half<HT, BC>(p.v + base + (size_t)s * 12 * BC, p.n + nbase + (size_t)s * BC, v);
@@ -512,13 +526,13 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     k_apply_a_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
-                double *part_p, int G, Fuse f) {
+                double *part_p, int G, int tpb, Fuse f) {
     __shared__ double sm[TileMap<BC>::THREADS];
     const int jj = threadIdx.x % BC, chunk = blockIdx.y;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     double at = 0, ap = 0;
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
         const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
         float2 acc[12][1];
@@ -550,19 +564,18 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     fuse_step1<BC, TileMap<BC>::THREADS>(f, part_t, part_p, G, sm);
 }
 
-// r -= alpha (D_W^dag t + s0 p); x_lo += alpha p (REL); partial |r|^2
-template <typename HT, int BC, bool REL>
+// r -= alpha (D_W^dag t + s0 p); partial |r|^2
+template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     k_apply_b_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
-                float2 *__restrict__ xlo, const double *__restrict__ alpha, double s0, float kappa, double *part_r,
-                int G, Fuse f) {
+                const double *__restrict__ alpha, double s0, float kappa, double *part_r, int G, int tpb, Fuse f) {
     __shared__ double sm[TileMap<BC>::THREADS];
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
     const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     const float a = (float)alpha[j], sh = (float)s0;
     double ar = 0;
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
         const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= g.V) continue;
         float2 acc[12][1];
@@ -583,12 +596,6 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
             rv.y = fmaf(-a, apv.y, rv.y);
             r[o] = rv;
             sr += rv.x * rv.x + rv.y * rv.y;
-            if (REL) {
-                float2 xv = xlo[o];
-                xv.x = fmaf(a, pv.x, xv.x);
-                xv.y = fmaf(a, pv.y, xv.y);
-                xlo[o] = xv;
-            }
         }
         ar += (double)sr;
     }
@@ -600,12 +607,12 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
 // p = r + beta p on the lattice tiles of tile group bx, p in the half format
 template <typename HT, int BC>
 __device__ __forceinline__ void update_p_h_tiles(int bx, int V, const float2 *__restrict__ r, HF<HT> p,
-                                                 const Scal &sc) {
+                                                 const Scal &sc, float2 *__restrict__ xlo) {
     const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
     if (!sc.upd_rhs[j]) return;
     const size_t base = (size_t)chunk * 12 * V * BC + jj, nbase = (size_t)chunk * V * BC + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-    const float b = (float)sc.beta[j];
+    const float b = (float)sc.beta[j], a = (float)sc.alpha[j];
     for (int tile = bx * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
         const int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
         if (s >= V) continue;
@@ -615,7 +622,14 @@ __device__ __forceinline__ void update_p_h_tiles(int bx, int V, const float2 *__
         float2 v[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            const float2 f = HT::f2(ps[c * BC]), rv = r[base + ((size_t)s * 12 + c) * BC];
+            const size_t o = base + ((size_t)s * 12 + c) * BC;
+            const float2 f = HT::f2(ps[c * BC]), rv = r[o];
+            if (xlo) { // x_lo += alpha p (p as stored: n times the half value)
+                float2 xv = xlo[o];
+                xv.x = fmaf(a * n, f.x, xv.x);
+                xv.y = fmaf(a * n, f.y, xv.y);
+                xlo[o] = xv;
+            }
             v[c] = make_float2(fmaf(b * n, f.x, rv.x), fmaf(b * n, f.y, rv.y));
         }
         st_site_half<HT, BC>(ps, pn, v);
@@ -637,7 +651,7 @@ template <int BC> __device__ __forceinline__ void st_rx2(float2 *p, float2 re, f
 template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     k_apply_a_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
-                 double *part_p, int G, Fuse f) {
+                 double *part_p, int G, int tpb, Fuse f) {
     typedef TileMap<BC, 2> TM;
     __shared__ double sm[SmemCols<BC, 2>::N];
     const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y;
@@ -645,7 +659,7 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     double at[2] = {0, 0}, ap[2] = {0, 0};
     const float2 nk = bc2(-kappa);
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
         const int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
         c2 acc[12];
@@ -677,11 +691,10 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     fuse_step1<BC, TM::THREADS>(f, part_t, part_p, G, sm);
 }
 
-template <typename HT, int BC, bool REL>
+template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     k_apply_b_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
-                 float2 *__restrict__ xlo, const double *__restrict__ alpha, double s0, float kappa, double *part_r,
-                 int G, Fuse f) {
+                 const double *__restrict__ alpha, double s0, float kappa, double *part_r, int G, int tpb, Fuse f) {
     typedef TileMap<BC, 2> TM;
     __shared__ double sm[SmemCols<BC, 2>::N];
     const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y, j = chunk * BC + jj;
@@ -690,7 +703,7 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     const float2 a = make_float2((float)alpha[j], (float)alpha[j + 1]), na = make_float2(-a.x, -a.y);
     const float2 sh = bc2((float)s0), nk = bc2(-kappa);
     double ar[2] = {0, 0};
-    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+    for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
         const int s = tile * TM::SPB + threadIdx.x / TM::TPS;
         if (s >= g.V) continue;
         c2 acc[12];
@@ -713,11 +726,6 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
             ri = __ffma2_rn(na, api, ri);
             st_rx2<BC>(r + o, rr, ri);
             sr = __ffma2_rn(rr, rr, __ffma2_rn(ri, ri, sr));
-            if (REL) {
-                float2 xr, xi;
-                ld_rx2<BC>(xlo + o, xr, xi);
-                st_rx2<BC>(xlo + o, __ffma2_rn(a, pr, xr), __ffma2_rn(a, pi, xi));
-            }
         }
         ar[0] += (double)sr.x;
         ar[1] += (double)sr.y;
@@ -805,11 +813,11 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     k_yp(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
          const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<TS>::type *__restrict__ ps,
          double2 *__restrict__ y, Scal sc, ShiftParams sp, int Gs, typename cplx_t<T>::type *__restrict__ p,
-         double2 *__restrict__ x64) {
+         typename XAcc<T>::type *__restrict__ x64, typename cplx_t<T>::type *__restrict__ xlo) {
     if ((int)blockIdx.x < Gs)
         shift_tiles<T, TS, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 0);
     else
-        update_p_tiles<T, BC>(blockIdx.x - Gs, V, r, p, sc, x64);
+        update_p_tiles<T, BC>(blockIdx.x - Gs, V, r, p, sc, x64, xlo);
 }
 
 // Launch YP of a half-storage iteration (p in the half format)
@@ -817,17 +825,17 @@ template <typename HT, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
     k_yp_h(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
            const float2 *__restrict__ r, float2 *__restrict__ ps, double2 *__restrict__ y, Scal sc, ShiftParams sp,
-           int Gs, HF<HT> p) {
+           int Gs, HF<HT> p, float2 *__restrict__ xlo) {
     if ((int)blockIdx.x < Gs)
         shift_tiles<float, float, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 0);
     else
-        update_p_h_tiles<HT, BC>(blockIdx.x - Gs, V, r, p, sc);
+        update_p_h_tiles<HT, BC>(blockIdx.x - Gs, V, r, p, sc, xlo);
 }
 
-// x_hi += x_lo ; x_lo = 0
+// x_hi += x_lo ; x_lo = 0 (x_hi in float-float: FP64 accuracy on the FP32 pipes)
 template <typename T, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_rel_accum(int V, double2 *__restrict__ xhi, typename cplx_t<T>::type *__restrict__ xlo, int G) {
+    k_rel_accum(int V, df64c *__restrict__ xhi, typename cplx_t<T>::type *__restrict__ xlo, int G) {
     typedef typename cplx_t<T>::type C;
     const int jj = threadIdx.x % BC, chunk = blockIdx.y;
     const size_t base = (size_t)chunk * 12 * V * BC + jj;
@@ -839,9 +847,9 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
         for (int c = 0; c < 12; ++c) {
             size_t o = base + ((size_t)s * 12 + c) * BC;
             C xl = xlo[o];
-            double2 xh = xhi[o];
-            xh.x += (double)xl.x;
-            xh.y += (double)xl.y;
+            df64c xh = xhi[o];
+            xh.x = xh.x + df64(xl.x);
+            xh.y = xh.y + df64(xl.y);
             xhi[o] = xh;
             xlo[o] = mkc<C>(0, 0);
         }
@@ -876,6 +884,51 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
             r[o] = mkc<C>(rv.x, rv.y);
             ar += rv.x * rv.x + rv.y * rv.y;
         }
+    }
+    double s1 = block_sum<BC>(ar, sm);
+    if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
+}
+
+// Residual replacement in float-float (FP64-accurate, on the FP32 pipes):
+// r_hi = b - (D_W^dag t + s0 x_hi) with t = D_W x_hi (both float-float fields);
+// r = T(r_hi); partial |r_hi|^2 (per-site sums of the high parts in FP32: the
+// norm only steers the recurrences and the convergence test).
+template <typename T, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<df64>::value)
+    k_rel_resid_df(Geom g, const df64c *__restrict__ U, const df64c *__restrict__ t, const df64c *__restrict__ xhi,
+                   Source src, typename cplx_t<T>::type *__restrict__ r, double s0, df64 kappa, double *part_r,
+                   int G) {
+    typedef typename cplx_t<T>::type C;
+    __shared__ double sm[TileMap<BC>::THREADS];
+    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
+    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+    const df64 sh(s0);
+    const int cls = src.b64 ? -1 : src.src_class[j], comp = src.b64 ? -1 : src.src_comp[j];
+    double ar = 0;
+    for (int tile = blockIdx.x * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
+        int s = tile * TileMap<BC>::SPB + threadIdx.x / BC;
+        if (s >= g.V) continue;
+        df64c acc[12][1];
+        wilson_hop_auto<df64, true, BC>(g, U, t + base, s, acc);
+        const bool in_class = cls >= 0 && src.colour[s] == cls;
+        float sr = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            size_t o = base + ((size_t)s * 12 + c) * BC;
+            const df64c tv = t[o], xv = xhi[o];
+            df64c bv;
+            if (src.b64) bv = df64c{df64(src.b64[o].x), df64(src.b64[o].y)}; // explicit source (rare)
+            else bv = df64c{df64((in_class && c == comp) ? 1.f : 0.f), df64(0.f)};
+            df64c rv;
+            rv.x = bv.x - (tv.x - kappa * acc[c][0].x + sh * xv.x);
+            rv.y = bv.y - (tv.y - kappa * acc[c][0].y + sh * xv.y);
+            if constexpr (std::is_same<T, float>::value) r[o] = make_float2(rv.x.hi + rv.x.lo, rv.y.hi + rv.y.lo);
+            else if constexpr (std::is_same<T, df64>::value) r[o] = rv;
+            else r[o] = mkc<C>(to_d(rv.x), to_d(rv.y));
+            sr += rv.x.hi * rv.x.hi + rv.y.hi * rv.y.hi;
+        }
+        ar += (double)sr;
     }
     double s1 = block_sum<BC>(ar, sm);
     if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
@@ -961,15 +1014,6 @@ __global__ void __launch_bounds__(SCAL_THREADS)
 }
 
 // ------------------------------------------------------------------ driver
-
-// columns per thread of the D_W kernels: two FP32 columns share one 16-byte
-// access and one link fetch
-#ifndef SMPQ_FP32_NR
-#define SMPQ_FP32_NR 1
-#endif
-template <typename T, int BC> struct NRSel {
-    static constexpr int value = (sizeof(T) == 4 && BC % SMPQ_FP32_NR == 0) ? SMPQ_FP32_NR : 1;
-};
 
 // elementwise float-float -> FP32 copy of a field (same tiled layout)
 __global__ void k_to_fp32(const df64c *__restrict__ in, float2 *__restrict__ out, size_t n) {
@@ -1119,29 +1163,37 @@ template <int BC> struct Solve {
     // HT (H16 or B16, T = float): p and t are half-format fields (components,
     // then norms) passed through the float2 pointers.
     template <typename T, typename TS, typename HT = void>
+    // xacc (nullable): the base solution accumulated by the p updates (FP64 for
+    // FP64 iterations, float-float for the mixed solve's first phase).
     int phase(typename cplx_t<T>::type *p, typename cplx_t<T>::type *t, typename cplx_t<T>::type *r,
-              typename cplx_t<T>::type *xlo, double2 *xhi, double2 *t64, typename cplx_t<TS>::type *ps, bool init,
-              bool rel, double theta2, int fixed, int max_iter) {
+              typename cplx_t<T>::type *xlo, df64c *xhi, df64c *t64, typename cplx_t<TS>::type *ps, bool init,
+              bool rel, double theta2, int fixed, int max_iter, typename XAcc<T>::type *xacc = nullptr,
+              bool replace_mid = true) {
         typedef typename cplx_t<T>::type C;
         constexpr bool half = !std::is_void<HT>::value;
-        constexpr int NR = NRSel<T, BC>::value;
-        const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
-        const int GN = (ntiles_n + TPB - 1) / TPB;
-        const dim3 grid(G, nchunk), gsup(Gs, nchunk), gridn(GN, nchunk);
-        const int TH = TileMap<BC>::THREADS, THN = TileMap<BC, NR>::THREADS;
+        const dim3 grid(G, nchunk), gsup(Gs, nchunk);
+        const int TH = TileMap<BC>::THREADS;
         const int sblocks = B;
+        const bool hi = sizeof(T) != sizeof(float); // FP64 or float-float iterations
+        // kernel shape of the D_W launches (the autotuner's choice): tiles per
+        // block, per phase, and for the FP32 kernels one or two columns per thread
+        const int tpb = std::max(1, hi ? spec.tpb_hi : spec.tpb_lo);
+        const bool two_cols = std::is_same<T, float>::value && !half && spec.nr == 2 && BC % 2 == 0;
+        auto blocks_for = [&](int spb) { return ((V + spb - 1) / spb + tpb - 1) / tpb; };
         // Half-storage iterations replace the residual at least every 10x drop:
         // their iterated residual drifts from the true one by about the format's
         // rounding times the condition number per iteration, so a 1000x drop
         // (the FP32 default) would outlast its meaning.
         const double delta = half ? std::max(ctx->opt.reliable_delta, 0.1) : ctx->opt.reliable_delta;
-        const double delta2 = rel ? delta * delta : 0.0;
+        // replace_mid = false: one replacement when every shift has converged
+        // (then only the base shift can re-activate, so the replacement never
+        // enters the shifted systems; the mixed solve's FP32 phase)
+        const double delta2 = rel && replace_mid ? delta * delta : 0.0;
         const Geom g = ctx->geom;
         const T kappa = (T)ctx->opt.kappa;
         const C *U = (const C *)Links<T>::get(ctx);
         const bool shifts = spec.n_sup > 0;
         const int per_iter = 3;
-        const bool hi = sizeof(T) != sizeof(float); // FP64 or float-float iterations
         if constexpr (half) {
             if (!rel || !xlo || !xhi || !t64)
                 return set_err(ctx, SMPQ_EINVAL, "internal: half-storage iterations need FP64 reliable updates");
@@ -1163,16 +1215,13 @@ template <int BC> struct Solve {
         // launch YP: Gy support blocks, then the lattice blocks of the p update
         const int Gy = shifts ? Gs : 0;
         const dim3 gridyp(Gy + G, nchunk);
-        // x += alpha p in FP64 for the true residual (the FP32 and half paths
-        // keep x_hi for their reliable updates instead)
-        double2 *xacc = rel ? nullptr : x64;
         // two columns per thread for even tiles (SMPQ_HALF_SOLVE_NR=1: one)
 #ifndef SMPQ_HALF_SOLVE_NR
 #define SMPQ_HALF_SOLVE_NR 2
 #endif
         constexpr bool h2cols = SMPQ_HALF_SOLVE_NR == 2 && BC % 2 == 0;
         typedef TileMap<BC, h2cols ? 2 : 1> TMH;
-        const int GH = h2cols ? ((V + TMH::SPB - 1) / TMH::SPB + TPB - 1) / TPB : G;
+        const int GH = blocks_for(TMH::SPB);
         const dim3 gridh(GH, nchunk);
         auto iteration_half = [&](int k) {
             if constexpr (half) {
@@ -1182,21 +1231,22 @@ template <int BC> struct Solve {
                 constexpr int THH = TMH::THREADS;
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
                 if constexpr (h2cols)
-                    k_apply_a_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH, f1);
+                    k_apply_a_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH, tpb, f1);
                 else
-                    k_apply_a_h<HT, BC><<<grid, TH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, G, f1);
+                    k_apply_a_h<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH, tpb, f1);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
                 // (half-storage solves always run with reliable updates)
                 if constexpr (h2cols)
-                    k_apply_b_h2<HT, BC, true><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo,
-                                                                      sc.alpha, sp.s0, (float)kappa, part2, GH, f2);
+                    k_apply_b_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, sc.alpha, sp.s0,
+                                                                (float)kappa, part2, GH, tpb, f2);
                 else
-                    k_apply_b_h<HT, BC, true><<<grid, TH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, (float2 *)xlo, sc.alpha,
-                                                                   sp.s0, (float)kappa, part2, G, f2);
+                    k_apply_b_h<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, sc.alpha, sp.s0,
+                                                               (float)kappa, part2, GH, tpb, f2);
                 if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
                 k_yp_h<HT, BC><<<gridyp, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class,
-                                                       (const float2 *)r, (float2 *)ps, y, sc, sp, Gy, hp);
+                                                       (const float2 *)r, (float2 *)ps, y, sc, sp, Gy, hp,
+                                                       (float2 *)xlo);
             }
         };
         auto iteration = [&](int k) {
@@ -1204,26 +1254,37 @@ template <int BC> struct Solve {
                 iteration_half(k);
                 return;
             }
-            if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-            k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(g, U, p, t, kappa, part0, part1, GN, f1);
-            if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-            if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
-            if (rel)
-                k_apply_b<T, BC, NR, true><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
-                                                                   GN, f2);
-            else
-                k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(g, U, t, p, r, xlo, sc.alpha, sp.s0, kappa, part2,
-                                                                    GN, f2);
-            if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+            // the D_W pair with NR columns per thread
+            auto apply_pair = [&](auto nr_c) {
+                constexpr int NR = decltype(nr_c)::value;
+                if constexpr (NR == 1 || (std::is_same<T, float>::value && BC % 2 == 0)) {
+                    typedef TileMap<BC, NR> TMN;
+                    const int GN = blocks_for(TMN::SPB);
+                    const dim3 gridn(GN, nchunk);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
+                    k_apply_a<T, BC, NR><<<gridn, TMN::THREADS, 0, st>>>(g, U, p, t, kappa, part0, part1, GN, tpb,
+                                                                          f1);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
+                    k_apply_b<T, BC, NR><<<gridn, TMN::THREADS, 0, st>>>(g, U, t, p, r, sc.alpha, sp.s0, kappa, part2,
+                                                                          GN, tpb, f2);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+                }
+            };
+            if (two_cols) apply_pair(std::integral_constant<int, 2>());
+            else apply_pair(std::integral_constant<int, 1>());
             k_yp<T, TS, BC><<<gridyp, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps, y,
-                                                   sc, sp, Gy, p, xacc);
+                                                   sc, sp, Gy, p, xacc, rel ? xlo : nullptr);
         };
+        // residual replacement: x_hi += x_lo, r = b - (A + s0) x_hi in float-float
         auto reliable = [&]() {
             ctx->launches += 4;
+            const df64 kdf(ctx->opt.kappa);
+            const df64c *Udf = (const df64c *)ctx->Udf.p;
+            Fuse none{};
             k_rel_accum<T, BC><<<grid, TH, 0, st>>>(V, xhi, xlo, G);
-            launch_dslash<double>(g, ctx->U64.p, xhi, t64, B, BC, 0, ctx->opt.kappa, st);
-            k_rel_resid<T, BC><<<grid, TH, 0, st>>>(g, (const double2 *)ctx->U64.p, t64, xhi, src, r, sp.s0,
-                                                     ctx->opt.kappa, part2, G);
+            k_apply_a<df64, BC, 1><<<grid, TH, 0, st>>>(g, Udf, xhi, t64, kdf, part0, part1, G, TPB, none);
+            k_rel_resid_df<T, BC><<<grid, TH, 0, st>>>(g, Udf, t64, xhi, src, r, sp.s0, kdf, part2, G);
             cudaMemsetAsync(sc.flags, 0, 2 * sizeof(int), st);
             s_rel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, base_shift);
         };
@@ -1364,37 +1425,47 @@ template <int BC> struct Solve {
             rc = S.template phase<double, double>((double2 *)ws[W_P].p, (double2 *)ws[W_T].p, (double2 *)ws[W_R].p,
                                                   nullptr, nullptr, nullptr,
                                                   shifts ? (double2 *)ws[W_PS].p : nullptr, true, false, 0.0, fixed,
-                                                  max_iter);
+                                                  max_iter, S.x64);
             if (rc) return rc;
             if (S.x64 && (rc = S.template true_residual<double>((double2 *)ws[W_T64].p, (double2 *)ws[W_R].p,
                                                                  S.true_rr)))
                 return rc;
         } else if (spec.prec == SMPQ_MIXED) {
-            // phase 1: float-float (FP64-accurate) vectors and D_W down to the switch residual
+            // phase 1: float-float (FP64-accurate) vectors and D_W down to the
+            // switch residual; the base solution x_hi accumulates in float-float
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(df64c)))) return rc;
             if ((rc = ensure(ctx, ws[W_T], nf * sizeof(df64c)))) return rc;
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(df64c)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(df64c)))) return rc;
             if (shifts) {
                 if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(double2)))) return rc;
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
-            if ((rc = S.alloc_x64())) return rc;
             double2 *ps = shifts ? (double2 *)ws[W_PS].p : nullptr;
             df64c *p = (df64c *)ws[W_P].p, *t = (df64c *)ws[W_T].p, *r = (df64c *)ws[W_R].p;
+            df64c *xh = (df64c *)ws[W_XHI].p;
             const double theta = ctx->opt.switch_residual;
-            rc = S.template phase<df64, double>(p, t, r, nullptr, nullptr, nullptr, ps, true, false, theta * theta, 0,
-                                                max_iter);
+            rc = S.template phase<df64, double>(p, t, r, nullptr, xh, nullptr, ps, true, false, theta * theta, 0,
+                                                max_iter, xh);
             if (rc) return rc;
-            // phase 2: FP32 vectors and D_W from the phase-1 state; the shifted
-            // directions in FP32 too (ps32_phase2), y stays FP64
+            // phase 2: FP32 vectors and D_W from the phase-1 state.  x_lo (FP32)
+            // accumulates the phase's part of the base solution; once every
+            // shift has converged the residual is replaced once (x_hi += x_lo,
+            // r = b - (A + s0) x_hi in float-float, the phase-1 t as scratch) and
+            // the base shift alone iterates on until its true residual is below
+            // tol.  A replacement during the phase would feed the FP32 drift of
+            // the base residual into every shifted system.  The shifted
+            // directions are FP32 too (ps32_phase2), y stays FP64.
             const size_t nps = shifts ? (size_t)sp.n * S.nsupf : 0;
             const bool ps32 = ps32_phase2 && shifts;
-            if ((rc = ensure(ctx, ws[W_XLO], 3 * nf * sizeof(float2) + (ps32 ? nps * sizeof(float2) : 0)))) return rc;
-            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf, *ps32p = r32 + nf;
+            if ((rc = ensure(ctx, ws[W_XLO], 4 * nf * sizeof(float2) + (ps32 ? nps * sizeof(float2) : 0)))) return rc;
+            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf, *xl32 = r32 + nf,
+                   *ps32p = xl32 + nf;
             const unsigned nb = (unsigned)((nf + 255) / 256);
             k_to_fp32<<<nb, 256, 0, S.st>>>(p, p32, nf);
             k_to_fp32<<<nb, 256, 0, S.st>>>(r, r32, nf);
+            cudaMemsetAsync(xl32, 0, nf * sizeof(float2), S.st);
             ctx->launches += 2;
             if (ps32) {
                 k_d2f<<<(unsigned)((nps + 255) / 256), 256, 0, S.st>>>(ps, ps32p, nps);
@@ -1402,16 +1473,16 @@ template <int BC> struct Solve {
             }
             cudaMemcpyAsync(S.hflags, S.sc.flags, sizeof(int), cudaMemcpyDeviceToHost, S.st);
             cudaStreamSynchronize(S.st);
+            if (S.hflags[0] > 0) S.relpath = true;
             if (S.hflags[0] > 0 && ps32) {
-                rc = S.template phase<float, float>(p32, t32, r32, nullptr, nullptr, nullptr, ps32p, false, false, 0.0,
-                                                    0, max_iter);
+                rc = S.template phase<float, float>(p32, t32, r32, xl32, xh, t, ps32p, false, true, 0.0, 0, max_iter,
+                                                    nullptr, false);
                 if (rc) return rc;
             } else if (S.hflags[0] > 0) {
-                rc = S.template phase<float, double>(p32, t32, r32, nullptr, nullptr, nullptr, ps, false, false, 0.0, 0,
-                                                     max_iter);
+                rc = S.template phase<float, double>(p32, t32, r32, xl32, xh, t, ps, false, true, 0.0, 0, max_iter,
+                                                     nullptr, false);
                 if (rc) return rc;
             }
-            if (S.x64 && (rc = S.template true_residual<float>((double2 *)ws[W_T64].p, r32, S.true_rr))) return rc;
         } else if (spec.prec == SMPQ_FP16N || spec.prec == SMPQ_BF16N) {
             // p and t in the half format, the rest as in the FP32 path
             const size_t hb = (half_field_bytes(S.V, S.B) + 255) / 256 * 256;
@@ -1428,7 +1499,7 @@ template <int BC> struct Solve {
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
             float2 *pp = (float2 *)ws[W_P].p, *tt = (float2 *)ws[W_T].p, *rr = (float2 *)ws[W_R].p;
             float2 *xl = (float2 *)ws[W_XLO].p, *ps = shifts ? (float2 *)ws[W_PS].p : nullptr;
-            double2 *xh = (double2 *)ws[W_XHI].p, *t64 = (double2 *)ws[W_T64].p;
+            df64c *xh = (df64c *)ws[W_XHI].p, *t64 = (df64c *)ws[W_T64].p;
             S.relpath = true;
             if (spec.prec == SMPQ_BF16N)
                 rc = S.template phase<float, float, B16>(pp, tt, rr, xl, xh, t64, ps, true, true, 0.0, fixed, max_iter);
@@ -1449,16 +1520,16 @@ template <int BC> struct Solve {
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
             S.relpath = true;
             rc = S.template phase<float, float>((float2 *)ws[W_P].p, (float2 *)ws[W_T].p, (float2 *)ws[W_R].p,
-                                                (float2 *)ws[W_XLO].p, (double2 *)ws[W_XHI].p,
-                                                (double2 *)ws[W_T64].p, shifts ? (float2 *)ws[W_PS].p : nullptr,
+                                                (float2 *)ws[W_XLO].p, (df64c *)ws[W_XHI].p,
+                                                (df64c *)ws[W_T64].p, shifts ? (float2 *)ws[W_PS].p : nullptr,
                                                 true, true, 0.0, fixed, max_iter);
             if (rc) return rc;
         }
         return S.finish(out, fixed, S.x64 ? S.true_rr : nullptr);
     }
 
-    // FP64 and mixed paths with the true_residual option: x64 (and t64 for
-    // the final check) on the whole lattice, x64 starting at 0
+    // FP64 path with the true_residual option: x64 (and t64 for the final
+    // check) on the whole lattice, x64 starting at 0
     int alloc_x64() {
         if (!ctx->opt.true_residual || spec.n_sup == 0) return SMPQ_OK;
         std::vector<Buf> &ws = ctx->ws;
@@ -1566,55 +1637,93 @@ int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi) {
 
 // ------------------------------------------------------------------ autotuner support
 // Average time (ms) of one t = D_W p plus one r -= alpha (D_W^dag t + s0 p)
-// launch in the iteration precision T, for B right-hand sides in tiles of BC,
-// on scratch fields (their values do not change the work).  reps launches each.
+// launch (the two D_W launches of an iteration, without their scalar steps)
+// for B right-hand sides in tiles of BC, tpb tiles per block and NR columns
+// per thread, on scratch fields (their values do not change the work).
+// reps launches each, after one untimed pair.
 namespace {
-template <typename T, int BC> float time_pair(smpq_ctx *ctx, int B, int reps, void *buf, double *part, double *alpha) {
+template <typename F> float time_launches(smpq_ctx *ctx, int reps, F once) {
+    cudaStream_t st = ctx->stream;
+    once(); // warm-up
+    cudaEventRecord(ctx->ev1, st);
+    for (int k = 0; k < reps; ++k) once();
+    cudaEventRecord(ctx->ev2, st);
+    if (cudaEventSynchronize(ctx->ev2) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2);
+    return ms / reps;
+}
+
+template <typename T, int BC, int NR>
+float time_pair(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part, double *alpha) {
     typedef typename cplx_t<T>::type C;
-    constexpr int NR = NRSel<T, BC>::value;
+    typedef TileMap<BC, NR> TM;
     const int V = ctx->V, nchunk = B / BC;
-    const int ntiles_n = (V + TileMap<BC, NR>::SPB - 1) / TileMap<BC, NR>::SPB;
-    const int GN = (ntiles_n + TPB - 1) / TPB;
+    const int GN = ((V + TM::SPB - 1) / TM::SPB + tpb - 1) / tpb;
     const size_t nf = (size_t)B * 12 * V;
     C *p = (C *)buf, *t = p + nf, *r = t + nf;
     const C *U = (const C *)Links<T>::get(ctx);
     const T kappa = (T)ctx->opt.kappa;
     cudaStream_t st = ctx->stream;
     const dim3 gridn(GN, nchunk);
-    const int THN = TileMap<BC, NR>::THREADS;
-    Fuse none{};
-    none.count = nullptr; // timing only: no scalar step
-    auto once = [&]() {
-        k_apply_a<T, BC, NR><<<gridn, THN, 0, st>>>(ctx->geom, U, p, t, kappa, part, part + (size_t)nchunk * GN * BC,
-                                                     GN, none);
-        k_apply_b<T, BC, NR, false><<<gridn, THN, 0, st>>>(ctx->geom, U, t, p, r, nullptr, alpha, 0.0, kappa, part,
-                                                            GN, none);
-    };
-    once(); // warm-up
-    cudaEventRecord(ctx->ev1, st);
-    for (int k = 0; k < reps; ++k) once();
-    cudaEventRecord(ctx->ev2, st);
-    cudaEventSynchronize(ctx->ev2);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2);
-    return ms / reps;
+    Fuse none{}; // timing only: no scalar step
+    return time_launches(ctx, reps, [&]() {
+        k_apply_a<T, BC, NR><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, U, p, t, kappa, part,
+                                                             part + (size_t)nchunk * GN * BC, GN, tpb, none);
+        k_apply_b<T, BC, NR><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, U, t, p, r, alpha, 0.0, kappa, part, GN, tpb,
+                                                             none);
+    });
 }
 
-template <typename T> float time_pair_bc(smpq_ctx *ctx, int B, int BC, int reps, void *buf, double *part, double *alpha) {
-    switch (BC) {
-    case 12: return time_pair<T, 12>(ctx, B, reps, buf, part, alpha);
-    case 24: return time_pair<T, 24>(ctx, B, reps, buf, part, alpha);
-    case 48: return time_pair<T, 48>(ctx, B, reps, buf, part, alpha);
+// the half-storage pair (two columns per thread, r and x_lo in FP32)
+template <typename HT, int BC>
+float time_pair_half(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part, double *alpha) {
+    typedef TileMap<BC, 2> TM;
+    const int V = ctx->V, nchunk = B / BC;
+    const int GN = ((V + TM::SPB - 1) / TM::SPB + tpb - 1) / tpb;
+    const size_t nf = (size_t)B * 12 * V;
+    const size_t hb = (half_field_bytes(V, B) + 255) / 256 * 256;
+    typename HT::h2 *pv = (typename HT::h2 *)buf, *tv = (typename HT::h2 *)((char *)buf + hb);
+    const HF<HT> hp{pv, (float *)(pv + nf)}, ht{tv, (float *)(tv + nf)};
+    float2 *r = (float2 *)((char *)buf + 2 * hb);
+    const typename HT::h2 *Uh = (const typename HT::h2 *)HLinks<HT>::get(ctx);
+    const float kappa = (float)ctx->opt.kappa;
+    cudaStream_t st = ctx->stream;
+    const dim3 gridn(GN, nchunk);
+    Fuse none{};
+    return time_launches(ctx, reps, [&]() {
+        k_apply_a_h2<HT, BC><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, Uh, hp, ht, kappa, part,
+                                                             part + (size_t)nchunk * GN * BC, GN, tpb, none);
+        k_apply_b_h2<HT, BC><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, Uh, ht, hp, r, alpha, 0.0, kappa, part, GN,
+                                                             tpb, none);
+    });
+}
+
+template <int BC> float time_kind(smpq_ctx *ctx, int kind, int B, int tpb, int nr, int reps, void *buf, double *part,
+                                  double *alpha) {
+    switch (kind) {
+    case 0: return time_pair<double, BC, 1>(ctx, B, tpb, reps, buf, part, alpha);
+    case 1:
+        return nr == 2 ? time_pair<float, BC, 2>(ctx, B, tpb, reps, buf, part, alpha)
+                       : time_pair<float, BC, 1>(ctx, B, tpb, reps, buf, part, alpha);
+    case 2: return time_pair<df64, BC, 1>(ctx, B, tpb, reps, buf, part, alpha);
+    case 3: return time_pair_half<H16, BC>(ctx, B, tpb, reps, buf, part, alpha);
+    case 4: return time_pair_half<B16, BC>(ctx, B, tpb, reps, buf, part, alpha);
     default: return -1.f;
     }
 }
 } // namespace
 
-float time_dslash_pair(smpq_ctx *ctx, int prec, int B, int BC, int reps, void *buf, double *part, double *alpha) {
-    if (prec == SMPQ_FP64) return time_pair_bc<double>(ctx, B, BC, reps, buf, part, alpha);
-    float t32 = time_pair_bc<float>(ctx, B, BC, reps, buf, part, alpha);
-    if (prec == SMPQ_FP32) return t32;
-    // SMPQ_MIXED: a fifth of the iterations (switch residual 1e-2) in float-float, the rest in FP32
-    float tdf = time_pair_bc<df64>(ctx, B, BC, reps, buf, part, alpha);
-    return 0.25f * tdf + 0.75f * t32;
+float time_dslash_pair(smpq_ctx *ctx, int kind, int B, int BC, int tpb, int nr, int reps, void *buf, double *part,
+                       double *alpha) {
+    if (tpb < 1 || B % BC) return -1.f;
+    switch (BC) {
+    case 12: return time_kind<12>(ctx, kind, B, tpb, nr, reps, buf, part, alpha);
+    case 24: return time_kind<24>(ctx, kind, B, tpb, nr, reps, buf, part, alpha);
+    case 48: return time_kind<48>(ctx, kind, B, tpb, nr, reps, buf, part, alpha);
+    default: return -1.f;
+    }
 }

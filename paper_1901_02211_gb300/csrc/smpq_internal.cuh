@@ -58,8 +58,16 @@ struct smpq_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evA = nullptr, evB = nullptr;
     // launch accounting and optional per-launch timing of the solver's D_W kernels
     long long launches = 0;
-    // autotuned RHS tile width per (V, B, precision)
-    std::vector<std::array<int, 4>> tuned; // {V, B, prec, BC}
+    // autotuned D_W launch shape per (lattice, B, precision): {BC, tiles per
+    // block FP64-accurate / FP32, columns per thread}; from_file: read from the cache
+    struct Tuned {
+        std::array<int, 4> dims;
+        int B, prec;
+        std::array<int, 4> shape;
+        int from_file;
+    };
+    std::vector<Tuned> tuned;
+    std::string tune_cache; // path of the tuning cache file ("" = none)
     int last_bc = 0;
     std::vector<cudaEvent_t> prof_ev; // 4 per iteration of one check interval
     double prof_a_ms = 0, prof_b_ms = 0;         // FP32 iterations
@@ -134,6 +142,10 @@ struct SolveSpec {
     const int *d_src_comp;     // [B] source component (spin*3 + colour) of rhs j
     const double *d_src_field; // optional explicit FP64 source in the solver's tiled layout
     const ShiftParams *shifts; // nullable: shifts and coefficients other than the context's rational
+    // shape of the D_W launches (the autotuner's choice; 0: 4, 4, 1): tiles per
+    // block in the FP64-accurate and in the FP32 / half iterations, columns
+    // per thread of the FP32 kernels (1 or 2)
+    int tpb_hi, tpb_lo, nr;
 };
 struct SolveOut {
     // y = R(H^2) b on the support, FP64, layout [j/BC][n_sup][12][BC] (the field
@@ -167,9 +179,14 @@ void lowmodes_qterm(smpq_ctx *ctx, const int *d_classes, int nc, double2 *qterm,
 int lowmodes_dov_project(smpq_ctx *ctx, const double2 *b, double2 *bperp, int B, std::vector<double> &wd,
                          cudaStream_t st);
 int lowmodes_dov_finish(smpq_ctx *ctx, double2 *out, int B, const std::vector<double> &wd, cudaStream_t st);
-// autotuner: average ms of one D_W + D_W^dag-update launch pair (scratch fields in buf:
-// 3 fields of B x 12 x V complex of the widest type used, part: partials, alpha: B doubles)
-float time_dslash_pair(smpq_ctx *ctx, int prec, int B, int BC, int reps, void *buf, double *part, double *alpha);
+// autotuner: average ms of one D_W + D_W^dag-update launch pair of the
+// iterations of `kind` (0 FP64, 1 FP32, 2 float-float, 3 FP16 + norms,
+// 4 BF16 + norms) for B columns in tiles of BC, tpb tiles per block and nr
+// columns per thread (FP32: 1 or 2).  Scratch in buf: 3 fields of B x 12 x V
+// float-float complex; part: 2 * B * V / 12 doubles of partials; alpha: B
+// doubles.  -1 on a bad shape or a CUDA error.
+float time_dslash_pair(smpq_ctx *ctx, int kind, int B, int BC, int tpb, int nr, int reps, void *buf, double *part,
+                       double *alpha);
 
 // probing.cu : sources, star support, contraction, Q
 int build_star_support(smpq_ctx *ctx, Buf &supsite, int *n_sup);

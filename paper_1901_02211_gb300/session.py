@@ -15,6 +15,8 @@ class Session:
         for k, v in options.items():
             if k == "bc":
                 o.bc[:] = list(v)
+            elif k == "tune_cache":
+                o.tune_cache = None if v is None else str(v).encode()
             else:
                 setattr(o, k, v)
         self.options = o
@@ -42,6 +44,8 @@ class Session:
         for k, v in options.items():
             if k == "bc":
                 self.options.bc[:] = list(v)
+            elif k == "tune_cache":
+                self.options.tune_cache = None if v is None else str(v).encode()
             else:
                 setattr(self.options, k, v)
         S.smpq_set_options(self.ctx, self.options)

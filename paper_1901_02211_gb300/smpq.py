@@ -56,6 +56,7 @@ class smpq_options(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("full_support", ctypes.c_int),
         ("true_residual", ctypes.c_int),
+        ("tune_cache", ctypes.c_char_p),
     ]
 
 
@@ -84,6 +85,10 @@ class smpq_stats(ctypes.Structure):
         ("rhs_tile", ctypes.c_int),
         ("q_round_dev", ctypes.c_double),
         ("true_resid", ctypes.c_double),
+        ("tiles_per_block_hi", ctypes.c_int),
+        ("tiles_per_block_lo", ctypes.c_int),
+        ("cols_per_thread", ctypes.c_int),
+        ("shape_from_cache", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -96,7 +101,7 @@ EXPORTS = [
     "smpq_build_sources", "smpq_colour_sites", "smpq_dslash", "smpq_apply_dov", "smpq_compute_qx",
     "smpq_compute_qx_classes", "smpq_dslash_noalloc", "smpq_trace_dwinv", "smpq_compute_qx_batch",
     "smpq_low_modes", "smpq_get_low_modes", "smpq_clear_low_modes", "smpq_time_dslash", "smpq_context_info",
-    "smpq_alu_peak",
+    "smpq_alu_peak", "smpq_tune_cache_lookup", "smpq_tune_cache_store",
 ]
 
 _lib = None
@@ -143,6 +148,8 @@ def load(build_if_missing=True):
         "smpq_clear_low_modes": [P],
         "smpq_context_info": [P, PI, PI],
         "smpq_alu_peak": [I, I, PD],
+        "smpq_tune_cache_lookup": [ctypes.c_char_p, ctypes.c_char_p, PI, I, I, PI],
+        "smpq_tune_cache_store": [ctypes.c_char_p, ctypes.c_char_p, PI, I, I, PI, D],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -190,6 +197,23 @@ def smpq_alu_peak(device=0, kind=ALU_FP32X2):
     v = ctypes.c_double()
     _check(load().smpq_alu_peak(device, kind, ctypes.byref(v)))
     return v.value
+
+
+def smpq_tune_cache_lookup(path, device, dims, B, precision):
+    """The cached launch shape (bc, tpb_hi, tpb_lo, nr) or None."""
+    d = (ctypes.c_int * 4)(*dims)
+    sh = (ctypes.c_int * 4)()
+    rc = load().smpq_tune_cache_lookup(os.fsencode(path), device.encode(), d, B, precision, sh)
+    if rc == SMPQ_ESTATE:
+        return None
+    _check(rc)
+    return tuple(sh)
+
+
+def smpq_tune_cache_store(path, device, dims, B, precision, shape, ms):
+    d = (ctypes.c_int * 4)(*dims)
+    sh = (ctypes.c_int * 4)(*shape)
+    _check(load().smpq_tune_cache_store(os.fsencode(path), device.encode(), d, B, precision, sh, ms))
 
 
 def _check_buf(ctx, a, count, kind, what):

@@ -94,7 +94,7 @@ def _struct_members(name):
     for decl in body.split(";"):
         decl = decl.strip()
         if decl:
-            out.extend(re.sub(r"\[.*?\]", "", v).split()[-1] for v in decl.split(","))
+            out.extend(re.sub(r"\[.*?\]", "", v).split()[-1].lstrip("*") for v in decl.split(","))
     return out
 
 
@@ -125,3 +125,27 @@ def test_buffer_checks_refuse_before_any_launch(monkeypatch):
     monkeypatch.setattr(S, "smpq_context_info", lambda ctx: ((0, 0, 0, 0), 0))
     with pytest.raises(S.SmpqError):
         S._volume(None)
+
+
+def test_tune_cache_round_trip(tmp_path):
+    """The autotuner's cache file: a stored shape is found again for the same
+    key only, the last matching line wins, malformed lines are skipped and a
+    missing file reads as 'not found' (host code, no GPU)."""
+    path = str(tmp_path / "tune.txt")
+    dev, dims = "NVIDIA GB300/152sm", (8, 8, 8, 16)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) is None
+    S.smpq_tune_cache_store(path, dev, dims, 3072, S.SMPQ_MIXED, (48, 4, 2, 1), 7.5)
+    S.smpq_tune_cache_store(path, dev, dims, 1536, S.SMPQ_MIXED, (24, 1, 8, 2), 3.0)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (48, 4, 2, 1)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 1536, S.SMPQ_MIXED) == (24, 1, 8, 2)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_FP32) is None
+    assert S.smpq_tune_cache_lookup(path, dev, (8, 8, 16, 8), 3072, S.SMPQ_MIXED) is None
+    assert S.smpq_tune_cache_lookup(path, "other/1sm", dims, 3072, S.SMPQ_MIXED) is None
+    with open(path, "a") as f:
+        f.write("smpq-tune-1|NVIDIA GB300/152sm|8 8 8 16|3072|2|7 4 4 1|1.0\n")  # tile 7: rejected
+        f.write("garbage line\n")
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (48, 4, 2, 1)
+    S.smpq_tune_cache_store(path, dev, dims, 3072, S.SMPQ_MIXED, (12, 8, 8, 2), 6.0)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (12, 8, 8, 2)
+    with pytest.raises(S.SmpqError):
+        S.smpq_tune_cache_store(path, "bad|name", dims, 3072, S.SMPQ_MIXED, (48, 4, 4, 1), 1.0)
