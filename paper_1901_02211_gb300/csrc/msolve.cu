@@ -1080,7 +1080,9 @@ template <int BC> struct Solve {
         nfield = (size_t)B * 12 * V;
         nsupf = (size_t)B * 12 * spec.n_sup;
         // the NR-column kernels have at most as many blocks per tile as the 1-column ones
-        npart = (size_t)nchunk * std::max(G, Gs) * BC;
+        // partial rows per tile: the most blocks any launch has per tile (the
+        // D_W launches at one tile per block have ntiles; the support kernels Gs)
+        npart = (size_t)nchunk * std::max(ntiles, Gs) * BC;
         std::vector<Buf> &ws = ctx->ws;
         if (ws.size() < W_COUNT) ws.resize(W_COUNT);
         int rc;
@@ -1180,6 +1182,9 @@ template <int BC> struct Solve {
         const int tpb = std::max(1, hi ? spec.tpb_hi : spec.tpb_lo);
         const bool two_cols = std::is_same<T, float>::value && !half && spec.nr == 2 && BC % 2 == 0;
         auto blocks_for = [&](int spb) { return ((V + spb - 1) / spb + tpb - 1) / tpb; };
+        // every launch's partial rows must fit the partial buffers (npart per buffer)
+        if ((size_t)blocks_for(TileMap<BC, 1>::SPB) * nchunk * BC > npart || (size_t)G * nchunk * BC > npart)
+            return set_err(ctx, SMPQ_EINVAL, "internal: launch shape exceeds the partial-sum buffers");
         // Half-storage iterations replace the residual at least every 10x drop:
         // their iterated residual drifts from the true one by about the format's
         // rounding times the condition number per iteration, so a 1000x drop
