@@ -399,8 +399,9 @@ def run_gpu(args):
     else:
         e2e_val = _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws)
     out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream) if rank == 0 else {}
-    if rank == 0 and args.uneven:
-        out["uneven_batch"] = _uneven(args, prec, dev, stream)
+    if rank == 0 and not args.no_extra:
+        out["uneven_batch"] = {"bf16n": _uneven(args, smpq.SMPQ_BF16N, dev, stream),
+                               "mixed": _uneven(args, smpq.SMPQ_MIXED, dev, stream)}
     if rank == 0 and not args.no_extra:
         out["c3_16x32"] = _c3_record(args, dev, stream)
         out["c5_32x64"] = _c5_record(args, dev, stream)
@@ -579,20 +580,20 @@ def _c5_record(args, dev, stream):
 
 def _uneven(args, prec, dev, stream):
     """The uneven batch: three lattices of different size and scheme (8^3x16 r = 2
-    Q = 1, 12^3x24 r = 4 Q = 2, 16^3x32 r = 4 Q = 3), one context each, issued
-    together through smpq_compute_qx_batch; sites of all three per second."""
+    Q = 1, 12^3x24 r = 4 Q = 2, 16^3x32 r = 4 Q = 3), one context each, in one
+    smpq_compute_qx_batch call: every CG iteration is the same three launches
+    for all three lattices.  Sites of all three per second."""
     import torch
 
     from paper_1901_02211_gb300 import Session, smpq
     from synth import make_config
-    # fixed batch sizes, so the three concurrent solves share device memory
-    # (the automatic size would give each one 60 % of what is free)
-    lattices = (("flux8x16_b", 2, 192), ("flux12x24", 4, 1536), ("flux16x32_b", 4, 768))
+    lattices = (("flux8x16_b", 2), ("flux12x24", 4), ("flux16x32_b", 4))
     sessions, re_, im_, sites, names = [], [], [], 0, []
-    for name, r, blk in lattices:
+    t0 = time.perf_counter()
+    for name, r in lattices:
         cfg = make_config(name)
-        s4 = Session(device=dev, stream=stream, precision=prec, tol=1e-10, rhs_block=blk, iters_per_check=10,
-                     use_graphs=1, switch_residual=args.switch, autotune=0)
+        s4 = Session(device=dev, stream=stream, precision=prec, tol=1e-10, iters_per_check=10, use_graphs=1,
+                     switch_residual=args.switch)
         s4.load_gauge(cfg["dims"], cfg["U"])
         s4.measure_spectrum(300)
         s4.build_sources(r, MODE)
@@ -602,6 +603,7 @@ def _uneven(args, prec, dev, stream):
         im_.append(torch.zeros(V, dtype=torch.float64, device="cuda"))
         sites += V
         names.append("%s r=%d (V=%d, Q=%d)" % (name, r, V, cfg["Q_closed"]))
+    setup = time.perf_counter() - t0
     ctxs = [s4.ctx for s4 in sessions]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -610,9 +612,12 @@ def _uneven(args, prec, dev, stream):
     dt = time.perf_counter() - t0
     for s4 in sessions:
         s4.close()
-    return {"value": sites / dt, "unit": "sites/s", "seconds": dt, "lattices": names, "Q": Qs,
-            "rhs": [x["n_rhs"] for x in st], "iterations": [x["max_iterations"] for x in st],
-            "note": "fixed batches 192 / 1536 / 768, RHS tile 48; GPU Lanczos intervals"}
+    return {"value": sites / dt, "unit": "sites/s", "seconds": dt, "setup_s": setup, "lattices": names, "Q": Qs,
+            "abs_Q_minus_round": [x["q_round_dev"] for x in st], "rhs": [x["n_rhs"] for x in st],
+            "rounds": st[0]["n_batches"], "rhs_tile": st[0]["rhs_tile"],
+            "iterations": [x["max_iterations"] for x in st], "true_resid_base": [x["true_resid"] for x in st],
+            "launch": "one solve for the three lattices: each CG iteration is 3 kernel launches covering all of "
+                      "them; sources in rounds sized to device memory; GPU Lanczos intervals (setup)"}
 
 
 def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
@@ -785,11 +790,10 @@ def main():
     ap.add_argument("--classes", type=int, default=0, help="profiling: only the first N colour classes")
     ap.add_argument("--low-modes", type=int, default=20,
                     help="also time the variant with this many low modes of H_W exact (0: skip)")
-    ap.add_argument("--uneven", action="store_true",
-                    help="also time the uneven batch of three lattices (8^3x16, 12^3x24, 16^3x32) in one call")
+
     ap.add_argument("--lanczos", type=int, default=300, help="Lanczos steps of the spectrum setup")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the one-step records of the 16^3x32 and 32^3x64 configurations")
+                    help="skip the records of the 16^3x32 and 32^3x64 configurations and of the uneven batch")
     ap.add_argument("--c5-max-iter", type=int, default=12000, help="iteration cap of the 32^3x64 record")
     ap.add_argument("--no-autotune", action="store_true",
                     help="widest RHS tile that divides the batch, without timing the candidates")

@@ -281,11 +281,17 @@ int smpq_compute_qx_classes(smpq_ctx *ctx, const int *classes, int n, double *q_
                             smpq_stats *stats);
 
 /* Uneven batch: q^SMP(x) for n lattices of different sizes and schemes, one
- * context each (distinct contexts, each with its gauge field, spectrum and
- * colouring loaded).  The n solves are issued concurrently from n host
- * threads on the contexts' own streams, so their kernels overlap on the GPU.
+ * context each (distinct contexts on one device, each with its gauge field,
+ * spectrum and colouring loaded; one precision and pole count for all; no
+ * low-mode projection, full_support or rhs_block = 1).  Up to four lattices
+ * share one solve: every CG iteration is the same three kernel launches for
+ * all of them (each RHS tile carries its lattice's geometry, links and
+ * rational), issued on the first context's stream, whose workspace holds the
+ * fields.  Their sources run in rounds sized to the device memory, each round
+ * taking about the same share of every lattice's sources.  Larger n runs in
+ * groups of four.  The default launch shape is used (no autotuning).
  * q_re[i], q_im[i]: double[V_i]; Q and stats (nullable): arrays of n.
- * Returns the first non-OK status (its message is on that context). */
+ * Returns the first non-OK status (its message is on the first context). */
 int smpq_compute_qx_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_device, double *Q,
                           smpq_stats *stats);
 

@@ -5,7 +5,6 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "smpq_internal.cuh"
@@ -147,6 +146,7 @@ void set_geom(smpq_ctx *ctx) {
 struct Shape {
     int bc, tpb_hi, tpb_lo, nr;
 };
+constexpr int TPB_DEFAULT = 4; // tiles per block of the lattice kernels (msolve.cu)
 
 std::string device_key(int dev) {
     cudaDeviceProp pr;
@@ -169,7 +169,7 @@ int tune_kind_lo(int prec) {
 
 Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
     *cached = 0;
-    Shape def{1, 4, 4, 1};
+    Shape def{1, TPB_DEFAULT, TPB_DEFAULT, 1};
     if (B == 1) return def;
     std::vector<int> cand;
     for (int bc : {12, 24, 48})
@@ -492,6 +492,184 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     }
     ctx->last_Q = tot[0];
     return SMPQ_OK;
+}
+
+// The uneven batch: q^SMP(x) on n lattices of different sizes (1 <= n <= 4,
+// one context each), their right-hand sides solved together: every CG
+// iteration is the same three launches for all lattices (each RHS tile knows
+// its lattice's geometry, links and rational).  The sources run in rounds;
+// each round takes about the same share of every lattice's sources, so all
+// rounds mix the lattices, and the rounds fit the device memory the first
+// context can use.
+int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_device, double *Q, smpq_stats *stats) {
+    smpq_ctx *c0 = ctxs[0];
+    cudaStream_t st = c0->stream;
+    const int prec = c0->opt.precision;
+    int rc;
+    for (int l = 0; l < n; ++l) {
+        smpq_ctx *c = ctxs[l];
+        if ((rc = check_ctx(c, true, true, true))) return rc;
+        if (c->device != c0->device || c->opt.precision != prec || c->opt.npoles != c0->opt.npoles)
+            return set_err(c0, SMPQ_EINVAL, "uneven batch: every context needs the same device, precision and poles");
+        if (c->lm_k > 0 || c->opt.full_support || c->opt.rhs_block == 1)
+            return set_err(c0, SMPQ_EINVAL, "uneven batch: no low-mode projection, full support or one-rhs batches");
+        if (on_device && ((rc = check_device_ptr(c0, q_re[l], "q_re")) || (rc = check_device_ptr(c0, q_im[l], "q_im"))))
+            return rc;
+        c->launches = 0;
+        c->prof_a_ms = c->prof_b_ms = c->prof_a_hi_ms = c->prof_b_hi_ms = 0;
+        c->prof_a_n = c->prof_b_n = c->prof_a_hi_n = c->prof_b_hi_n = 0;
+    }
+    cudaEventRecord(c0->evA, st);
+    // every lattice's star support, qterm and class list
+    std::vector<int> nsup(n), N(n);
+    size_t need = 0, held = 0;
+    for (int l = 0; l < n; ++l) {
+        smpq_ctx *c = ctxs[l];
+        if ((rc = build_star_support(c, c->ws[W_SUP], &nsup[l]))) return rc;
+        if ((rc = ensure(c, c->ws[W_QTERM], (size_t)c->n_classes * 12 * c->members * sizeof(double2)))) return rc;
+        N[l] = 12 * c->n_classes;
+        need += (size_t)N[l] * bytes_per_rhs(c, prec, nsup[l], c->opt.npoles);
+    }
+    for (const Buf &b : c0->ws) held += b.bytes;
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const double budget = 0.6 * (double)(freeb + held);
+    int rounds = std::max(1, (int)std::ceil((double)need / budget));
+    // per-round batch of each lattice: its share, a multiple of the tile width
+    int BC = 48;
+    std::vector<int> Bl(n);
+    for (int l = 0; l < n; ++l)
+        if ((N[l] + rounds - 1) / rounds < 48) BC = 12;
+    for (int l = 0; l < n; ++l) Bl[l] = ((N[l] + rounds - 1) / rounds + BC - 1) / BC * BC;
+    rounds = 0;
+    for (int l = 0; l < n; ++l) rounds = std::max(rounds, (N[l] + Bl[l] - 1) / Bl[l]);
+    int Btot = 0;
+    for (int l = 0; l < n; ++l) Btot += Bl[l];
+    // launch shape: the default tiles per block, one column per thread (timing
+    // candidates would need scratch the size of the round again)
+    const int from_cache = 0;
+    const Shape shape{BC, TPB_DEFAULT, TPB_DEFAULT, 1};
+    // global per-rhs tables (support class, source component, source class) in the first context
+    if ((rc = ensure(c0, c0->ws[W_RHS], (size_t)3 * Btot * sizeof(int)))) return rc;
+    int *d_rhs_class = (int *)c0->ws[W_RHS].p, *d_src_comp = d_rhs_class + Btot, *d_src_class = d_src_comp + Btot;
+    std::vector<int> h_rhs(3 * (size_t)Btot);
+    std::vector<SolveSpec> specs(n);
+    std::vector<SolveOut> outs(n);
+    std::vector<int> maxit(n, 0), nb(n, 0);
+    std::vector<long long> totit(n, 0);
+    std::vector<double> worst(n, 0), truer(n, -1), solve_ms(n, 0);
+    int nrel = 0;
+    for (int r = 0; r < rounds; ++r) {
+        int j0 = 0;
+        for (int l = 0; l < n; ++l) {
+            smpq_ctx *c = ctxs[l];
+            for (int j = 0; j < Bl[l]; ++j) { // rhs r * Bl + j of lattice l: class (r Bl + j) / 12, component % 12
+                const int g = r * Bl[l] + j;
+                const int cl = g < N[l] ? g / 12 : -1;
+                h_rhs[j0 + j] = cl;
+                h_rhs[Btot + j0 + j] = g % 12;
+                h_rhs[2 * Btot + j0 + j] = cl;
+            }
+            SolveSpec &sp = specs[l];
+            sp = SolveSpec{};
+            sp.B = Bl[l];
+            sp.BC = BC;
+            sp.prec = prec;
+            sp.n_sup = nsup[l];
+            sp.d_supsite = (const int *)c->ws[W_SUP].p;
+            sp.d_rhs_class = d_rhs_class;
+            sp.d_colour = (const int *)c->d_colour.p;
+            sp.d_src_class = d_src_class;
+            sp.d_src_comp = d_src_comp;
+            sp.tpb_hi = shape.tpb_hi;
+            sp.tpb_lo = shape.tpb_lo;
+            sp.nr = 1;
+            j0 += Bl[l];
+        }
+        cudaMemcpyAsync(d_rhs_class, h_rhs.data(), h_rhs.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+        if ((rc = multishift_solve_batch(ctxs, specs.data(), outs.data(), n))) {
+            for (int l = 1; l < n; ++l) ctxs[l]->err = c0->err;
+            return rc;
+        }
+        j0 = 0;
+        for (int l = 0; l < n; ++l) {
+            smpq_ctx *c = ctxs[l];
+            const int *rc_l = d_rhs_class + j0, *comp_l = d_src_comp + j0;
+            launch_add_c0b(nsup[l], Bl[l], BC, (const int *)c->ws[W_SUP].p, rc_l, comp_l, (const int *)c->d_colour.p,
+                           c->c0, outs[l].y, st);
+            launch_contract(c->geom, (const double *)c->U64.p, outs[l].y, nsup[l], Bl[l], BC, rc_l, comp_l,
+                            (const int *)c->d_members.p, c->members, c->opt.kappa, (double2 *)c->ws[W_QTERM].p, st);
+            c->launches += 2;
+            maxit[l] = std::max(maxit[l], outs[l].iterations);
+            totit[l] += outs[l].iterations;
+            worst[l] = std::max(worst[l], outs[l].max_resid);
+            if (outs[l].true_resid >= 0) truer[l] = std::max(truer[l], outs[l].true_resid);
+            solve_ms[l] += outs[l].solve_ms;
+            ++nb[l];
+            j0 += Bl[l];
+        }
+        nrel += outs[0].reliable_updates;
+    }
+    // every lattice's q(x) and Q (all classes)
+    for (int l = 0; l < n; ++l) {
+        smpq_ctx *c = ctxs[l];
+        if ((rc = ensure(c, c->ws[W_RHS], (size_t)c->n_classes * sizeof(int) + 4 * sizeof(double)))) return rc;
+        int *d_classes = (int *)c->ws[W_RHS].p;
+        double *d_tot = (double *)(((uintptr_t)(d_classes + c->n_classes) + 15) & ~(uintptr_t)15);
+        std::vector<int> cls(c->n_classes);
+        for (int k = 0; k < c->n_classes; ++k) cls[k] = k;
+        cudaMemcpyAsync(d_classes, cls.data(), cls.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+        double *dq_re = q_re[l], *dq_im = q_im[l];
+        if (!on_device) {
+            if ((rc = ensure(c, c->ws[W_Q], 2 * (size_t)c->V * sizeof(double)))) return rc;
+            dq_re = (double *)c->ws[W_Q].p;
+            dq_im = dq_re + c->V;
+        }
+        launch_qsum((const double2 *)c->ws[W_QTERM].p, d_classes, c->n_classes, (const int *)c->d_members.p,
+                    c->members, dq_re, dq_im, 0.5, st);
+        launch_qtotal(dq_re, dq_im, nullptr, c->V, d_tot, st);
+        c->launches += 2;
+        double tot[2];
+        cudaMemcpyAsync(tot, d_tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (!on_device) {
+            cudaMemcpyAsync(q_re[l], dq_re, c->V * sizeof(double), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(q_im[l], dq_im, c->V * sizeof(double), cudaMemcpyDeviceToHost, st);
+        }
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_check(c0, e, "uneven batch");
+        c->last_Q = tot[0];
+        if (Q) Q[l] = tot[0];
+        if (stats) {
+            smpq_stats &sx = stats[l];
+            std::memset(&sx, 0, sizeof(sx));
+            sx.n_rhs = N[l];
+            sx.n_classes = c->n_classes;
+            sx.n_batches = nb[l];
+            sx.max_iterations = maxit[l];
+            sx.total_iterations = totit[l];
+            sx.reliable_updates = nrel;
+            sx.max_resid = worst[l];
+            sx.max_im_q = tot[1];
+            sx.Q = tot[0];
+            sx.q_round_dev = std::fabs(tot[0] - std::nearbyint(tot[0]));
+            sx.solve_ms = solve_ms[l];
+            sx.kernel_launches = c->launches; // (the shared solve's launches are on the first context)
+            sx.rhs_tile = BC;
+            sx.true_resid = truer[l];
+            sx.tiles_per_block_hi = shape.tpb_hi;
+            sx.tiles_per_block_lo = shape.tpb_lo;
+            sx.cols_per_thread = 1;
+            sx.shape_from_cache = from_cache;
+        }
+    }
+    cudaEventRecord(c0->evB, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(c0, e, "uneven batch");
+    float tms = 0;
+    cudaEventElapsedTime(&tms, c0->evA, c0->evB);
+    if (stats)
+        for (int l = 0; l < n; ++l) stats[l].total_ms = tms;
+    return cuda_check(c0, cudaGetLastError(), "uneven batch launch");
 }
 
 } // namespace
@@ -998,17 +1176,20 @@ int smpq_compute_qx_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, 
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return set_err(ctxs[i], SMPQ_EINVAL, "a context appears twice in the batch");
     }
-    std::vector<int> rc(n, SMPQ_OK);
-    std::vector<std::thread> th;
-    th.reserve(n);
-    for (int i = 0; i < n; ++i)
-        th.emplace_back([&, i]() {
-            rc[i] = smpq_compute_qx(ctxs[i], q_re[i], q_im[i], on_device, Q ? &Q[i] : nullptr,
-                                    stats ? &stats[i] : nullptr);
-        });
-    for (auto &t : th) t.join();
-    for (int i = 0; i < n; ++i)
-        if (rc[i]) return rc[i];
+    // groups of at most 4 lattices share the launches of one solve
+    for (int g0 = 0; g0 < n; g0 += 4) {
+        const int m = std::min(4, n - g0);
+        DeviceGuard dg(ctxs[g0]->device);
+        for (int l = g0; l < g0 + m; ++l) StreamEntry se(ctxs[l], ctxs[l]->user_stream);
+        // the other contexts' queued work precedes the group's solve on the first one's stream
+        for (int l = g0 + 1; l < g0 + m; ++l) {
+            cudaEventRecord(ctxs[l]->ev0, ctxs[l]->stream);
+            cudaStreamWaitEvent(ctxs[g0]->stream, ctxs[l]->ev0, 0);
+        }
+        const int rc = compute_batch(ctxs + g0, m, q_re + g0, q_im + g0, on_device, Q ? Q + g0 : nullptr,
+                                     stats ? stats + g0 : nullptr);
+        if (rc) return rc;
+    }
     return SMPQ_OK;
 }
 

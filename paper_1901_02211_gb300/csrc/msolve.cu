@@ -111,6 +111,37 @@ __device__ __forceinline__ double2 source_at(const Source &src, int V, int s, in
     return make_double2((cl >= 0 && src.colour[s] == cl && c == src.src_comp[j]) ? 1.0 : 0.0, 0.0);
 }
 
+// ------------------------------------------------------------------ the lattices of a launch
+// The RHS tiles of a launch (blockIdx.y) belong to one lattice, or to several
+// of different sizes (the uneven batch of smpq_compute_qx_batch): lattice l
+// owns the tiles from chunk0_l on, and its part of every field buffer starts
+// at element f0_l.  The iteration kernels take this table; M = false is the
+// one-lattice form (entry 0, known at compile time).
+constexpr int MAX_LAT = 4;
+struct Lat {
+    Geom g;
+    const void *U;  // links in the launch's precision
+    long long f0;   // first element (complex value) of the lattice's fields
+    long long p0;   // first partial-sum row of the lattice in this launch
+    int chunk0;     // first RHS tile
+    int G;          // blocks per tile in this launch (launch YP: lattice blocks)
+    double s0;      // base (smallest) shift of the lattice's rational
+    int n_sup, Gs;  // launch YP: support entries per rhs, support blocks per tile
+    int B;          // right-hand sides of the lattice
+    const int *supsite;
+    long long sup0; // first element of the lattice's support fields (y; ps shift by shift)
+};
+struct Lats {
+    int n;
+    Lat l[MAX_LAT];
+};
+template <bool M> __device__ __forceinline__ int lat_index(const Lats &L) {
+    if constexpr (!M) return 0;
+    int l = 0;
+    while (l + 1 < L.n && (int)blockIdx.y >= L.l[l + 1].chunk0) ++l;
+    return l;
+}
+
 // ------------------------------------------------------------------ scalar steps (one thread per column)
 // First scalar step of column j: alpha and the shift recurrences zeta_{k+1},
 // alpha_i (tt = |D_W p|^2, pp = |p|^2, so <p, A p> = tt + s0 pp).
@@ -202,8 +233,8 @@ __device__ void s2_column(int j, double rrn, const Scal &sc, const ShiftParams &
 struct Fuse {
     int *count; // [tiles] blocks of the tile that have stored their partials; back to 0 after each launch
     Scal sc;
-    ShiftParams sp;
-    int B;
+    const ShiftParams *sp; // [lattices] each lattice's shifts (device memory)
+    int B;                 // right-hand sides of the solve (stride of the shift-major scalars)
     double tol2, delta2, theta2; // (second step only)
 };
 
@@ -226,15 +257,15 @@ __device__ __forceinline__ bool last_block_of_tile(int *count, int G, bool wrote
     return last;
 }
 
-// Sum over the G blocks of RHS tile `chunk` of the partials of each column, in
+// Sum over the G blocks of an RHS tile (partial rows prow...) of each column, in
 // a fixed order (NT / BC lanes per column, then the lanes in order); every
 // thread of the block calls it, threads < BC receive their column's total.
-template <int BC, int NT> __device__ double tile_sum(const double *part, int chunk, int G, double *sm) {
+template <int BC, int NT> __device__ double tile_sum(const double *part, size_t prow, int G, double *sm) {
     constexpr int K = NT / BC;
     const int t = threadIdx.x, jj = t % BC, k = t / BC;
     double v = 0;
     if (k < K)
-        for (int b = k; b < G; b += K) v += __ldcg(part + ((size_t)chunk * G + b) * BC + jj);
+        for (int b = k; b < G; b += K) v += __ldcg(part + (prow + b) * BC + jj);
     if (k < K) sm[t] = v;
     __syncthreads();
     double tot = 0;
@@ -245,21 +276,23 @@ template <int BC, int NT> __device__ double tile_sum(const double *part, int chu
 }
 
 // end of lattice kernel A: the tile's last block runs the first scalar step
+// (lattice l, its tile's partial rows from prow)
 template <int BC, int NT>
-__device__ __forceinline__ void fuse_step1(const Fuse &f, const double *part_t, const double *part_p, int G,
-                                           double *sm) {
+__device__ __forceinline__ void fuse_step1(const Fuse &f, int l, const double *part_t, const double *part_p,
+                                           size_t prow, int G, double *sm) {
     if (!f.count || !last_block_of_tile(f.count, G, threadIdx.x < BC)) return;
-    const double tt = tile_sum<BC, NT>(part_t, blockIdx.y, G, sm);
-    const double pp = tile_sum<BC, NT>(part_p, blockIdx.y, G, sm);
-    if (threadIdx.x < BC) s1_column(blockIdx.y * BC + threadIdx.x, tt, pp, f.sc, f.sp, f.B);
+    const double tt = tile_sum<BC, NT>(part_t, prow, G, sm);
+    const double pp = tile_sum<BC, NT>(part_p, prow, G, sm);
+    if (threadIdx.x < BC) s1_column(blockIdx.y * BC + threadIdx.x, tt, pp, f.sc, f.sp[l], f.B);
 }
 // end of lattice kernel B: the tile's last block runs the second scalar step
 template <int BC, int NT>
-__device__ __forceinline__ void fuse_step2(const Fuse &f, const double *part_r, int G, double *sm) {
+__device__ __forceinline__ void fuse_step2(const Fuse &f, int l, const double *part_r, size_t prow, int G,
+                                           double *sm) {
     if (!f.count || !last_block_of_tile(f.count, G, threadIdx.x < BC)) return;
-    const double rr = tile_sum<BC, NT>(part_r, blockIdx.y, G, sm);
+    const double rr = tile_sum<BC, NT>(part_r, prow, G, sm);
     if (threadIdx.x < BC)
-        s2_column(blockIdx.y * BC + threadIdx.x, rr, f.sc, f.sp, f.B, f.tol2, f.delta2, f.theta2);
+        s2_column(blockIdx.y * BC + threadIdx.x, rr, f.sc, f.sp[l], f.B, f.tol2, f.delta2, f.theta2);
 }
 
 // ------------------------------------------------------------------ lattice kernels
@@ -321,15 +354,22 @@ template <int BC, int NR> struct SmemCols {
 };
 
 // t = D_W p ; partials |t|^2 -> part_t, |p|^2 -> part_p (NR columns per thread)
-template <typename T, int BC, int NR>
+template <typename T, int BC, int NR, bool M>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
-    k_apply_a(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ p,
-              typename cplx_t<T>::type *__restrict__ t, T kappa, double *part_t, double *part_p, int G, int tpb, Fuse f) {
+    k_apply_a(Lats L, const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ t,
+              T kappa, double *part_t, double *part_p, int tpb, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
     __shared__ double sm[SmemCols<BC, NR>::N];
-    const int jj = (threadIdx.x % TM::TPS) * NR, chunk = blockIdx.y;
-    const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return; // beyond this lattice's blocks (uneven batch)
+    const Geom &g = la.g;
+    const C *__restrict__ U = (const C *)la.U;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = (threadIdx.x % TM::TPS) * NR;
+    const size_t base = la.f0 + (size_t)cl * 12 * g.V * BC + jj;
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     double at[NR], ap[NR];
 #pragma unroll
@@ -365,23 +405,31 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     double s1 = block_total<BC, NR>(at, sm);
     double s2 = block_total<BC, NR>(ap, sm);
     if (threadIdx.x < BC) {
-        part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
-        part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
+        part_t[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[(prow + blockIdx.x) * BC + threadIdx.x] = s2;
     }
-    fuse_step1<BC, TM::THREADS>(f, part_t, part_p, G, sm);
+    fuse_step1<BC, TM::THREADS>(f, l, part_t, part_p, prow, G, sm);
 }
 
 // r -= alpha (D_W^dag t + s0 p); partial |r|^2 (NR columns per thread)
-template <typename T, int BC, int NR>
+template <typename T, int BC, int NR, bool M>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
-    k_apply_b(Geom g, const typename cplx_t<T>::type *__restrict__ U, const typename cplx_t<T>::type *__restrict__ t,
-              const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ r,
-              const double *__restrict__ alpha, double s0, T kappa, double *part_r, int G, int tpb, Fuse f) {
+    k_apply_b(Lats L, const typename cplx_t<T>::type *__restrict__ t, const typename cplx_t<T>::type *__restrict__ p,
+              typename cplx_t<T>::type *__restrict__ r, const double *__restrict__ alpha, T kappa, double *part_r,
+              int tpb, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
     __shared__ double sm[SmemCols<BC, NR>::N];
-    const int jj = (threadIdx.x % TM::TPS) * NR, chunk = blockIdx.y, j = chunk * BC + jj;
-    const size_t base = (size_t)chunk * 12 * g.V * BC + jj;
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const C *__restrict__ U = (const C *)la.U;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const double s0 = la.s0;
+    const int jj = (threadIdx.x % TM::TPS) * NR, j = blockIdx.y * BC + jj;
+    const size_t base = la.f0 + (size_t)cl * 12 * g.V * BC + jj;
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     T a[NR];
 #pragma unroll
@@ -420,8 +468,8 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
         for (int q = 0; q < NR; ++q) ar[q] += (double)sr[q];
     }
     double s1 = block_total<BC, NR>(ar, sm);
-    if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
-    fuse_step2<BC, TM::THREADS>(f, part_r, G, sm);
+    if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TM::THREADS>(f, l, part_r, prow, G, sm);
 }
 
 // The base system's solution x accumulated by the p update: FP64 for the FP64
@@ -434,15 +482,18 @@ template <> struct XAcc<df64> { typedef df64c type; };
 // p = r + beta p on the lattice tiles of tile group bx; with x64, first
 // x64 += alpha p, with xlo, first xlo += alpha p in T (the part of the base
 // solution that the next residual replacement folds into x_hi)
+// (tile0: first element of the block's RHS tile in the fields; the tile is
+// blockIdx.y of the solve, so rhs j = blockIdx.y * BC + column)
 template <typename T, int BC>
-__device__ __forceinline__ void update_p_tiles(int bx, int V, const typename cplx_t<T>::type *__restrict__ r,
+__device__ __forceinline__ void update_p_tiles(int bx, int V, size_t tile0,
+                                               const typename cplx_t<T>::type *__restrict__ r,
                                                typename cplx_t<T>::type *__restrict__ p, const Scal &sc,
                                                typename XAcc<T>::type *__restrict__ x64,
                                                typename cplx_t<T>::type *__restrict__ xlo) {
     typedef typename cplx_t<T>::type C;
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    const int jj = threadIdx.x % BC, j = blockIdx.y * BC + jj;
     if (!sc.upd_rhs[j]) return;
-    const size_t base = (size_t)chunk * 12 * V * BC + jj;
+    const size_t base = tile0 + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     const T b = (T)sc.beta[j];
     const double a = sc.alpha[j];
@@ -523,13 +574,19 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS)
 }
 
 // t = D_W p in the half format; partials |t|^2 (before rounding) and |p|^2
-template <typename HT, int BC>
+template <typename HT, int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
-    k_apply_a_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
-                double *part_p, int G, int tpb, Fuse f) {
+    k_apply_a_h(Lats L, HF<HT> p, HF<HT> t, float kappa, double *part_t, double *part_p, int tpb, Fuse f) {
     __shared__ double sm[TileMap<BC>::THREADS];
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y;
-    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const typename HT::h2 *__restrict__ U = (const typename HT::h2 *)la.U;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = threadIdx.x % BC;
+    const size_t base = la.f0 + (size_t)cl * 12 * g.V * BC + jj, nbase = la.f0 / 12 + (size_t)cl * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     double at = 0, ap = 0;
     for (int tile = blockIdx.x * tpb, tend = min(ntiles, tile + tpb); tile < tend; ++tile) {
@@ -558,20 +615,28 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     const double s1 = block_sum<BC>(at, sm);
     const double s2 = block_sum<BC>(ap, sm);
     if (threadIdx.x < BC) {
-        part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
-        part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
+        part_t[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[(prow + blockIdx.x) * BC + threadIdx.x] = s2;
     }
-    fuse_step1<BC, TileMap<BC>::THREADS>(f, part_t, part_p, G, sm);
+    fuse_step1<BC, TileMap<BC>::THREADS>(f, l, part_t, part_p, prow, G, sm);
 }
 
 // r -= alpha (D_W^dag t + s0 p); partial |r|^2
-template <typename HT, int BC>
+template <typename HT, int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
-    k_apply_b_h(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
-                const double *__restrict__ alpha, double s0, float kappa, double *part_r, int G, int tpb, Fuse f) {
+    k_apply_b_h(Lats L, HF<HT> t, HF<HT> p, float2 *__restrict__ r, const double *__restrict__ alpha, float kappa,
+                double *part_r, int tpb, Fuse f) {
     __shared__ double sm[TileMap<BC>::THREADS];
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
-    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const typename HT::h2 *__restrict__ U = (const typename HT::h2 *)la.U;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const double s0 = la.s0;
+    const int jj = threadIdx.x % BC, j = blockIdx.y * BC + jj;
+    const size_t base = la.f0 + (size_t)cl * 12 * g.V * BC + jj, nbase = la.f0 / 12 + (size_t)cl * g.V * BC + jj;
     const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     const float a = (float)alpha[j], sh = (float)s0;
     double ar = 0;
@@ -600,17 +665,17 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
         ar += (double)sr;
     }
     const double s1 = block_sum<BC>(ar, sm);
-    if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
-    fuse_step2<BC, TileMap<BC>::THREADS>(f, part_r, G, sm);
+    if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TileMap<BC>::THREADS>(f, l, part_r, prow, G, sm);
 }
 
 // p = r + beta p on the lattice tiles of tile group bx, p in the half format
 template <typename HT, int BC>
-__device__ __forceinline__ void update_p_h_tiles(int bx, int V, const float2 *__restrict__ r, HF<HT> p,
-                                                 const Scal &sc, float2 *__restrict__ xlo) {
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+__device__ __forceinline__ void update_p_h_tiles(int bx, int V, size_t tile0, const float2 *__restrict__ r,
+                                                 HF<HT> p, const Scal &sc, float2 *__restrict__ xlo) {
+    const int jj = threadIdx.x % BC, j = blockIdx.y * BC + jj;
     if (!sc.upd_rhs[j]) return;
-    const size_t base = (size_t)chunk * 12 * V * BC + jj, nbase = (size_t)chunk * V * BC + jj;
+    const size_t base = tile0 + jj, nbase = tile0 / 12 + jj;
     const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     const float b = (float)sc.beta[j], a = (float)sc.alpha[j];
     for (int tile = bx * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
@@ -648,14 +713,20 @@ template <int BC> __device__ __forceinline__ void st_rx2(float2 *p, float2 re, f
     *reinterpret_cast<float4 *>(p) = make_float4(re.x, im.x, re.y, im.y);
 }
 
-template <typename HT, int BC>
+template <typename HT, int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
-    k_apply_a_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> p, HF<HT> t, float kappa, double *part_t,
-                 double *part_p, int G, int tpb, Fuse f) {
+    k_apply_a_h2(Lats L, HF<HT> p, HF<HT> t, float kappa, double *part_t, double *part_p, int tpb, Fuse f) {
     typedef TileMap<BC, 2> TM;
     __shared__ double sm[SmemCols<BC, 2>::N];
-    const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y;
-    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const typename HT::h2 *__restrict__ U = (const typename HT::h2 *)la.U;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = (threadIdx.x % TM::TPS) * 2;
+    const size_t base = la.f0 + (size_t)cl * 12 * g.V * BC + jj, nbase = la.f0 / 12 + (size_t)cl * g.V * BC + jj;
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     double at[2] = {0, 0}, ap[2] = {0, 0};
     const float2 nk = bc2(-kappa);
@@ -685,20 +756,28 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
     const double s1 = block_total<BC, 2>(at, sm);
     const double s2 = block_total<BC, 2>(ap, sm);
     if (threadIdx.x < BC) {
-        part_t[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
-        part_p[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s2;
+        part_t[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[(prow + blockIdx.x) * BC + threadIdx.x] = s2;
     }
-    fuse_step1<BC, TM::THREADS>(f, part_t, part_p, G, sm);
+    fuse_step1<BC, TM::THREADS>(f, l, part_t, part_p, prow, G, sm);
 }
 
-template <typename HT, int BC>
+template <typename HT, int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
-    k_apply_b_h2(Geom g, const typename HT::h2 *__restrict__ U, HF<HT> t, HF<HT> p, float2 *__restrict__ r,
-                 const double *__restrict__ alpha, double s0, float kappa, double *part_r, int G, int tpb, Fuse f) {
+    k_apply_b_h2(Lats L, HF<HT> t, HF<HT> p, float2 *__restrict__ r, const double *__restrict__ alpha, float kappa,
+                 double *part_r, int tpb, Fuse f) {
     typedef TileMap<BC, 2> TM;
     __shared__ double sm[SmemCols<BC, 2>::N];
-    const int jj = (threadIdx.x % TM::TPS) * 2, chunk = blockIdx.y, j = chunk * BC + jj;
-    const size_t base = (size_t)chunk * 12 * g.V * BC + jj, nbase = (size_t)chunk * g.V * BC + jj;
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const typename HT::h2 *__restrict__ U = (const typename HT::h2 *)la.U;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const double s0 = la.s0;
+    const int jj = (threadIdx.x % TM::TPS) * 2, j = blockIdx.y * BC + jj;
+    const size_t base = la.f0 + (size_t)cl * 12 * g.V * BC + jj, nbase = la.f0 / 12 + (size_t)cl * g.V * BC + jj;
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     const float2 a = make_float2((float)alpha[j], (float)alpha[j + 1]), na = make_float2(-a.x, -a.y);
     const float2 sh = bc2((float)s0), nk = bc2(-kappa);
@@ -731,27 +810,33 @@ __global__ void __launch_bounds__(TileMap<BC, 2>::THREADS, 2)
         ar[1] += (double)sr.y;
     }
     const double s1 = block_total<BC, 2>(ar, sm);
-    if (threadIdx.x < BC) part_r[((size_t)chunk * G + blockIdx.x) * BC + threadIdx.x] = s1;
-    fuse_step2<BC, TM::THREADS>(f, part_r, G, sm);
+    if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TM::THREADS>(f, l, part_r, prow, G, sm);
 }
 
 // Shifted updates on the support: y += c_i alpha_i p_i ; p_i = zeta_new_i r + beta_i p_i.
 // Support entry k of rhs j sits on lattice site supsite[rhs_class[j] * n_sup + k]
 // (identity when supsite == nullptr).  r is read in the iteration precision T,
 // ps ([shift][chunk][n_sup][12][BC]) is kept in TS, y ([chunk][n_sup][12][BC]) in FP64.
+// (one lattice: rtile0 is the first element of the RHS tile in r, cl the tile
+// within the lattice, j0 the solve's first rhs of the tile; ps and y are the
+// lattice's support fields, [shift][tile][n_sup][12][BC] and
+// [tile][n_sup][12][BC] for its B right-hand sides; the shift-major scalars
+// have stride Btot)
 template <typename T, typename TS, int BC>
-__device__ __forceinline__ void shift_tiles(int bx, int V, int n_sup, int nshift, int B,
-                                            const int *__restrict__ supsite, const int *__restrict__ rhs_class,
+__device__ __forceinline__ void shift_tiles(int bx, int cl, int j0, size_t rtile0, int n_sup, int nshift, int B,
+                                            int Btot, const int *__restrict__ supsite,
+                                            const int *__restrict__ rhs_class,
                                             const typename cplx_t<T>::type *__restrict__ r,
                                             typename cplx_t<TS>::type *__restrict__ ps, double2 *__restrict__ y,
                                             const Scal &sc, const ShiftParams &sp, int init) {
     typedef typename cplx_t<T>::type CR;
     typedef typename cplx_t<TS>::type C;
-    const int jj = threadIdx.x % BC, chunk = blockIdx.y, j = chunk * BC + jj;
+    const int jj = threadIdx.x % BC, j = j0 + jj;
     const int cls = rhs_class[j];
     if (cls < 0) return;
-    const size_t rbase = (size_t)chunk * 12 * V * BC + jj;
-    const size_t sbase = (size_t)chunk * 12 * n_sup * BC + jj;
+    const size_t rbase = rtile0 + jj;
+    const size_t sbase = (size_t)cl * 12 * n_sup * BC + jj;
     const size_t sstride = (size_t)B * 12 * n_sup; // one shift
     const int ntiles = (n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
     for (int tile = bx * TPB, tend = min(ntiles, tile + TPB); tile < tend; ++tile) {
@@ -776,10 +861,10 @@ __device__ __forceinline__ void shift_tiles(int bx, int V, int n_sup, int nshift
 #pragma unroll
         for (int c = 0; c < 12; ++c) yv[c] = y[sbase + ((size_t)k * 12 + c) * BC];
         for (int i = 0; i < nshift; ++i) {
-            if (!sc.upd[i * B + j]) continue;
-            double ca = sp.c[i] * sc.alpha_s[i * B + j];
-            TS zn = (TS)sc.zeta_new[i * B + j];
-            TS bs = (TS)sc.beta_s[i * B + j];
+            if (!sc.upd[i * Btot + j]) continue;
+            double ca = sp.c[i] * sc.alpha_s[i * Btot + j];
+            TS zn = (TS)sc.zeta_new[i * Btot + j];
+            TS bs = (TS)sc.beta_s[i * Btot + j];
             C *pi = ps + i * sstride + sbase;
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
@@ -798,38 +883,51 @@ __device__ __forceinline__ void shift_tiles(int bx, int V, int n_sup, int nshift
 }
 
 // shifted directions at the start of a solve: p_i = b (= r), y = 0
+// (one lattice per launch: blockIdx.y is its tile, chunk0 its first tile in
+// the solve; r points at the lattice's part of the field)
 template <typename T, typename TS, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_shift_init(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite,
+    k_shift_init(int V, int n_sup, int nshift, int B, int chunk0, const int *__restrict__ supsite,
                  const int *__restrict__ rhs_class, const typename cplx_t<T>::type *__restrict__ r,
                  typename cplx_t<TS>::type *__restrict__ ps, double2 *__restrict__ y, Scal sc, ShiftParams sp) {
-    shift_tiles<T, TS, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 1);
+    shift_tiles<T, TS, BC>(blockIdx.x, blockIdx.y, (chunk0 + blockIdx.y) * BC, (size_t)blockIdx.y * 12 * V * BC, n_sup,
+                           nshift, B, B, supsite, rhs_class, r, ps, y, sc, sp, 1);
 }
 
 // Launch YP of an iteration: blocks x < Gs update y and the shifted directions
 // on the support, the others p (and x64) on the lattice.
-template <typename T, typename TS, int BC>
+template <typename T, typename TS, int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_yp(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
-         const typename cplx_t<T>::type *__restrict__ r, typename cplx_t<TS>::type *__restrict__ ps,
-         double2 *__restrict__ y, Scal sc, ShiftParams sp, int Gs, typename cplx_t<T>::type *__restrict__ p,
+    k_yp(Lats L, int nshift, int Btot, const int *__restrict__ rhs_class, const typename cplx_t<T>::type *__restrict__ r,
+         typename cplx_t<TS>::type *__restrict__ ps, double2 *__restrict__ y, Scal sc,
+         const ShiftParams *__restrict__ sp, typename cplx_t<T>::type *__restrict__ p,
          typename XAcc<T>::type *__restrict__ x64, typename cplx_t<T>::type *__restrict__ xlo) {
-    if ((int)blockIdx.x < Gs)
-        shift_tiles<T, TS, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 0);
-    else
-        update_p_tiles<T, BC>(blockIdx.x - Gs, V, r, p, sc, x64, xlo);
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    const int cl = blockIdx.y - la.chunk0, bx = blockIdx.x;
+    const size_t tile0 = la.f0 + (size_t)cl * 12 * la.g.V * BC;
+    if (bx < la.Gs)
+        shift_tiles<T, TS, BC>(bx, cl, blockIdx.y * BC, tile0, la.n_sup, nshift, la.B, Btot, la.supsite, rhs_class, r,
+                               ps + (size_t)nshift * la.sup0, y + la.sup0, sc, sp[l], 0);
+    else if (bx < la.Gs + la.G)
+        update_p_tiles<T, BC>(bx - la.Gs, la.g.V, tile0, r, p, sc, x64, xlo);
 }
 
 // Launch YP of a half-storage iteration (p in the half format)
-template <typename HT, int BC>
+template <typename HT, int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS)
-    k_yp_h(int V, int n_sup, int nshift, int B, const int *__restrict__ supsite, const int *__restrict__ rhs_class,
-           const float2 *__restrict__ r, float2 *__restrict__ ps, double2 *__restrict__ y, Scal sc, ShiftParams sp,
-           int Gs, HF<HT> p, float2 *__restrict__ xlo) {
-    if ((int)blockIdx.x < Gs)
-        shift_tiles<float, float, BC>(blockIdx.x, V, n_sup, nshift, B, supsite, rhs_class, r, ps, y, sc, sp, 0);
-    else
-        update_p_h_tiles<HT, BC>(blockIdx.x - Gs, V, r, p, sc, xlo);
+    k_yp_h(Lats L, int nshift, int Btot, const int *__restrict__ rhs_class, const float2 *__restrict__ r,
+           float2 *__restrict__ ps, double2 *__restrict__ y, Scal sc, const ShiftParams *__restrict__ sp, HF<HT> p,
+           float2 *__restrict__ xlo) {
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    const int cl = blockIdx.y - la.chunk0, bx = blockIdx.x;
+    const size_t tile0 = la.f0 + (size_t)cl * 12 * la.g.V * BC;
+    if (bx < la.Gs)
+        shift_tiles<float, float, BC>(bx, cl, blockIdx.y * BC, tile0, la.n_sup, nshift, la.B, Btot, la.supsite,
+                                      rhs_class, r, ps + (size_t)nshift * la.sup0, y + la.sup0, sc, sp[l], 0);
+    else if (bx < la.Gs + la.G)
+        update_p_h_tiles<HT, BC>(bx - la.Gs, la.g.V, tile0, r, p, sc, xlo);
 }
 
 // x_hi += x_lo ; x_lo = 0 (x_hi in float-float: FP64 accuracy on the FP32 pipes)
@@ -1034,86 +1132,142 @@ constexpr bool ps32_phase2 = false;
 constexpr bool ps32_phase2 = true;
 #endif
 
-// One multi-shift solve of B right-hand sides in tiles of BC columns.  The
+// One lattice of a solve, as its caller describes it: the context (geometry,
+// links), the right-hand sides and support (spec), its rational's shifts and
+// where the results go.  A solve of several lattices (the uneven batch) takes
+// precision, tolerance and options from the first lattice's context.
+struct LatIn {
+    smpq_ctx *ctx;
+    const SolveSpec *spec;
+    ShiftParams sp;
+    SolveOut *out;
+};
+
+// One multi-shift solve of B right-hand sides in tiles of BC columns, over
+// one lattice or several of different sizes in the same launches.  The
 // solve runs in one or two phases:
 //   SMPQ_FP64  : FP64 iterations (vectors, D_W, shifted directions);
 //   SMPQ_FP32  : FP32 iterations with FP64 reliable updates of the base system;
 //   SMPQ_FP16N / SMPQ_BF16N : the same with p and t stored in FP16 / BF16 with
 //                per-site norms and reconstruct-12 links;
-//   SMPQ_MIXED : FP64 iterations until every right-hand side has
-//                ||r|| <= theta ||b||, then FP32 iterations without residual
-//                replacement; the shifted directions are FP64 in the first
-//                phase and FP32 in the second, y stays FP64 throughout.
-// Scalars, reductions and y are FP64 in every mode.
+//   SMPQ_MIXED : FP64-accurate iterations until every right-hand side has
+//                ||r|| <= theta ||b||, then FP32 iterations ending in one
+//                residual replacement of the base system; the shifted
+//                directions are FP64 in the first phase and FP32 in the
+//                second, y stays FP64 throughout.
+// Scalars, reductions and y are FP64 in every mode.  The fields of all
+// lattices share one buffer per vector: lattice l's part starts at element
+// f0[l] (its tiles first come at tile ch0[l] of the solve).
 template <int BC> struct Solve {
-    smpq_ctx *ctx;
-    const SolveSpec &spec;
-    ShiftParams sp;
-    int B, V, nchunk, G, Gs;
-    size_t nfield, nsupf, npart;
+    smpq_ctx *ctx; // the first lattice's context: stream, workspace, options
+    std::vector<LatIn> in;
+    int nl;
+    // per lattice: sites, right-hand sides, tiles, first tile, first rhs, blocks
+    // per tile of the one-column lattice kernels (TPB tiles each), of the
+    // support kernels, one-column tiles; field, support-field and partial-row offsets
+    std::vector<int> V, Bl, nch, ch0, j0, G1, Gs1, nt1;
+    std::vector<size_t> f0, s0, p0;
+    std::vector<Source> srcl;
+    std::vector<ShiftParams> sph; // host copies behind spd
+    int B = 0, nchunk = 0, nshift = 0;
+    size_t nfield = 0, nsupf = 0, npart = 0;
     cudaStream_t st;
     Scal sc;
-    Source src;
+    const ShiftParams *spd = nullptr; // [nl] device copies
     double *part0, *part1, *part2;
     double2 *y;
     double tol2;
-    int base_shift;
     int *hflags = nullptr;
-    int *count = nullptr;     // [nchunk] arrival counters of the fused scalar steps
-    double2 *x64 = nullptr;   // base-system solution in FP64 (true residual), nullable
-    double *true_rr = nullptr; // [B] |b - (A + s0) x64|^2
+    int *count = nullptr;       // [nchunk] arrival counters of the fused scalar steps
+    double2 *x64 = nullptr;     // base-system solution in FP64 (true residual), nullable
+    double *true_rr = nullptr;  // [B] |b - (A + s0) x64|^2
     int iters = 0, nrel = 0;
     bool prof;
     int chk;
+    bool shifts;
+    int tpb_hi = TPB, tpb_lo = TPB, nr = 1;
 
-    Solve(smpq_ctx *c, const SolveSpec &s, const ShiftParams &p) : ctx(c), spec(s), sp(p) {}
+    explicit Solve(const std::vector<LatIn> &lats) : ctx(lats[0].ctx), in(lats), nl((int)lats.size()) {}
+
+    // the per-rhs scalars of lattice l (the shift-major ones keep the solve's stride B)
+    Scal scal_of(int l) const {
+        Scal s = sc;
+        const int o = j0[l];
+        s.rr += o; s.bb += o; s.alpha += o; s.beta += o; s.alpha_prev += o; s.beta_prev += o; s.rr_ref += o;
+        s.act_rhs += o; s.upd_rhs += o; s.iters += o;
+        s.zeta += o; s.zeta_prev += o; s.zeta_new += o; s.alpha_s += o; s.beta_s += o; s.act += o; s.upd += o;
+        return s;
+    }
 
     int setup(double tol, double *hist, int hist_len) {
-        B = spec.B;
-        V = ctx->V;
-        nchunk = B / BC;
         st = ctx->stream;
-        const int ntiles = (V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-        G = (ntiles + TPB - 1) / TPB;
-        const int nsup_tiles = (spec.n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
-        Gs = std::max(1, (nsup_tiles + TPB - 1) / TPB);
-        nfield = (size_t)B * 12 * V;
-        nsupf = (size_t)B * 12 * spec.n_sup;
-        // the NR-column kernels have at most as many blocks per tile as the 1-column ones
-        // partial rows per tile: the most blocks any launch has per tile (the
-        // D_W launches at one tile per block have ntiles; the support kernels Gs)
-        npart = (size_t)nchunk * std::max(ntiles, Gs) * BC;
+        shifts = in[0].spec->n_sup > 0;
+        nshift = in[0].sp.n;
+        V.resize(nl); Bl.resize(nl); nch.resize(nl); ch0.resize(nl); j0.resize(nl); G1.resize(nl); Gs1.resize(nl);
+        nt1.resize(nl); f0.resize(nl); s0.resize(nl); p0.resize(nl); srcl.resize(nl); sph.resize(nl);
+        for (int l = 0; l < nl; ++l) {
+            const SolveSpec &sp = *in[l].spec;
+            if (sp.B % BC || in[l].sp.n != nshift || (sp.n_sup > 0) != shifts || in[l].ctx->device != ctx->device)
+                return set_err(ctx, SMPQ_EINVAL, "lattices of one solve need the same tile width, poles, support "
+                                                 "kind and device");
+            V[l] = in[l].ctx->V;
+            Bl[l] = sp.B;
+            nch[l] = sp.B / BC;
+            ch0[l] = nchunk;
+            j0[l] = B;
+            nt1[l] = (V[l] + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+            G1[l] = (nt1[l] + TPB - 1) / TPB;
+            const int nsup_tiles = (sp.n_sup + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+            Gs1[l] = std::max(1, (nsup_tiles + TPB - 1) / TPB);
+            f0[l] = nfield;
+            s0[l] = nsupf;
+            p0[l] = npart / BC;
+            nchunk += nch[l];
+            B += sp.B;
+            nfield += (size_t)sp.B * 12 * V[l];
+            nsupf += (size_t)sp.B * 12 * sp.n_sup;
+            // partial rows per tile: the most blocks any launch has per tile (the
+            // D_W launches at one tile per block have nt1; the support kernels Gs1)
+            npart += (size_t)nch[l] * std::max(nt1[l], Gs1[l]) * BC;
+            sph[l] = in[l].sp;
+        }
+        tpb_hi = std::max(1, in[0].spec->tpb_hi > 0 ? in[0].spec->tpb_hi : TPB);
+        tpb_lo = std::max(1, in[0].spec->tpb_lo > 0 ? in[0].spec->tpb_lo : TPB);
+        nr = in[0].spec->nr == 2 ? 2 : 1;
         std::vector<Buf> &ws = ctx->ws;
         if (ws.size() < W_COUNT) ws.resize(W_COUNT);
         int rc;
         if ((rc = ensure(ctx, ws[W_PART], 3 * npart * sizeof(double)))) return rc;
-        const size_t nscal = (size_t)B * 8 + (size_t)sp.n * B * 5;
-        const size_t nint = (size_t)B * 3 + (size_t)sp.n * B * 2 + 8 + (size_t)nchunk;
-        if ((rc = ensure(ctx, ws[W_SCAL], nscal * sizeof(double) + nint * sizeof(int)))) return rc;
+        const size_t nscal = (size_t)B * 8 + (size_t)nshift * B * 5;
+        const size_t nint = (size_t)B * 3 + (size_t)nshift * B * 2 + 8 + (size_t)nchunk;
+        const size_t spbytes = ((size_t)nl * sizeof(ShiftParams) + 255) / 256 * 256;
+        if ((rc = ensure(ctx, ws[W_SCAL], spbytes + nscal * sizeof(double) + nint * sizeof(int)))) return rc;
         part0 = (double *)ws[W_PART].p;
         part1 = part0 + npart;
         part2 = part1 + npart;
-        double *d = (double *)ws[W_SCAL].p;
+        spd = (const ShiftParams *)ws[W_SCAL].p;
+        cudaMemcpyAsync((void *)spd, sph.data(), nl * sizeof(ShiftParams), cudaMemcpyHostToDevice, st);
+        double *d = (double *)((char *)ws[W_SCAL].p + spbytes);
         sc.rr = d; d += B; sc.bb = d; d += B; sc.alpha = d; d += B; sc.beta = d; d += B;
         sc.alpha_prev = d; d += B; sc.beta_prev = d; d += B; sc.rr_ref = d; d += B;
-        sc.zeta = d; d += sp.n * B; sc.zeta_prev = d; d += sp.n * B; sc.zeta_new = d; d += sp.n * B;
-        sc.alpha_s = d; d += sp.n * B; sc.beta_s = d; d += sp.n * B;
+        sc.zeta = d; d += nshift * B; sc.zeta_prev = d; d += nshift * B; sc.zeta_new = d; d += nshift * B;
+        sc.alpha_s = d; d += nshift * B; sc.beta_s = d; d += nshift * B;
         true_rr = d; d += B;
         int *ip = (int *)d;
         sc.act_rhs = ip; ip += B; sc.upd_rhs = ip; ip += B; sc.iters = ip; ip += B;
-        sc.act = ip; ip += sp.n * B; sc.upd = ip; ip += sp.n * B;
+        sc.act = ip; ip += nshift * B; sc.upd = ip; ip += nshift * B;
         sc.flags = ip; ip += 4; sc.iter_counter = ip; ip += 4;
         count = ip;
         sc.hist = hist;
         sc.hist_len = hist_len;
-        src.colour = spec.d_colour;
-        src.src_class = spec.d_src_class;
-        src.src_comp = spec.d_src_comp;
-        src.b64 = (const double2 *)spec.d_src_field;
+        for (int l = 0; l < nl; ++l) { // the lattice's sources, its per-rhs tables at its first rhs
+            const SolveSpec &sp = *in[l].spec;
+            srcl[l].colour = sp.d_colour;
+            srcl[l].src_class = sp.d_src_class ? sp.d_src_class + j0[l] : nullptr;
+            srcl[l].src_comp = sp.d_src_comp ? sp.d_src_comp + j0[l] : nullptr;
+            srcl[l].b64 = sp.d_src_field ? (const double2 *)sp.d_src_field + f0[l] : nullptr;
+        }
         tol2 = tol * tol;
-        base_shift = 0;
-        for (int i = 1; i < sp.n; ++i)
-            if (sp.sig[i] < sp.sig[base_shift]) base_shift = i;
         prof = ctx->opt.profile != 0;
         chk = std::max(1, ctx->opt.iters_per_check);
         if (prof) {
@@ -1135,6 +1289,67 @@ template <int BC> struct Solve {
         if (hflags) cudaFreeHost(hflags);
     }
 
+    // The lattice table of a D_W launch: blocks per tile for spb sites per tile
+    // and tpb tiles per block; partial rows lattice after lattice.  *gx: the
+    // grid's x extent (the largest lattice's blocks).
+    template <typename T, typename HT = void> Lats lats_dw(int spb, int tpb, int *gx) const {
+        Lats L{};
+        L.n = nl;
+        size_t prow = 0;
+        *gx = 1;
+        for (int l = 0; l < nl; ++l) {
+            Lat &a = L.l[l];
+            a.g = in[l].ctx->geom;
+            if constexpr (std::is_void<HT>::value) a.U = Links<T>::get(in[l].ctx);
+            else a.U = HLinks<HT>::get(in[l].ctx);
+            a.f0 = (long long)f0[l];
+            a.chunk0 = ch0[l];
+            a.G = ((V[l] + spb - 1) / spb + tpb - 1) / tpb;
+            a.p0 = (long long)prow;
+            a.s0 = sph[l].s0;
+            a.B = Bl[l];
+            prow += (size_t)nch[l] * a.G;
+            *gx = std::max(*gx, a.G);
+        }
+        return L;
+    }
+    // the lattice table of launch YP: support blocks, then lattice blocks (one column, TPB tiles)
+    Lats lats_yp(int *gx) const {
+        Lats L{};
+        L.n = nl;
+        *gx = 1;
+        for (int l = 0; l < nl; ++l) {
+            Lat &a = L.l[l];
+            a.g = in[l].ctx->geom;
+            a.f0 = (long long)f0[l];
+            a.chunk0 = ch0[l];
+            a.G = G1[l];
+            a.Gs = shifts ? Gs1[l] : 0;
+            a.n_sup = in[l].spec->n_sup;
+            a.supsite = in[l].spec->d_supsite;
+            a.sup0 = (long long)s0[l];
+            a.B = Bl[l];
+            a.s0 = sph[l].s0;
+            *gx = std::max(*gx, a.Gs + a.G);
+        }
+        return L;
+    }
+    // one lattice alone (its part of every buffer), for the per-lattice launches
+    template <typename T> Lats lats_one(int l) const {
+        Lats L{};
+        L.n = 1;
+        Lat &a = L.l[0];
+        a.g = in[l].ctx->geom;
+        a.U = Links<T>::get(in[l].ctx);
+        a.f0 = (long long)f0[l];
+        a.chunk0 = 0;
+        a.G = G1[l];
+        a.p0 = (long long)p0[l];
+        a.s0 = sph[l].s0;
+        a.B = Bl[l];
+        return L;
+    }
+
     void collect(int n, bool hi) {
         if (!prof) return;
         for (int k = 0; k < n; ++k) {
@@ -1151,40 +1366,35 @@ template <int BC> struct Solve {
         (hi ? ctx->prof_b_hi_n : ctx->prof_b_n) += n;
     }
 
-    // Iterate with vectors of precision T and shifted directions of precision TS.
-    // init: start from x = 0 (sources); otherwise continue from the current state.
-    // rel: FP64 reliable updates (needs xlo, xhi, t64).  theta2 > 0: return once
-    // every active right-hand side has ||r||^2 <= theta2 ||b||^2.
-    // fixed > 0: exactly `fixed` iterations, no checks (Lanczos).
     // a half-format field of this solve passed through a float2 pointer
     template <typename HT> HF<HT> hfield(void *f) const {
         typename HT::h2 *v = (typename HT::h2 *)f;
         return HF<HT>{v, (float *)(v + nfield)};
     }
 
+    // Iterate with vectors of precision T and shifted directions of precision TS.
+    // init: start from x = 0 (sources); otherwise continue from the current state.
+    // rel: FP64 reliable updates (needs xlo, xhi, t64).  theta2 > 0: return once
+    // every active right-hand side has ||r||^2 <= theta2 ||b||^2.
+    // fixed > 0: exactly `fixed` iterations, no checks (Lanczos).
     // HT (H16 or B16, T = float): p and t are half-format fields (components,
     // then norms) passed through the float2 pointers.
-    template <typename T, typename TS, typename HT = void>
     // xacc (nullable): the base solution accumulated by the p updates (FP64 for
     // FP64 iterations, float-float for the mixed solve's first phase).
+    template <typename T, typename TS, typename HT = void>
     int phase(typename cplx_t<T>::type *p, typename cplx_t<T>::type *t, typename cplx_t<T>::type *r,
               typename cplx_t<T>::type *xlo, df64c *xhi, df64c *t64, typename cplx_t<TS>::type *ps, bool init,
               bool rel, double theta2, int fixed, int max_iter, typename XAcc<T>::type *xacc = nullptr,
               bool replace_mid = true) {
         typedef typename cplx_t<T>::type C;
         constexpr bool half = !std::is_void<HT>::value;
-        const dim3 grid(G, nchunk), gsup(Gs, nchunk);
         const int TH = TileMap<BC>::THREADS;
-        const int sblocks = B;
         const bool hi = sizeof(T) != sizeof(float); // FP64 or float-float iterations
+        const bool multi = nl > 1;
         // kernel shape of the D_W launches (the autotuner's choice): tiles per
         // block, per phase, and for the FP32 kernels one or two columns per thread
-        const int tpb = std::max(1, hi ? spec.tpb_hi : spec.tpb_lo);
-        const bool two_cols = std::is_same<T, float>::value && !half && spec.nr == 2 && BC % 2 == 0;
-        auto blocks_for = [&](int spb) { return ((V + spb - 1) / spb + tpb - 1) / tpb; };
-        // every launch's partial rows must fit the partial buffers (npart per buffer)
-        if ((size_t)blocks_for(TileMap<BC, 1>::SPB) * nchunk * BC > npart || (size_t)G * nchunk * BC > npart)
-            return set_err(ctx, SMPQ_EINVAL, "internal: launch shape exceeds the partial-sum buffers");
+        const int tpb = hi ? tpb_hi : tpb_lo;
+        const bool two_cols = std::is_same<T, float>::value && !half && nr == 2 && BC % 2 == 0 && !multi;
         // Half-storage iterations replace the residual at least every 10x drop:
         // their iterated residual drifts from the true one by about the format's
         // rounding times the condition number per iteration, so a 1000x drop
@@ -1194,64 +1404,83 @@ template <int BC> struct Solve {
         // (then only the base shift can re-activate, so the replacement never
         // enters the shifted systems; the mixed solve's FP32 phase)
         const double delta2 = rel && replace_mid ? delta * delta : 0.0;
-        const Geom g = ctx->geom;
         const T kappa = (T)ctx->opt.kappa;
-        const C *U = (const C *)Links<T>::get(ctx);
-        const bool shifts = spec.n_sup > 0;
         const int per_iter = 3;
         if constexpr (half) {
             if (!rel || !xlo || !xhi || !t64)
                 return set_err(ctx, SMPQ_EINVAL, "internal: half-storage iterations need FP64 reliable updates");
         }
+        // every launch's partial rows must fit the partial buffers (npart per
+        // buffer): the D_W launches at this tpb (one column: the most blocks)
+        // and the one-column lattice kernels
+        {
+            size_t rows = 0;
+            for (int l = 0; l < nl; ++l)
+                rows += (size_t)nch[l] * std::max((nt1[l] + tpb - 1) / tpb, G1[l]);
+            if (rows * BC > npart)
+                return set_err(ctx, SMPQ_EINVAL, "internal: launch shape exceeds the partial-sum buffers");
+        }
         if (init) {
-            if constexpr (half)
-                k_init_h<HT, BC><<<grid, TH, 0, st>>>(g, src, (float2 *)r, hfield<HT>(p), (float2 *)xlo, xhi, part0, G);
-            else
-                k_init<T, BC><<<grid, TH, 0, st>>>(g, src, r, p, xlo, xhi, part0, G);
-            s_init<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part0, sc, sp, sqrt(tol2));
-            if (shifts)
-                k_shift_init<T, TS, BC><<<gsup, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite,
-                                                             spec.d_rhs_class, r, ps, y, sc, sp);
-            ctx->launches += 2 + (shifts ? 1 : 0);
+            for (int l = 0; l < nl; ++l) {
+                const dim3 grid(G1[l], nch[l]);
+                const Geom &g = in[l].ctx->geom;
+                const size_t o = f0[l];
+                double *pl = part0 + p0[l] * BC;
+                if constexpr (half)
+                    k_init_h<HT, BC><<<grid, TH, 0, st>>>(g, srcl[l], (float2 *)r + o, hfield_at<HT>(p, o),
+                                                          (float2 *)xlo + o, xhi + o, pl, G1[l]);
+                else
+                    k_init<T, BC><<<grid, TH, 0, st>>>(g, srcl[l], r + o, p + o, xlo ? xlo + o : nullptr,
+                                                       xhi ? xhi + o : nullptr, pl, G1[l]);
+                s_init<<<Bl[l], SCAL_THREADS, 0, st>>>(B, BC, G1[l], pl, scal_of(l), sph[l], sqrt(tol2));
+                if (shifts)
+                    k_shift_init<T, TS, BC><<<dim3(Gs1[l], nch[l]), TH, 0, st>>>(
+                        V[l], in[l].spec->n_sup, nshift, Bl[l], ch0[l], in[l].spec->d_supsite,
+                        in[l].spec->d_rhs_class, r + o, ps + (size_t)nshift * s0[l], y + s0[l], sc, sph[l]);
+                ctx->launches += 2 + (shifts ? 1 : 0);
+            }
         }
         // the scalar steps ride on the last block of each RHS tile of launches A and B
-        const Fuse f1{count, sc, sp, B, 0.0, 0.0, 0.0};
-        const Fuse f2{count, sc, sp, B, tol2, delta2, theta2};
-        // launch YP: Gy support blocks, then the lattice blocks of the p update
-        const int Gy = shifts ? Gs : 0;
-        const dim3 gridyp(Gy + G, nchunk);
+        const Fuse f1{count, sc, spd, B, 0.0, 0.0, 0.0};
+        const Fuse f2{count, sc, spd, B, tol2, delta2, theta2};
+        int gyp;
+        const Lats Lyp = lats_yp(&gyp);
+        const dim3 gridyp(gyp, nchunk);
+        const int *rhs_class = in[0].spec->d_rhs_class;
         // two columns per thread for even tiles (SMPQ_HALF_SOLVE_NR=1: one)
 #ifndef SMPQ_HALF_SOLVE_NR
 #define SMPQ_HALF_SOLVE_NR 2
 #endif
         constexpr bool h2cols = SMPQ_HALF_SOLVE_NR == 2 && BC % 2 == 0;
         typedef TileMap<BC, h2cols ? 2 : 1> TMH;
-        const int GH = blocks_for(TMH::SPB);
-        const dim3 gridh(GH, nchunk);
         auto iteration_half = [&](int k) {
             if constexpr (half) {
-                typedef typename HT::h2 H2;
-                const H2 *Uh = (const H2 *)HLinks<HT>::get(ctx);
                 const HF<HT> hp = hfield<HT>(p), ht = hfield<HT>(t);
                 constexpr int THH = TMH::THREADS;
-                if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-                if constexpr (h2cols)
-                    k_apply_a_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH, tpb, f1);
-                else
-                    k_apply_a_h<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, hp, ht, (float)kappa, part0, part1, GH, tpb, f1);
-                if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
-                if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
-                // (half-storage solves always run with reliable updates)
-                if constexpr (h2cols)
-                    k_apply_b_h2<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, sc.alpha, sp.s0,
-                                                                (float)kappa, part2, GH, tpb, f2);
-                else
-                    k_apply_b_h<HT, BC><<<gridh, THH, 0, st>>>(g, Uh, ht, hp, (float2 *)r, sc.alpha, sp.s0,
-                                                               (float)kappa, part2, GH, tpb, f2);
-                if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-                k_yp_h<HT, BC><<<gridyp, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class,
-                                                       (const float2 *)r, (float2 *)ps, y, sc, sp, Gy, hp,
-                                                       (float2 *)xlo);
+                int gx;
+                const Lats Ld = lats_dw<T, HT>(TMH::SPB, tpb, &gx);
+                const dim3 gridh(gx, nchunk);
+                auto launch = [&](auto m) {
+                    constexpr bool M = decltype(m)::value;
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
+                    if constexpr (h2cols)
+                        k_apply_a_h2<HT, BC, M><<<gridh, THH, 0, st>>>(Ld, hp, ht, (float)kappa, part0, part1, tpb, f1);
+                    else
+                        k_apply_a_h<HT, BC, M><<<gridh, THH, 0, st>>>(Ld, hp, ht, (float)kappa, part0, part1, tpb, f1);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
+                    if constexpr (h2cols)
+                        k_apply_b_h2<HT, BC, M><<<gridh, THH, 0, st>>>(Ld, ht, hp, (float2 *)r, sc.alpha, (float)kappa,
+                                                                       part2, tpb, f2);
+                    else
+                        k_apply_b_h<HT, BC, M><<<gridh, THH, 0, st>>>(Ld, ht, hp, (float2 *)r, sc.alpha, (float)kappa,
+                                                                      part2, tpb, f2);
+                    if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+                    k_yp_h<HT, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, (const float2 *)r,
+                                                             (float2 *)ps, y, sc, spd, hp, (float2 *)xlo);
+                };
+                if (multi) launch(std::true_type());
+                else launch(std::false_type());
             }
         };
         auto iteration = [&](int k) {
@@ -1259,39 +1488,54 @@ template <int BC> struct Solve {
                 iteration_half(k);
                 return;
             }
-            // the D_W pair with NR columns per thread
-            auto apply_pair = [&](auto nr_c) {
+            // the D_W pair with NR columns per thread, then launch YP
+            auto launch = [&](auto nr_c, auto m) {
                 constexpr int NR = decltype(nr_c)::value;
-                if constexpr (NR == 1 || (std::is_same<T, float>::value && BC % 2 == 0)) {
+                constexpr bool M = decltype(m)::value;
+                if constexpr (NR == 1 || (std::is_same<T, float>::value && BC % 2 == 0 && !M)) {
                     typedef TileMap<BC, NR> TMN;
-                    const int GN = blocks_for(TMN::SPB);
-                    const dim3 gridn(GN, nchunk);
+                    int gx;
+                    const Lats Ld = lats_dw<T>(TMN::SPB, tpb, &gx);
+                    const dim3 gridn(gx, nchunk);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-                    k_apply_a<T, BC, NR><<<gridn, TMN::THREADS, 0, st>>>(g, U, p, t, kappa, part0, part1, GN, tpb,
-                                                                          f1);
+                    k_apply_a<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, p, t, kappa, part0, part1, tpb, f1);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
-                    k_apply_b<T, BC, NR><<<gridn, TMN::THREADS, 0, st>>>(g, U, t, p, r, sc.alpha, sp.s0, kappa, part2,
-                                                                          GN, tpb, f2);
+                    k_apply_b<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, t, p, r, sc.alpha, kappa, part2, tpb,
+                                                                            f2);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+                    k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p, xacc,
+                                                              rel ? xlo : nullptr);
                 }
             };
-            if (two_cols) apply_pair(std::integral_constant<int, 2>());
-            else apply_pair(std::integral_constant<int, 1>());
-            k_yp<T, TS, BC><<<gridyp, TH, 0, st>>>(V, spec.n_sup, sp.n, B, spec.d_supsite, spec.d_rhs_class, r, ps, y,
-                                                   sc, sp, Gy, p, xacc, rel ? xlo : nullptr);
+            if (multi) launch(std::integral_constant<int, 1>(), std::true_type());
+            else if (two_cols) launch(std::integral_constant<int, 2>(), std::false_type());
+            else launch(std::integral_constant<int, 1>(), std::false_type());
         };
-        // residual replacement: x_hi += x_lo, r = b - (A + s0) x_hi in float-float
+        // residual replacement, lattice by lattice: x_hi += x_lo, r = b - (A + s0) x_hi in float-float
         auto reliable = [&]() {
-            ctx->launches += 4;
             const df64 kdf(ctx->opt.kappa);
-            const df64c *Udf = (const df64c *)ctx->Udf.p;
             Fuse none{};
-            k_rel_accum<T, BC><<<grid, TH, 0, st>>>(V, xhi, xlo, G);
-            k_apply_a<df64, BC, 1><<<grid, TH, 0, st>>>(g, Udf, xhi, t64, kdf, part0, part1, G, TPB, none);
-            k_rel_resid_df<T, BC><<<grid, TH, 0, st>>>(g, Udf, t64, xhi, src, r, sp.s0, kdf, part2, G);
+            for (int l = 0; l < nl; ++l) {
+                const dim3 grid(G1[l], nch[l]);
+                const size_t o = f0[l];
+                const Geom &g = in[l].ctx->geom;
+                const df64c *Udf = (const df64c *)in[l].ctx->Udf.p;
+                k_rel_accum<T, BC><<<grid, TH, 0, st>>>(V[l], xhi + o, xlo + o, G1[l]);
+                k_apply_a<df64, BC, 1, false><<<grid, TH, 0, st>>>(lats_one<df64>(l), xhi, t64, kdf, part0, part1,
+                                                                   TPB, none);
+                k_rel_resid_df<T, BC><<<grid, TH, 0, st>>>(g, Udf, t64 + o, xhi + o, srcl[l], r + o, sph[l].s0, kdf,
+                                                           part2 + p0[l] * BC, G1[l]);
+                ctx->launches += 3;
+            }
             cudaMemsetAsync(sc.flags, 0, 2 * sizeof(int), st);
-            s_rel<<<sblocks, SCAL_THREADS, 0, st>>>(B, BC, G, part2, sc, sp, tol2, base_shift);
+            for (int l = 0; l < nl; ++l) {
+                int base = 0;
+                for (int i = 1; i < nshift; ++i)
+                    if (sph[l].sig[i] < sph[l].sig[base]) base = i;
+                s_rel<<<Bl[l], SCAL_THREADS, 0, st>>>(B, BC, G1[l], part2 + p0[l] * BC, scal_of(l), sph[l], tol2, base);
+                ctx->launches += 1;
+            }
         };
         if (fixed > 0) {
             for (int k = 0; k < fixed; ++k) {
@@ -1354,26 +1598,36 @@ template <int BC> struct Solve {
         return status;
     }
 
-    bool relpath = false; // FP32 / half paths: the last reliable update left |b - (A + s0) x_hi|^2 in sc.rr
+    // a half field's view at element offset o (components o..., norms o / 12...)
+    template <typename HT> HF<HT> hfield_at(void *f, size_t o) const {
+        HF<HT> h = hfield<HT>(f);
+        return HF<HT>{h.v + o, h.n + o / 12};
+    }
 
-    // True residual of the base system from the FP64 solution x64 (FP64 and
-    // mixed paths): t64 = D_W x64, |b - (D_W^dag t64 + s0 x64)|^2 per rhs into
-    // rr_out (the FP32 copy of that residual goes to the scratch field rs).
-    template <typename T>
-    int true_residual(double2 *t64, typename cplx_t<T>::type *rs, double *rr_out) {
-        const dim3 grid(G, nchunk);
+    bool relpath = false; // FP32 / half / mixed: the last reliable update left |b - (A + s0) x_hi|^2 in sc.rr
+
+    // True residual of the base system from the FP64 solution x64 (FP64 path):
+    // t64 = D_W x64, |b - (D_W^dag t64 + s0 x64)|^2 per rhs into rr_out (the
+    // residual itself goes to the scratch field rs).
+    int true_residual(double2 *t64, double2 *rs, double *rr_out) {
         const int TH = TileMap<BC>::THREADS;
-        launch_dslash<double>(ctx->geom, ctx->U64.p, x64, t64, B, BC, 0, ctx->opt.kappa, st);
-        k_rel_resid<T, BC><<<grid, TH, 0, st>>>(ctx->geom, (const double2 *)ctx->U64.p, t64, x64, src, rs, sp.s0,
-                                                ctx->opt.kappa, part2, G);
-        s_sum_rhs<<<B, SCAL_THREADS, 0, st>>>(BC, G, part2, rr_out);
-        ctx->launches += 3;
+        for (int l = 0; l < nl; ++l) {
+            const dim3 grid(G1[l], nch[l]);
+            const size_t o = f0[l];
+            smpq_ctx *c = in[l].ctx;
+            launch_dslash<double>(c->geom, c->U64.p, x64 + o, t64 + o, Bl[l], BC, 0, ctx->opt.kappa, st);
+            k_rel_resid<double, BC><<<grid, TH, 0, st>>>(c->geom, (const double2 *)c->U64.p, t64 + o, x64 + o,
+                                                         srcl[l], rs + o, sph[l].s0, ctx->opt.kappa,
+                                                         part2 + p0[l] * BC, G1[l]);
+            s_sum_rhs<<<Bl[l], SCAL_THREADS, 0, st>>>(BC, G1[l], part2 + p0[l] * BC, rr_out + j0[l]);
+            ctx->launches += 3;
+        }
         return cuda_check(ctx, cudaGetLastError(), "true residual");
     }
 
-    int finish(SolveOut *out, int fixed, const double *d_true_rr = nullptr) {
+    int finish(int fixed, const double *d_true_rr = nullptr) {
         cudaEventRecord(ctx->ev2, st);
-        std::vector<double> hz((size_t)sp.n * B), hrr(B), hbb(B);
+        std::vector<double> hz((size_t)nshift * B), hrr(B), hbb(B);
         std::vector<int> hit(B);
         std::vector<double> htr(d_true_rr ? B : 0);
         if (d_true_rr) cudaMemcpyAsync(htr.data(), d_true_rr, B * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1383,46 +1637,59 @@ template <int BC> struct Solve {
         cudaMemcpyAsync(hit.data(), sc.iters, B * sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_check(ctx, e, "multishift statistics");
-        double worst = 0;
-        int maxit = 0;
-        for (int j = 0; j < B; ++j) {
-            if (!(hbb[j] > 0)) continue;
-            for (int i = 0; i < sp.n; ++i)
-                worst = std::max(worst, std::fabs(hz[(size_t)i * B + j]) * std::sqrt(hrr[j] / hbb[j]));
-            maxit = std::max(maxit, hit[j]);
-        }
         float ms = 0;
         cudaEventElapsedTime(&ms, ctx->ev1, ctx->ev2);
-        out->y = y;
-        out->iterations = fixed > 0 ? fixed : maxit;
-        out->reliable_updates = nrel;
-        out->max_resid = worst;
-        out->true_resid = -1;
-        if (relpath || d_true_rr) {
-            double tr = 0;
-            for (int j = 0; j < B; ++j)
-                if (hbb[j] > 0) tr = std::max(tr, std::sqrt((d_true_rr ? htr[j] : hrr[j]) / hbb[j]));
-            out->true_resid = tr;
+        for (int l = 0; l < nl; ++l) {
+            double worst = 0, tr = 0;
+            int maxit = 0;
+            for (int j = j0[l]; j < j0[l] + Bl[l]; ++j) {
+                if (!(hbb[j] > 0)) continue;
+                for (int i = 0; i < nshift; ++i)
+                    worst = std::max(worst, std::fabs(hz[(size_t)i * B + j]) * std::sqrt(hrr[j] / hbb[j]));
+                maxit = std::max(maxit, hit[j]);
+                tr = std::max(tr, std::sqrt((d_true_rr ? htr[j] : hrr[j]) / hbb[j]));
+            }
+            SolveOut *out = in[l].out;
+            out->y = y + s0[l];
+            out->iterations = fixed > 0 ? fixed : maxit;
+            out->reliable_updates = nrel;
+            out->max_resid = worst;
+            out->true_resid = (relpath || d_true_rr) ? tr : -1;
+            out->solve_ms = ms;
         }
-        out->solve_ms = ms;
         return cuda_check(ctx, cudaGetLastError(), "multishift launch");
     }
 
-    static int run(smpq_ctx *ctx, const SolveSpec &spec, const ShiftParams &sp, double tol, int max_iter,
-                   SolveOut *out, double *hist, int hist_len, int fixed) {
-        Solve S(ctx, spec, sp);
+    // FP64 path with the true_residual option: x64 (and t64 for the final
+    // check) on the whole lattice, x64 starting at 0
+    int alloc_x64() {
+        if (!ctx->opt.true_residual || !shifts) return SMPQ_OK;
+        std::vector<Buf> &ws = ctx->ws;
+        int rc;
+        if ((rc = ensure(ctx, ws[W_XHI], nfield * sizeof(double2)))) return rc;
+        if ((rc = ensure(ctx, ws[W_T64], nfield * sizeof(double2)))) return rc;
+        x64 = (double2 *)ws[W_XHI].p;
+        cudaMemsetAsync(x64, 0, nfield * sizeof(double2), st);
+        return SMPQ_OK;
+    }
+
+    static int run(const std::vector<LatIn> &lats, double tol, int max_iter, double *hist, int hist_len, int fixed) {
+        Solve S(lats);
+        smpq_ctx *ctx = S.ctx;
         int rc = S.setup(tol, hist, hist_len);
         if (rc) return rc;
         std::vector<Buf> &ws = ctx->ws;
         const size_t nf = S.nfield;
-        const bool shifts = spec.n_sup > 0;
+        const bool shifts = S.shifts;
+        const int prec = lats[0].spec->prec;
+        const int n = S.nshift;
         cudaEventRecord(ctx->ev1, S.st);
-        if (spec.prec == SMPQ_FP64) {
+        if (prec == SMPQ_FP64) {
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(double2)))) return rc;
             if ((rc = ensure(ctx, ws[W_T], nf * sizeof(double2)))) return rc;
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(double2)))) return rc;
             if (shifts) {
-                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(double2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)n * S.nsupf * sizeof(double2)))) return rc;
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
@@ -1432,10 +1699,8 @@ template <int BC> struct Solve {
                                                   shifts ? (double2 *)ws[W_PS].p : nullptr, true, false, 0.0, fixed,
                                                   max_iter, S.x64);
             if (rc) return rc;
-            if (S.x64 && (rc = S.template true_residual<double>((double2 *)ws[W_T64].p, (double2 *)ws[W_R].p,
-                                                                 S.true_rr)))
-                return rc;
-        } else if (spec.prec == SMPQ_MIXED) {
+            if (S.x64 && (rc = S.true_residual((double2 *)ws[W_T64].p, (double2 *)ws[W_R].p, S.true_rr))) return rc;
+        } else if (prec == SMPQ_MIXED) {
             // phase 1: float-float (FP64-accurate) vectors and D_W down to the
             // switch residual; the base solution x_hi accumulates in float-float
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(df64c)))) return rc;
@@ -1443,7 +1708,7 @@ template <int BC> struct Solve {
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(df64c)))) return rc;
             if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(df64c)))) return rc;
             if (shifts) {
-                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(double2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)n * S.nsupf * sizeof(double2)))) return rc;
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
@@ -1462,7 +1727,7 @@ template <int BC> struct Solve {
             // tol.  A replacement during the phase would feed the FP32 drift of
             // the base residual into every shifted system.  The shifted
             // directions are FP32 too (ps32_phase2), y stays FP64.
-            const size_t nps = shifts ? (size_t)sp.n * S.nsupf : 0;
+            const size_t nps = shifts ? (size_t)n * S.nsupf : 0;
             const bool ps32 = ps32_phase2 && shifts;
             if ((rc = ensure(ctx, ws[W_XLO], 4 * nf * sizeof(float2) + (ps32 ? nps * sizeof(float2) : 0)))) return rc;
             float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf, *xl32 = r32 + nf,
@@ -1488,17 +1753,17 @@ template <int BC> struct Solve {
                                                      nullptr, false);
                 if (rc) return rc;
             }
-        } else if (spec.prec == SMPQ_FP16N || spec.prec == SMPQ_BF16N) {
+        } else if (prec == SMPQ_FP16N || prec == SMPQ_BF16N) {
             // p and t in the half format, the rest as in the FP32 path
-            const size_t hb = (half_field_bytes(S.V, S.B) + 255) / 256 * 256;
+            const size_t hb = (nf * 4 + nf / 12 * 4 + 255) / 256 * 256;
             if ((rc = ensure(ctx, ws[W_P], hb))) return rc;
             if ((rc = ensure(ctx, ws[W_T], hb))) return rc;
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(float2)))) return rc;
             if ((rc = ensure(ctx, ws[W_XLO], nf * sizeof(float2)))) return rc;
-            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(double2)))) return rc;
-            if ((rc = ensure(ctx, ws[W_T64], nf * sizeof(double2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(df64c)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T64], nf * sizeof(df64c)))) return rc;
             if (shifts) {
-                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(float2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)n * S.nsupf * sizeof(float2)))) return rc;
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
@@ -1506,7 +1771,7 @@ template <int BC> struct Solve {
             float2 *xl = (float2 *)ws[W_XLO].p, *ps = shifts ? (float2 *)ws[W_PS].p : nullptr;
             df64c *xh = (df64c *)ws[W_XHI].p, *t64 = (df64c *)ws[W_T64].p;
             S.relpath = true;
-            if (spec.prec == SMPQ_BF16N)
+            if (prec == SMPQ_BF16N)
                 rc = S.template phase<float, float, B16>(pp, tt, rr, xl, xh, t64, ps, true, true, 0.0, fixed, max_iter);
             else
                 rc = S.template phase<float, float, H16>(pp, tt, rr, xl, xh, t64, ps, true, true, 0.0, fixed, max_iter);
@@ -1516,45 +1781,31 @@ template <int BC> struct Solve {
             if ((rc = ensure(ctx, ws[W_T], nf * sizeof(float2)))) return rc;
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(float2)))) return rc;
             if ((rc = ensure(ctx, ws[W_XLO], nf * sizeof(float2)))) return rc;
-            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(double2)))) return rc;
-            if ((rc = ensure(ctx, ws[W_T64], nf * sizeof(double2)))) return rc;
+            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(df64c)))) return rc;
+            if ((rc = ensure(ctx, ws[W_T64], nf * sizeof(df64c)))) return rc;
             if (shifts) {
-                if ((rc = ensure(ctx, ws[W_PS], (size_t)sp.n * S.nsupf * sizeof(float2)))) return rc;
+                if ((rc = ensure(ctx, ws[W_PS], (size_t)n * S.nsupf * sizeof(float2)))) return rc;
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
             }
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
             S.relpath = true;
             rc = S.template phase<float, float>((float2 *)ws[W_P].p, (float2 *)ws[W_T].p, (float2 *)ws[W_R].p,
-                                                (float2 *)ws[W_XLO].p, (df64c *)ws[W_XHI].p,
-                                                (df64c *)ws[W_T64].p, shifts ? (float2 *)ws[W_PS].p : nullptr,
-                                                true, true, 0.0, fixed, max_iter);
+                                                (float2 *)ws[W_XLO].p, (df64c *)ws[W_XHI].p, (df64c *)ws[W_T64].p,
+                                                shifts ? (float2 *)ws[W_PS].p : nullptr, true, true, 0.0, fixed,
+                                                max_iter);
             if (rc) return rc;
         }
-        return S.finish(out, fixed, S.x64 ? S.true_rr : nullptr);
-    }
-
-    // FP64 path with the true_residual option: x64 (and t64 for the final
-    // check) on the whole lattice, x64 starting at 0
-    int alloc_x64() {
-        if (!ctx->opt.true_residual || spec.n_sup == 0) return SMPQ_OK;
-        std::vector<Buf> &ws = ctx->ws;
-        int rc;
-        if ((rc = ensure(ctx, ws[W_XHI], nfield * sizeof(double2)))) return rc;
-        if ((rc = ensure(ctx, ws[W_T64], nfield * sizeof(double2)))) return rc;
-        x64 = (double2 *)ws[W_XHI].p;
-        cudaMemsetAsync(x64, 0, nfield * sizeof(double2), st);
-        return SMPQ_OK;
+        return S.finish(fixed, S.x64 ? S.true_rr : nullptr);
     }
 };
 
-int dispatch_bc(smpq_ctx *ctx, const SolveSpec &spec, const ShiftParams &sp, double tol, int max_iter, SolveOut *out,
-                double *hist, int hist_len, int fixed) {
-    switch (spec.BC) {
-    case 1: return Solve<1>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    case 12: return Solve<12>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    case 24: return Solve<24>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    case 48: return Solve<48>::run(ctx, spec, sp, tol, max_iter, out, hist, hist_len, fixed);
-    default: return set_err(ctx, SMPQ_EINVAL, "unsupported rhs tile width");
+int dispatch_bc(const std::vector<LatIn> &lats, double tol, int max_iter, double *hist, int hist_len, int fixed) {
+    switch (lats[0].spec->BC) {
+    case 1: return Solve<1>::run(lats, tol, max_iter, hist, hist_len, fixed);
+    case 12: return Solve<12>::run(lats, tol, max_iter, hist, hist_len, fixed);
+    case 24: return Solve<24>::run(lats, tol, max_iter, hist, hist_len, fixed);
+    case 48: return Solve<48>::run(lats, tol, max_iter, hist, hist_len, fixed);
+    default: return set_err(lats[0].ctx, SMPQ_EINVAL, "unsupported rhs tile width");
     }
 }
 
@@ -1573,8 +1824,19 @@ ShiftParams make_shifts(const smpq_ctx *ctx) {
 
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out) {
     if (spec.B % spec.BC) return set_err(ctx, SMPQ_EINVAL, "rhs count must be a multiple of the tile width");
-    ShiftParams sp = spec.shifts ? *spec.shifts : make_shifts(ctx);
-    return dispatch_bc(ctx, spec, sp, ctx->opt.tol, ctx->opt.max_iter, out, nullptr, 0, 0);
+    std::vector<LatIn> lats{LatIn{ctx, &spec, spec.shifts ? *spec.shifts : make_shifts(ctx), out}};
+    return dispatch_bc(lats, ctx->opt.tol, ctx->opt.max_iter, nullptr, 0, 0);
+}
+
+int multishift_solve_batch(smpq_ctx *const *ctxs, const SolveSpec *specs, SolveOut *outs, int n) {
+    if (n < 1 || n > MAX_LAT) return set_err(ctxs[0], SMPQ_EINVAL, "a batched solve takes 1 to 4 lattices");
+    std::vector<LatIn> lats;
+    for (int l = 0; l < n; ++l) {
+        if (specs[l].B % specs[l].BC || specs[l].BC != specs[0].BC || specs[l].prec != specs[0].prec)
+            return set_err(ctxs[0], SMPQ_EINVAL, "the lattices of a batched solve need one precision and tile width");
+        lats.push_back(LatIn{ctxs[l], &specs[l], specs[l].shifts ? *specs[l].shifts : make_shifts(ctxs[l]), &outs[l]});
+    }
+    return dispatch_bc(lats, ctxs[0]->opt.tol, ctxs[0]->opt.max_iter, nullptr, 0, 0);
 }
 
 // ------------------------------------------------------------------ spectrum (Lanczos from CG coefficients)
@@ -1619,7 +1881,8 @@ int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi) {
     spec.d_src_field = (const double *)b;
     SolveOut out;
     // the counter lives in the scalar block; reset it through a fresh solve
-    rc = dispatch_bc(ctx, spec, sp, 0.0, iters, &out, hist, iters, iters);
+    std::vector<LatIn> lats{LatIn{ctx, &spec, sp, &out}};
+    rc = dispatch_bc(lats, 0.0, iters, hist, iters, iters);
     if (rc) return rc;
     std::vector<double> h(2 * (size_t)iters);
     cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
@@ -1662,6 +1925,16 @@ template <typename F> float time_launches(smpq_ctx *ctx, int reps, F once) {
     return ms / reps;
 }
 
+// the table of a single-lattice launch over the context's lattice
+Lats lats_single(smpq_ctx *ctx, const void *U, int G) {
+    Lats L{};
+    L.n = 1;
+    L.l[0].g = ctx->geom;
+    L.l[0].U = U;
+    L.l[0].G = G;
+    return L;
+}
+
 template <typename T, int BC, int NR>
 float time_pair(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part, double *alpha) {
     typedef typename cplx_t<T>::type C;
@@ -1670,16 +1943,15 @@ float time_pair(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part
     const int GN = ((V + TM::SPB - 1) / TM::SPB + tpb - 1) / tpb;
     const size_t nf = (size_t)B * 12 * V;
     C *p = (C *)buf, *t = p + nf, *r = t + nf;
-    const C *U = (const C *)Links<T>::get(ctx);
+    const Lats L = lats_single(ctx, Links<T>::get(ctx), GN);
     const T kappa = (T)ctx->opt.kappa;
     cudaStream_t st = ctx->stream;
     const dim3 gridn(GN, nchunk);
     Fuse none{}; // timing only: no scalar step
     return time_launches(ctx, reps, [&]() {
-        k_apply_a<T, BC, NR><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, U, p, t, kappa, part,
-                                                             part + (size_t)nchunk * GN * BC, GN, tpb, none);
-        k_apply_b<T, BC, NR><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, U, t, p, r, alpha, 0.0, kappa, part, GN, tpb,
-                                                             none);
+        k_apply_a<T, BC, NR, false><<<gridn, TM::THREADS, 0, st>>>(L, p, t, kappa, part,
+                                                                    part + (size_t)nchunk * GN * BC, tpb, none);
+        k_apply_b<T, BC, NR, false><<<gridn, TM::THREADS, 0, st>>>(L, t, p, r, alpha, kappa, part, tpb, none);
     });
 }
 
@@ -1694,16 +1966,15 @@ float time_pair_half(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double 
     typename HT::h2 *pv = (typename HT::h2 *)buf, *tv = (typename HT::h2 *)((char *)buf + hb);
     const HF<HT> hp{pv, (float *)(pv + nf)}, ht{tv, (float *)(tv + nf)};
     float2 *r = (float2 *)((char *)buf + 2 * hb);
-    const typename HT::h2 *Uh = (const typename HT::h2 *)HLinks<HT>::get(ctx);
+    const Lats L = lats_single(ctx, HLinks<HT>::get(ctx), GN);
     const float kappa = (float)ctx->opt.kappa;
     cudaStream_t st = ctx->stream;
     const dim3 gridn(GN, nchunk);
     Fuse none{};
     return time_launches(ctx, reps, [&]() {
-        k_apply_a_h2<HT, BC><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, Uh, hp, ht, kappa, part,
-                                                             part + (size_t)nchunk * GN * BC, GN, tpb, none);
-        k_apply_b_h2<HT, BC><<<gridn, TM::THREADS, 0, st>>>(ctx->geom, Uh, ht, hp, r, alpha, 0.0, kappa, part, GN,
-                                                             tpb, none);
+        k_apply_a_h2<HT, BC, false><<<gridn, TM::THREADS, 0, st>>>(L, hp, ht, kappa, part,
+                                                                    part + (size_t)nchunk * GN * BC, tpb, none);
+        k_apply_b_h2<HT, BC, false><<<gridn, TM::THREADS, 0, st>>>(L, ht, hp, r, alpha, kappa, part, tpb, none);
     });
 }
 

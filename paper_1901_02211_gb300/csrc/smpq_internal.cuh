@@ -158,6 +158,10 @@ struct SolveOut {
     float solve_ms = 0;
 };
 int multishift_solve(smpq_ctx *ctx, const SolveSpec &spec, SolveOut *out);
+// one solve over n (1..4) lattices of different sizes, their right-hand sides
+// in the same launches (ctxs[0] supplies stream, workspace and options; every
+// spec has the same precision and tile width and its own B, support, sources)
+int multishift_solve_batch(smpq_ctx *const *ctxs, const SolveSpec *specs, SolveOut *outs, int n);
 int lanczos_extremes(smpq_ctx *ctx, int iters, double *lo, double *hi);
 // lowmodes.cu : the k + 1 eigenpairs of H_W of smallest |lambda| (block of m
 // columns, m a multiple of 12, at most 48) into ctx->lm_*; evals / resid get
