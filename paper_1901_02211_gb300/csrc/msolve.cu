@@ -1113,6 +1113,17 @@ __global__ void __launch_bounds__(SCAL_THREADS)
 
 // ------------------------------------------------------------------ driver
 
+// p = r for every right-hand side whose base shift a residual replacement has
+// re-activated (a restart of its CG from the true residual)
+template <typename C>
+__global__ void k_restart_p(const C *__restrict__ r, C *__restrict__ p, size_t n, int BC, int V,
+                            const int *__restrict__ act_rhs) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = (int)(i / ((size_t)12 * V * BC)) * BC + (int)(i % BC); // tile layout [j/BC][V][12][BC]
+    if (act_rhs[j]) p[i] = r[i];
+}
+
 // elementwise float-float -> FP32 copy of a field (same tiled layout)
 __global__ void k_to_fp32(const df64c *__restrict__ in, float2 *__restrict__ out, size_t n) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1535,6 +1546,18 @@ template <int BC> struct Solve {
                     if (sph[l].sig[i] < sph[l].sig[base]) base = i;
                 s_rel<<<Bl[l], SCAL_THREADS, 0, st>>>(B, BC, G1[l], part2 + p0[l] * BC, scal_of(l), sph[l], tol2, base);
                 ctx->launches += 1;
+            }
+            // A replacement once every shift has converged (replace_mid = false)
+            // re-activates at most the base shift, whose true residual can then be
+            // many times the iterated one: its CG restarts from p = r (the old
+            // direction belongs to the drifted residual history).
+            if (!replace_mid && !half) {
+                for (int l = 0; l < nl; ++l) {
+                    const size_t nfl = (size_t)12 * V[l] * Bl[l];
+                    k_restart_p<C><<<(unsigned)((nfl + 255) / 256), 256, 0, st>>>(r + f0[l], p + f0[l], nfl, BC, V[l],
+                                                                                   sc.act_rhs + j0[l]);
+                    ctx->launches += 1;
+                }
             }
         };
         if (fixed > 0) {
