@@ -384,6 +384,18 @@ def run_gpu(args):
     Qp, stp = step()
     s.set_options(profile=0, true_residual=1)
     Qt, stt = step()
+    enforced = None
+    if prec == smpq.SMPQ_MIXED and sub is None and not args.no_baselines:
+        # the variant that drives the base system to a true residual below tol
+        s.set_options(true_residual=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Qe, ste = step()
+        te = time.perf_counter() - t0
+        enforced = {"value": V_step / te, "unit": "sites/s", "iterations": ste["max_iterations"],
+                    "true_resid_base": ste["true_resid"], "Q": Qe, "abs_dQ_vs_headline": abs(Qe - Q),
+                    "note": "true_residual = 2: after every shift converged, one residual replacement and a CG "
+                            "restart of the base shift until its true residual is below tol"}
     s.set_options(true_residual=0)
     B = stats[-1]["n_rhs"] // max(1, stats[-1]["n_batches"])
     peak_hbm, peak_kind = _peaks()
@@ -411,6 +423,8 @@ def run_gpu(args):
     out["spectrum"] = {"lmin2": a, "lmax2": b, "lanczos_lmin2": lo, "lanczos_lmax2": hi, "setup_s": spectrum_s,
                        "source": "GPU Lanczos (smpq_measure_spectrum, %d steps), widened 0.98/1.02" % args.lanczos}
     out["alu_peaks"] = alu
+    if enforced is not None:
+        out["mixed_base_residual_enforced"] = enforced
     out["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
     if rank == 0 and not args.no_dslash:
         out["dslash"] = _dslash_formats(s, V, B)
@@ -563,8 +577,9 @@ def _c5_record(args, dev, stream):
     (12 sources, the batch the configuration names) in FP32 with FP64
     reliable updates; the throughput is that class's sites per second scaled
     to the lattice, labelled extrapolated.  On this rough field H_W is barely
-    gapped, so the iteration cap is raised (bounded) and |Q - round Q| of the
-    class's sites is reported, not asserted."""
+    gapped (lambda^2_min about 5e-5): the iteration cap is bounded, and a solve
+    that reaches it is reported with the residual it reached.  Q of one class
+    is a partial sum over its sites, not an integer: reported, not asserted."""
     from paper_1901_02211_gb300 import smpq
     from synth import make_config
     t0 = time.perf_counter()
@@ -794,7 +809,7 @@ def main():
     ap.add_argument("--lanczos", type=int, default=300, help="Lanczos steps of the spectrum setup")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the records of the 16^3x32 and 32^3x64 configurations and of the uneven batch")
-    ap.add_argument("--c5-max-iter", type=int, default=12000, help="iteration cap of the 32^3x64 record")
+    ap.add_argument("--c5-max-iter", type=int, default=6000, help="iteration cap of the 32^3x64 record")
     ap.add_argument("--no-autotune", action="store_true",
                     help="widest RHS tile that divides the batch, without timing the candidates")
     args = ap.parse_args()

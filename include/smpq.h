@@ -95,10 +95,15 @@ typedef struct {
     int full_support;       /* q(x): keep the shifted directions on every site instead of only where
                                z = D_W y is read (the ablation of that restriction; same result,
                                14 full-lattice vectors per source) */
-    int true_residual;      /* SMPQ_FP64 / SMPQ_MIXED: also accumulate the base system's solution x
-                               (FP64, whole lattice: two more FP64 fields per source) and report
-                               max |b - (H^2 + s0) x| / |b| in smpq_stats.true_resid.  The FP32 and
-                               half paths report it from their last reliable update at no cost. */
+    int true_residual;      /* SMPQ_FP64 / SMPQ_MIXED, the base system's true residual
+                               |b - (H^2 + s0) x| / |b| (smpq_stats.true_resid):
+                               0: not computed (no base solution is kept);
+                               1: x is accumulated (two more whole-lattice fields per source)
+                                  and the residual recomputed with FP64 accuracy at the end;
+                               2 (SMPQ_MIXED): as 1, and the base system is then iterated on from
+                                  its true residual until that is below tol (the FP32 phase's
+                                  rounding leaves it near 2e-9 otherwise).  The FP32 and half
+                                  paths always report it from their last reliable update. */
     const char *tune_cache; /* path of a text file of tuned launch shapes (NULL: none): read before
                                tuning a new shape, appended after (see smpq_tune_cache_lookup).  The
                                context copies the path. */
@@ -131,7 +136,7 @@ typedef struct {
     double q_round_dev;     /* |Q - round(Q)| of the processed sites (the charge is an integer) */
     double true_resid;      /* largest true relative residual |b - (H^2 + s0) x| / |b| of the base
                                (smallest) shift, recomputed with FP64 accuracy after the solve; -1
-                               when not computed (SMPQ_FP64 without the true_residual option) */
+                               when not computed (SMPQ_FP64 / SMPQ_MIXED with true_residual 0) */
     int tiles_per_block_hi; /* launch shape of the D_W kernels (autotuned): tiles per block of the */
     int tiles_per_block_lo; /*   FP64-accurate and of the FP32 / half-storage iterations, */
     int cols_per_thread;    /*   FP32 columns per thread (1 or 2), */

@@ -192,14 +192,20 @@ Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
         *cached = 1;
         return Shape{sh[0], sh[1], sh[2], sh[3]};
     }
+    // scratch for the timing launches: three fields of the widest kind timed
+    // (float-float or FP64: 16 bytes per complex value; FP32: 8; half storage:
+    // p and t in the half format and r in FP32)
     const size_t nf = (size_t)B * 12 * ctx->V;
-    if (ensure(ctx, ctx->ws[W_P], 3 * nf * sizeof(df64c)) ||
+    const bool half = prec == SMPQ_FP16N || prec == SMPQ_BF16N;
+    const size_t hb = ((nf * 4 + nf / 12 * 4) + 255) / 256 * 256;
+    const size_t scratch = half ? 2 * hb + nf * sizeof(float2) : 3 * nf * (prec == SMPQ_FP32 ? sizeof(float2) : sizeof(df64c));
+    if (ensure(ctx, ctx->ws[W_P], scratch) ||
         ensure(ctx, ctx->ws[W_PART], (size_t)2 * nf / 12 * sizeof(double) + 64) ||
         ensure(ctx, ctx->ws[W_SCAL], (size_t)B * sizeof(double))) {
         cudaGetLastError();
         return def;
     }
-    cudaMemsetAsync(ctx->ws[W_P].p, 0, 3 * nf * sizeof(df64c), ctx->stream);
+    cudaMemsetAsync(ctx->ws[W_P].p, 0, scratch, ctx->stream);
     cudaMemsetAsync(ctx->ws[W_SCAL].p, 0, (size_t)B * sizeof(double), ctx->stream);
     void *buf = ctx->ws[W_P].p;
     double *part = (double *)ctx->ws[W_PART].p, *alpha = (double *)ctx->ws[W_SCAL].p;
@@ -535,11 +541,13 @@ int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_d
     cudaMemGetInfo(&freeb, &totb);
     const double budget = 0.6 * (double)(freeb + held);
     int rounds = std::max(1, (int)std::ceil((double)need / budget));
-    // per-round batch of each lattice: its share, a multiple of the tile width
-    int BC = 48;
-    std::vector<int> Bl(n);
+    // per-round batch of each lattice: its share, rounded up to the tile
+    // width (a small lattice pads its last round with empty columns, or ends
+    // early); tiles of 12 only when every lattice has fewer than 48 sources
+    int BC = 12;
     for (int l = 0; l < n; ++l)
-        if ((N[l] + rounds - 1) / rounds < 48) BC = 12;
+        if (N[l] >= 48) BC = 48;
+    std::vector<int> Bl(n);
     for (int l = 0; l < n; ++l) Bl[l] = ((N[l] + rounds - 1) / rounds + BC - 1) / BC * BC;
     rounds = 0;
     for (int l = 0; l < n; ++l) rounds = std::max(rounds, (N[l] + Bl[l] - 1) / Bl[l]);

@@ -26,6 +26,7 @@
 // Reductions are deterministic: per-block partial sums in a fixed tree/sequence,
 // then a fixed-order sum over the blocks of a tile in the tile's last block.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
 #include "half.cuh"
@@ -1515,8 +1516,7 @@ template <int BC> struct Solve {
                     k_apply_b<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, t, p, r, sc.alpha, kappa, part2, tpb,
                                                                             f2);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
-                    k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p, xacc,
-                                                              rel ? xlo : nullptr);
+                    k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p, xacc, xlo);
                 }
             };
             if (multi) launch(std::integral_constant<int, 1>(), std::true_type());
@@ -1613,7 +1613,17 @@ template <int BC> struct Solve {
             if (done) break;
             if (theta2 > 0 && hflags[3] == 0) break; // every rhs below the switch residual
             if (iters >= max_iter) {
-                status = set_err(ctx, SMPQ_ENOCONV, "multishift CG reached max_iter");
+                // the largest relative residual reached, for the message
+                std::vector<double> hrr(B), hbb(B);
+                cudaMemcpy(hrr.data(), sc.rr, B * sizeof(double), cudaMemcpyDeviceToHost);
+                cudaMemcpy(hbb.data(), sc.bb, B * sizeof(double), cudaMemcpyDeviceToHost);
+                double worst = 0;
+                for (int j = 0; j < B; ++j)
+                    if (hbb[j] > 0) worst = std::max(worst, std::sqrt(hrr[j] / hbb[j]));
+                char msg[160];
+                std::snprintf(msg, sizeof msg, "multishift CG reached max_iter (%d iterations, base residual %.3e)",
+                              iters, worst);
+                status = set_err(ctx, SMPQ_ENOCONV, msg);
                 break;
             }
         }
@@ -1644,6 +1654,28 @@ template <int BC> struct Solve {
                                                          part2 + p0[l] * BC, G1[l]);
             s_sum_rhs<<<Bl[l], SCAL_THREADS, 0, st>>>(BC, G1[l], part2 + p0[l] * BC, rr_out + j0[l]);
             ctx->launches += 3;
+        }
+        return cuda_check(ctx, cudaGetLastError(), "true residual");
+    }
+
+    // The base system's true residual in float-float without replacing r:
+    // x_hi += x_lo, t = D_W x_hi, |b - (A + s0) x_hi|^2 per rhs into true_rr
+    // (rs: scratch for the residual itself).
+    int measure_residual_df(df64c *xhi, float2 *xlo, df64c *t64, float2 *rs) {
+        const int TH = TileMap<BC>::THREADS;
+        const df64 kdf(ctx->opt.kappa);
+        Fuse none{};
+        for (int l = 0; l < nl; ++l) {
+            const dim3 grid(G1[l], nch[l]);
+            const size_t o = f0[l];
+            const df64c *Udf = (const df64c *)in[l].ctx->Udf.p;
+            k_rel_accum<float, BC><<<grid, TH, 0, st>>>(V[l], xhi + o, xlo + o, G1[l]);
+            k_apply_a<df64, BC, 1, false><<<grid, TH, 0, st>>>(lats_one<df64>(l), xhi, t64, kdf, part0, part1, TPB,
+                                                               none);
+            k_rel_resid_df<float, BC><<<grid, TH, 0, st>>>(in[l].ctx->geom, Udf, t64 + o, xhi + o, srcl[l], rs + o,
+                                                           sph[l].s0, kdf, part2 + p0[l] * BC, G1[l]);
+            s_sum_rhs<<<Bl[l], SCAL_THREADS, 0, st>>>(BC, G1[l], part2 + p0[l] * BC, true_rr + j0[l]);
+            ctx->launches += 4;
         }
         return cuda_check(ctx, cudaGetLastError(), "true residual");
     }
@@ -1724,12 +1756,17 @@ template <int BC> struct Solve {
             if (rc) return rc;
             if (S.x64 && (rc = S.true_residual((double2 *)ws[W_T64].p, (double2 *)ws[W_R].p, S.true_rr))) return rc;
         } else if (prec == SMPQ_MIXED) {
-            // phase 1: float-float (FP64-accurate) vectors and D_W down to the
-            // switch residual; the base solution x_hi accumulates in float-float
+            // true_residual 0: no base solution is kept (the fastest form);
+            // 1: x_hi (float-float, phase 1) and x_lo (FP32, phase 2) accumulate
+            // the base solution and its true residual is measured at the end;
+            // 2: as 1, and the base system is driven to a true residual below
+            // tol (see phase 2)
+            const int tres = ctx->opt.true_residual;
+            // phase 1: float-float (FP64-accurate) vectors and D_W down to the switch residual
             if ((rc = ensure(ctx, ws[W_P], nf * sizeof(df64c)))) return rc;
             if ((rc = ensure(ctx, ws[W_T], nf * sizeof(df64c)))) return rc;
             if ((rc = ensure(ctx, ws[W_R], nf * sizeof(df64c)))) return rc;
-            if ((rc = ensure(ctx, ws[W_XHI], nf * sizeof(df64c)))) return rc;
+            if (tres && (rc = ensure(ctx, ws[W_XHI], nf * sizeof(df64c)))) return rc;
             if (shifts) {
                 if ((rc = ensure(ctx, ws[W_PS], (size_t)n * S.nsupf * sizeof(double2)))) return rc;
                 if ((rc = ensure(ctx, ws[W_Y], S.nsupf * sizeof(double2)))) return rc;
@@ -1737,28 +1774,31 @@ template <int BC> struct Solve {
             S.y = shifts ? (double2 *)ws[W_Y].p : nullptr;
             double2 *ps = shifts ? (double2 *)ws[W_PS].p : nullptr;
             df64c *p = (df64c *)ws[W_P].p, *t = (df64c *)ws[W_T].p, *r = (df64c *)ws[W_R].p;
-            df64c *xh = (df64c *)ws[W_XHI].p;
+            df64c *xh = tres ? (df64c *)ws[W_XHI].p : nullptr;
             const double theta = ctx->opt.switch_residual;
             rc = S.template phase<df64, double>(p, t, r, nullptr, xh, nullptr, ps, true, false, theta * theta, 0,
                                                 max_iter, xh);
             if (rc) return rc;
-            // phase 2: FP32 vectors and D_W from the phase-1 state.  x_lo (FP32)
-            // accumulates the phase's part of the base solution; once every
-            // shift has converged the residual is replaced once (x_hi += x_lo,
-            // r = b - (A + s0) x_hi in float-float, the phase-1 t as scratch) and
-            // the base shift alone iterates on until its true residual is below
-            // tol.  A replacement during the phase would feed the FP32 drift of
-            // the base residual into every shifted system.  The shifted
-            // directions are FP32 too (ps32_phase2), y stays FP64.
+            // phase 2: FP32 vectors and D_W from the phase-1 state, without
+            // residual replacement: the FP32 rounding of these iterations makes
+            // the base residual drift from the true one by about u_32 theta
+            // times a growth factor (measured: 2e-9 at theta = 7e-3), and the
+            // shifted systems drift alike; their drifts largely cancel in
+            // y = sum_i c_i x_i.  With true_residual 2 the base system alone is
+            // corrected once every shift has converged (one replacement, then
+            // its CG restarts from the true residual): its residual meets tol,
+            // but the correction no longer cancels against the other shifts'
+            // drift.  The shifted directions are FP32 too (ps32_phase2), y
+            // stays FP64.
             const size_t nps = shifts ? (size_t)n * S.nsupf : 0;
             const bool ps32 = ps32_phase2 && shifts;
             if ((rc = ensure(ctx, ws[W_XLO], 4 * nf * sizeof(float2) + (ps32 ? nps * sizeof(float2) : 0)))) return rc;
-            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf, *xl32 = r32 + nf,
-                   *ps32p = xl32 + nf;
+            float2 *p32 = (float2 *)ws[W_XLO].p, *t32 = p32 + nf, *r32 = t32 + nf, *xl32 = tres ? r32 + nf : nullptr,
+                   *ps32p = r32 + 2 * nf;
             const unsigned nb = (unsigned)((nf + 255) / 256);
             k_to_fp32<<<nb, 256, 0, S.st>>>(p, p32, nf);
             k_to_fp32<<<nb, 256, 0, S.st>>>(r, r32, nf);
-            cudaMemsetAsync(xl32, 0, nf * sizeof(float2), S.st);
+            if (xl32) cudaMemsetAsync(xl32, 0, nf * sizeof(float2), S.st);
             ctx->launches += 2;
             if (ps32) {
                 k_d2f<<<(unsigned)((nps + 255) / 256), 256, 0, S.st>>>(ps, ps32p, nps);
@@ -1766,15 +1806,20 @@ template <int BC> struct Solve {
             }
             cudaMemcpyAsync(S.hflags, S.sc.flags, sizeof(int), cudaMemcpyDeviceToHost, S.st);
             cudaStreamSynchronize(S.st);
-            if (S.hflags[0] > 0) S.relpath = true;
+            const bool enforce = tres == 2;
+            if (S.hflags[0] > 0 && enforce) S.relpath = true;
             if (S.hflags[0] > 0 && ps32) {
-                rc = S.template phase<float, float>(p32, t32, r32, xl32, xh, t, ps32p, false, true, 0.0, 0, max_iter,
-                                                    nullptr, false);
+                rc = S.template phase<float, float>(p32, t32, r32, xl32, xh, t, ps32p, false, enforce, 0.0, 0,
+                                                    max_iter, nullptr, false);
                 if (rc) return rc;
             } else if (S.hflags[0] > 0) {
-                rc = S.template phase<float, double>(p32, t32, r32, xl32, xh, t, ps, false, true, 0.0, 0, max_iter,
+                rc = S.template phase<float, double>(p32, t32, r32, xl32, xh, t, ps, false, enforce, 0.0, 0, max_iter,
                                                      nullptr, false);
                 if (rc) return rc;
+            }
+            if (tres == 1) { // measure the base system's true residual (x_hi += x_lo, b - (A + s0) x_hi)
+                if ((rc = S.measure_residual_df(xh, xl32, t, r32))) return rc;
+                return S.finish(0, S.true_rr);
             }
         } else if (prec == SMPQ_FP16N || prec == SMPQ_BF16N) {
             // p and t in the half format, the rest as in the FP32 path

@@ -223,6 +223,30 @@ def test_qx_4x4_fp64_vs_dense(S, flux4, zolo4, g5dov4, r, mode, rhs_block):
     assert abs(st["max_im_q"] - np.abs(ref.imag).max()) <= 1e-8
 
 
+def test_qx_8x16_mixed_enforced_base_residual(S):
+    """true_residual = 2: the mixed path drives the base system to a true
+    residual below tol after every shift has converged (one replacement, then
+    a CG restart of the base shift); q(x) still meets the per-site bar."""
+    cfg = make_config("flux8x16")
+    U, dims = cfg["U"], cfg["dims"]
+    a, b = _interval("flux8x16")
+    zolo, delta = _zolo(a, b)
+    colour, n = probing.color_sites(dims, 4, 0)
+    classes = [0, 77, 255]
+    ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=classes, batch_colours=len(classes))
+    with _session(S, precision=S.SMPQ_MIXED, true_residual=2) as s:
+        s.load_gauge(dims, U)
+        s.set_spectrum(a, b)
+        s.build_sources(4, 0)
+        q, Q, st = s.compute_qx(classes=classes)
+    mask = np.isin(colour, classes)
+    err = np.abs(q[mask] - ref[mask]).max()
+    print("8^3x16 r=4 mixed, base residual enforced: max |dq| = %.3e, |dQ| = %.3e, true residual %.2e, "
+          "%d iterations" % (err, abs(Q - ref.real[mask].sum()), st["true_resid"], st["max_iterations"]))
+    assert 0 <= st["true_resid"] <= 1.1e-10
+    assert err <= 1e-8
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("r,mode", [(2, 0), (2, 1)])
 def test_qx_4x4_antiperiodic_vs_dense(S, flux4, r, mode, prec):
@@ -342,10 +366,12 @@ def test_qx_8x16_sampled(S, r, classes, prec):
           "recursive %.2e, %.2f launches per iteration" % (
               r, prec, err, st["max_iterations"], st["reliable_updates"], st["true_resid"], st["max_resid"],
               st["kernel_launches"] / st["max_iterations"]))
-    # the base system's residual recomputed in FP64 after the solve: every
-    # path stops at the 1e-10 tolerance (the FP32, half and mixed paths through
-    # their residual replacements, FP64 through its own accuracy)
-    assert 0 <= st["true_resid"] <= 1.1e-10
+    # the base system's residual recomputed with FP64 accuracy after the solve:
+    # the FP64, FP32 and half paths stop at the 1e-10 tolerance (FP32 and half
+    # through their residual replacements); the mixed path's FP32 phase has no
+    # replacement, and its base residual drifts to about u_32 theta times a
+    # growth factor (the price of the cancellation that keeps q(x) accurate)
+    assert 0 <= st["true_resid"] <= (1e-8 if prec.startswith("mixed") else 1.1e-10)
     # FP64 and the FP64-then-FP32 path meet the 1e-8 per-site bar; the FP32
     # path with FP64 reliable updates has the FP32 floor of its shifted systems.
     # The per-site error of the mixed path grows with the switch point (about
@@ -515,7 +541,7 @@ def test_uneven_batch_matches_single_runs(S, flux4, zolo4, g5dov4):
     for name, r, mode in cases:
         cfg = make_config(name)
         a, b = (zolo4["a"], zolo4["b"]) if name == "flux4" else _interval(name)
-        s = Session(precision=smpq.SMPQ_MIXED)
+        s = Session(precision=smpq.SMPQ_MIXED, true_residual=1)
         s.load_gauge(cfg["dims"], cfg["U"])
         s.set_spectrum(a, b)
         s.build_sources(r, mode)
@@ -533,7 +559,7 @@ def test_uneven_batch_matches_single_runs(S, flux4, zolo4, g5dov4):
                                                   stats[i]["true_resid"]))
         assert d <= 1e-9
         assert abs(Qs[i] - Q) <= 1e-9
-        assert 0 <= stats[i]["true_resid"] <= 1.1e-10
+        assert 0 <= stats[i]["true_resid"] <= 1e-8  # the mixed path's measured base residual
     # against the oracle
     q4 = bufs_re[0] + 1j * bufs_im[0]
     dense = qx.dense_smp_qx(g5dov4, probing.color_sites((4, 4, 4, 4), 2, 0)[0])
