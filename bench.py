@@ -270,10 +270,11 @@ def _kernel_table(prec, stats, V, B, peak_hbm, peak_kind, alu):
     b_vecs = 6 if prec == smpq.SMPQ_FP32 else 4  # t, p, r (+ x_lo) read, r (+ x_lo) written
     half = prec in (smpq.SMPQ_FP16N, smpq.SMPQ_BF16N)
     lo = {smpq.SMPQ_FP16N: "fp16n", smpq.SMPQ_BF16N: "bf16n"}.get(prec, "fp32")
+    st_ = "_st" if stats[-1].get("staged") and lo == "fp32" else ""  # neighbours staged in shared memory
     kern = {}
     for key, ms_k, n_k, esz_k, nvec in (
-            ("k_apply_a[%s]" % lo, "dslash_ms", "dslash_launches", 8, 2),
-            ("k_apply_b[%s]" % lo, "update_ms", "update_launches", 8, b_vecs),
+            ("k_apply_a%s[%s]" % (st_, lo), "dslash_ms", "dslash_launches", 8, 2),
+            ("k_apply_b%s[%s]" % (st_, lo), "update_ms", "update_launches", 8, b_vecs),
             ("k_apply_a[fp64-accurate]", "dslash_hi_ms", "dslash_hi_launches", 16, 2),
             ("k_apply_b[fp64-accurate]", "update_hi_ms", "update_hi_launches", 16, 4)):
         tot = sum(x[ms_k] for x in stats)
@@ -366,9 +367,13 @@ def run_gpu(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
+        # the NVTX range names the timed steps for a profiler's launch list
+        # (ncu --nvtx --nvtx-include smpq_timed_steps/)
+        torch.cuda.nvtx.range_push("smpq_timed_steps")
         for _ in range(args.steps):
             Q, st = step()
             stats.append(st)
+        torch.cuda.nvtx.range_pop()
         e1.record()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
@@ -377,6 +382,7 @@ def run_gpu(args):
     value = ws * V_step / (ms / 1000.0)
     clocks = clk.summary()
     launches = sum(x["kernel_launches"] for x in stats)
+    q_out = {"headline": (q_re + 1j * q_im).cpu().numpy()} if sub is None else {}
 
     # one more step with CUDA events around every D_W launch (graphs off): the
     # kernel times of the roofline; then one with the FP64 true residual
@@ -392,6 +398,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         Qe, ste = step()
         te = time.perf_counter() - t0
+        q_out["mixed_base_residual_enforced"] = (q_re + 1j * q_im).cpu().numpy()
         enforced = {"value": V_step / te, "unit": "sites/s", "iterations": ste["max_iterations"],
                     "true_resid_base": ste["true_resid"], "Q": Qe, "abs_dQ_vs_headline": abs(Qe - Q),
                     "note": "true_residual = 2: after every shift converged, one residual replacement and a CG "
@@ -410,7 +417,7 @@ def run_gpu(args):
         pass
     else:
         e2e_val = _e2e(args, s, dims, U, V, a, b, prec, dev, stream, ws)
-    out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream) if rank == 0 else {}
+    out = _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream, q_out) if rank == 0 else {}
     if rank == 0 and not args.no_extra:
         out["uneven_batch"] = {"bf16n": _uneven(args, smpq.SMPQ_BF16N, dev, stream),
                                "mixed": _uneven(args, smpq.SMPQ_MIXED, dev, stream)}
@@ -444,11 +451,15 @@ def _dslash_formats(s, V, B, reps=20):
     from paper_1901_02211_gb300 import smpq
     peak, kind = _peaks()
     res = {"columns": B, "reps": reps, "peak": peak, "peak_source": kind, "unit": "GB/s"}
-    for name, prec in (("fp16n_recon12", smpq.SMPQ_FP16N), ("bf16n_recon12", smpq.SMPQ_BF16N),
-                       ("fp32", smpq.SMPQ_FP32), ("fp64", smpq.SMPQ_FP64)):
+    staging = s.options.staging
+    for name, prec, stg in (("fp16n_recon12", smpq.SMPQ_FP16N, staging), ("bf16n_recon12", smpq.SMPQ_BF16N, staging),
+                            ("fp32", smpq.SMPQ_FP32, 1), ("fp32_unstaged", smpq.SMPQ_FP32, 0),
+                            ("fp64", smpq.SMPQ_FP64, staging)):
+        s.set_options(staging=stg)  # FP32: neighbours staged in shared memory, or plain loads
         ms, nbytes = smpq.smpq_time_dslash(s.ctx, B, False, prec, reps)
         gbs = nbytes / (ms / 1000.0) / 1e9
         res[name] = {"avg_launch_ms": ms, "algorithmic_bytes": nbytes, "achieved": gbs, "frac": gbs / peak}
+    s.set_options(staging=staging)
     return res
 
 
@@ -635,11 +646,16 @@ def _uneven(args, prec, dev, stream):
                       "them; sources in rounds sized to device memory; GPU Lanczos intervals (setup)"}
 
 
-def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
+def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream, q_out=None):
+    """Comparison paths on the same GPU.  fp64_batched runs every class: its
+    q(x) on the whole lattice is the FP64 reference that the other paths' q(x)
+    and Q are compared with (q_out: name -> whole-lattice q(x) of the timed
+    path and its variants)."""
     import torch
 
     from paper_1901_02211_gb300 import Session, smpq
     out = {}
+    q32 = None
     if not args.no_baselines:
         # FP64 one-source-at-a-time path and FP64 batched path on a sample of classes
         sample = list(range(0, n_classes, n_classes // 2))[:2]
@@ -652,7 +668,7 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
             s3.compute_qx()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            q, Qs, st3 = s3.compute_qx()
+            q32, Qs, st3 = s3.compute_qx()
             dt = time.perf_counter() - t0
             s3.close()
             out["fp32_reliable"] = {"value": V / dt, "unit": "sites/s", "extrapolated": False,
@@ -665,7 +681,7 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
             s3.load_gauge(dims, U)
             s3.set_spectrum(a, b)
             s3.build_sources(args.rmin, MODE)
-            cls = sample if blk == 1 else list(range(0, n_classes, 8))
+            cls = sample if blk == 1 else list(range(n_classes))
             s3.compute_qx(classes=cls[:1])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -673,9 +689,19 @@ def _baselines(args, rank, dims, U, V, a, b, n_classes, dev, stream):
             dt = time.perf_counter() - t0
             s3.close()
             per_class = dt / len(cls)
-            out[key] = {"value": V / (per_class * n_classes), "unit": "sites/s", "extrapolated": True,
+            full = len(cls) == n_classes
+            out[key] = {"value": V / (per_class * n_classes), "unit": "sites/s", "extrapolated": not full,
                         "sample": "%d of %d classes (%d sources), %.3f s" % (len(cls), n_classes, 12 * len(cls), dt),
                         "max_iterations": st3["max_iterations"]}
+            if full:
+                # the whole lattice in FP64: the reference for the other paths' q(x) and Q
+                out[key]["Q"] = Qs
+                cmp = dict(q_out or {})
+                if q32 is not None:
+                    cmp["fp32_reliable"] = q32
+                out[key]["vs_fp64_whole_lattice"] = {
+                    name: {"max_abs_dq": float(np.abs(qq - q).max()),
+                           "abs_dQ": abs(float(qq.real.sum() - q.real.sum()))} for name, qq in cmp.items()}
         # ablation of the star support: the shifted directions on every site
         # (14 full-lattice vectors per source) against the restricted path, on
         # the same sample of classes and in the same precision
@@ -776,7 +802,10 @@ def _report(args, ws, V, ms, value, prec, B, esz, clocks, e2e_val, U, launches, 
                    "Q": st["Q"], "abs_Q_minus_round": st["q_round_dev"], "max_im_q": st["max_im_q"],
                    "profiled_step_ms": stp["total_ms"], "timed_step_ms": ms,
                    "kernel_ms_per_step": {kk: v["share_ms"] for kk, v in kern.items()},
-                   "kernel_avg_launch_ms": {kk: v["ms"] for kk, v in kern.items()}},
+                   "kernel_avg_launch_ms": {kk: v["ms"] for kk, v in kern.items()},
+                   "launch_shape": {"rhs_tile": st["rhs_tile"], "tiles_per_block_hi": st["tiles_per_block_hi"],
+                                    "tiles_per_block_lo": st["tiles_per_block_lo"],
+                                    "cols_per_thread": st["cols_per_thread"], "staged_fp32": st["staged"]}},
     }
     if sub is not None:
         line["config"]["workload"] += " (profiling subset: first %d classes)" % len(sub)

@@ -102,11 +102,17 @@ typedef struct {
                                   and the residual recomputed with FP64 accuracy at the end;
                                2 (SMPQ_MIXED): as 1, and the base system is then iterated on from
                                   its true residual until that is below tol (the FP32 phase's
-                                  rounding leaves it near 2e-9 otherwise).  The FP32 and half
+                                  rounding leaves it at a few times 1e-8 otherwise, at the
+                                  default switch_residual).  The FP32 and half
                                   paths always report it from their last reliable update. */
     const char *tune_cache; /* path of a text file of tuned launch shapes (NULL: none): read before
                                tuning a new shape, appended after (see smpq_tune_cache_lookup).  The
                                context copies the path. */
+    int staging;            /* FP32 D_W launches (SMPQ_FP32 and the second phase of SMPQ_MIXED) with
+                               the neighbour sites staged in shared memory by bulk asynchronous
+                               copies, one column per thread: -1 the autotuner chooses (staged when
+                               autotune is 0), 0 never, 1 always (RHS tiles of 12 columns or more).
+                               The stand-alone FP32 D_W of smpq_time_dslash stages unless this is 0. */
 } smpq_options;
 
 typedef struct {
@@ -140,13 +146,16 @@ typedef struct {
     int tiles_per_block_hi; /* launch shape of the D_W kernels (autotuned): tiles per block of the */
     int tiles_per_block_lo; /*   FP64-accurate and of the FP32 / half-storage iterations, */
     int cols_per_thread;    /*   FP32 columns per thread (1 or 2), */
-    int shape_from_cache;   /*   1 if the shape came from the tune_cache file */
+    int shape_from_cache;   /*   1 if the shape came from the tune_cache file, */
+    int staged;             /*   1 if the FP32 D_W launches staged the neighbour sites in shared
+                                 memory (bulk asynchronous copies; one column per thread) */
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
  * 10 iterations per check, graphs on, profiling off, switch_residual 7e-3,
- * autotuning on, no true-residual accumulation, no tuning cache file. */
+ * autotuning on, no true-residual accumulation, no tuning cache file, staging
+ * chosen by the autotuner (-1). */
 int smpq_options_default(smpq_options *opt);
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t, e.g.
@@ -311,20 +320,21 @@ int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, d
 /* The autotuner's cache file (host only; not part of the paper's method).
  * A shape is {RHS tile width (1, 12, 24, 48), tiles per block of the
  * FP64-accurate D_W launches, tiles per block of the FP32 / half-storage ones,
- * FP32 columns per thread (1, 2)}, keyed by a device string (as the library
- * writes it: "<name>/<SMs>sm"), the lattice dims, the batch B and the
- * precision.  One line per entry:
- *   smpq-tune-1|<device>|<nx> <ny> <nz> <nt>|<B>|<precision>|<bc> <tpb_hi> <tpb_lo> <nr>|<ms>
- * lookup: SMPQ_OK and shape[4] filled from the last matching well-formed line,
+ * FP32 columns per thread (1, 2), FP32 neighbours staged in shared memory (0,
+ * 1; 1 only with one column)}, keyed by a device string (as the library writes
+ * it: "<name>/<SMs>sm"), the lattice dims, the batch B and the precision.  One
+ * line per entry:
+ *   smpq-tune-2|<device>|<nx> <ny> <nz> <nt>|<B>|<precision>|<bc> <tpb_hi> <tpb_lo> <nr> <staged>|<ms>
+ * lookup: SMPQ_OK and shape[5] filled from the last matching well-formed line,
  * SMPQ_ESTATE if the file is missing or has no such line, SMPQ_EINVAL for
  * NULL arguments.  store: appends one line (ms = the tuner's estimate per
  * iteration pair); SMPQ_EINVAL if the file cannot be opened or the device
  * string holds '|' or a newline.  Neither call takes a lock: processes that
  * tune the same shape at once both append, and the last line wins. */
 int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[4], int B, int precision,
-                           int shape[4]);
+                           int shape[5]);
 int smpq_tune_cache_store(const char *path, const char *device, const int dims[4], int B, int precision,
-                          const int shape[4], double ms);
+                          const int shape[5], double ms);
 
 /* Measured arithmetic peak of GPU `device` (not part of the paper's method: the
  * denominator of the ALU rooflines the solver's FP64-accurate kernels are

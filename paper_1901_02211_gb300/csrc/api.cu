@@ -120,6 +120,7 @@ int validate_options(smpq_ctx *ctx, const smpq_options *o) {
     if (o->rhs_block < 0 || (o->rhs_block > 1 && o->rhs_block % 12))
         return set_err(ctx, SMPQ_EINVAL, "rhs_block must be 0, 1 or a multiple of 12");
     if (o->iters_per_check < 1) return set_err(ctx, SMPQ_EINVAL, "iters_per_check must be positive");
+    if (o->staging < -1 || o->staging > 1) return set_err(ctx, SMPQ_EINVAL, "staging must be -1, 0 or 1");
     return SMPQ_OK;
 }
 
@@ -144,7 +145,7 @@ void set_geom(smpq_ctx *ctx) {
 // of every candidate on the solver's own workspace; kept in the context and,
 // with opt.tune_cache set, in a text file that later processes read first.
 struct Shape {
-    int bc, tpb_hi, tpb_lo, nr;
+    int bc, tpb_hi, tpb_lo, nr, staged;
 };
 constexpr int TPB_DEFAULT = 4; // tiles per block of the lattice kernels (msolve.cu)
 
@@ -158,7 +159,7 @@ std::string device_key(int dev) {
 }
 
 std::string cache_key(const char *device, const int dims[4], int B, int precision) {
-    return std::string("smpq-tune-1|") + device + "|" + std::to_string(dims[0]) + " " + std::to_string(dims[1]) +
+    return std::string("smpq-tune-2|") + device + "|" + std::to_string(dims[0]) + " " + std::to_string(dims[1]) +
            " " + std::to_string(dims[2]) + " " + std::to_string(dims[3]) + "|" + std::to_string(B) + "|" +
            std::to_string(precision) + "|";
 }
@@ -167,30 +168,32 @@ int tune_kind_lo(int prec) {
     return prec == SMPQ_FP64 ? 0 : prec == SMPQ_FP16N ? 3 : prec == SMPQ_BF16N ? 4 : 1;
 }
 
-Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
+Shape tune_shape_raw(smpq_ctx *ctx, int B, int prec, int *cached) {
     *cached = 0;
-    Shape def{1, TPB_DEFAULT, TPB_DEFAULT, 1};
+    Shape def{1, TPB_DEFAULT, TPB_DEFAULT, 1, 0};
     if (B == 1) return def;
     std::vector<int> cand;
     for (int bc : {12, 24, 48})
         if (B % bc == 0) cand.push_back(bc);
     if (cand.empty()) return def;
     def.bc = cand.back();
+    const int kind_lo = tune_kind_lo(prec);
+    def.staged = kind_lo == 1 && ctx->opt.staging != 0 ? 1 : 0; // FP32 iterations: staged neighbours
     if (!ctx->opt.autotune) return def;
     for (auto &e : ctx->tuned)
         if (e.dims == std::array<int, 4>{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]} && e.B == B &&
             e.prec == prec) {
             *cached = e.from_file;
-            return Shape{e.shape[0], e.shape[1], e.shape[2], e.shape[3]};
+            return Shape{e.shape[0], e.shape[1], e.shape[2], e.shape[3], e.shape[4]};
         }
     const std::string dev = device_key(ctx->device);
-    int sh[4];
+    int sh[5];
     if (!ctx->tune_cache.empty() &&
         smpq_tune_cache_lookup(ctx->tune_cache.c_str(), dev.c_str(), ctx->dims, B, prec, sh) == SMPQ_OK &&
         B % sh[0] == 0) {
-        ctx->tuned.push_back({{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]}, B, prec, {sh[0], sh[1], sh[2], sh[3]}, 1});
+        ctx->tuned.push_back({{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]}, B, prec, {sh[0], sh[1], sh[2], sh[3], sh[4]}, 1});
         *cached = 1;
-        return Shape{sh[0], sh[1], sh[2], sh[3]};
+        return Shape{sh[0], sh[1], sh[2], sh[3], sh[4]};
     }
     // scratch for the timing launches: three fields of the widest kind timed
     // (float-float or FP64: 16 bytes per complex value; FP32: 8; half storage:
@@ -201,39 +204,44 @@ Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
     const size_t scratch = half ? 2 * hb + nf * sizeof(float2) : 3 * nf * (prec == SMPQ_FP32 ? sizeof(float2) : sizeof(df64c));
     if (ensure(ctx, ctx->ws[W_P], scratch) ||
         ensure(ctx, ctx->ws[W_PART], (size_t)2 * nf / 12 * sizeof(double) + 64) ||
-        ensure(ctx, ctx->ws[W_SCAL], (size_t)B * sizeof(double))) {
+        ensure(ctx, ctx->ws[W_SCAL], (size_t)B * sizeof(double) + 16)) {
         cudaGetLastError();
         return def;
     }
     cudaMemsetAsync(ctx->ws[W_P].p, 0, scratch, ctx->stream);
-    cudaMemsetAsync(ctx->ws[W_SCAL].p, 0, (size_t)B * sizeof(double), ctx->stream);
+    cudaMemsetAsync(ctx->ws[W_SCAL].p, 0, (size_t)B * sizeof(double) + 16, ctx->stream);
     void *buf = ctx->ws[W_P].p;
     double *part = (double *)ctx->ws[W_PART].p, *alpha = (double *)ctx->ws[W_SCAL].p;
-    const int kind_lo = tune_kind_lo(prec);
+    int *err = (int *)(alpha + B); // staging-wait flag of the staged timings
     const bool mixed = prec == SMPQ_MIXED, fp64 = prec == SMPQ_FP64;
     Shape best = def;
     float tbest = 1e30f;
     for (int bc : cand) {
-        Shape s{bc, 4, 4, 1};
+        Shape s{bc, 4, 4, 1, 0};
         float tlo = 1e30f, thi = 0.f;
         // the FP32 / half / FP64 iterations (FP64 runs with the tiles-per-block
-        // of the FP64-accurate iterations)
+        // of the FP64-accurate iterations); FP32 also with staged neighbours
         for (int tpb : {1, 2, 4, 8})
-            for (int nr : {1, 2}) {
-                if (nr == 2 && kind_lo != 1) continue;
-                const float t = time_dslash_pair(ctx, kind_lo, B, bc, tpb, nr, fp64 ? 2 : 3, buf, part, alpha);
+            for (int v : {0, 1, 2}) { // 0, 1: one or two columns per thread; 2: staged
+                if (v > 0 && kind_lo != 1) continue;
+                if (kind_lo == 1 && ((v == 2 && ctx->opt.staging == 0) || (v < 2 && ctx->opt.staging == 1)))
+                    continue;
+                const int nr = v == 1 ? 2 : 1;
+                const float t = time_dslash_pair(ctx, v == 2 ? 5 : kind_lo, B, bc, tpb, nr, fp64 ? 2 : 3, buf, part,
+                                                 alpha, err);
                 ctx->launches += 2 * (1 + (fp64 ? 2 : 3));
                 if (t > 0 && t < tlo) {
                     tlo = t;
                     if (fp64) s.tpb_hi = tpb;
                     else s.tpb_lo = tpb;
                     s.nr = nr;
+                    s.staged = v == 2 ? 1 : 0;
                 }
             }
         if (mixed) { // the float-float iterations: about a fifth of the solve
             float th = 1e30f;
             for (int tpb : {1, 2, 4, 8}) {
-                const float t = time_dslash_pair(ctx, 2, B, bc, tpb, 1, 2, buf, part, alpha);
+                const float t = time_dslash_pair(ctx, 2, B, bc, tpb, 1, 2, buf, part, alpha, err);
                 ctx->launches += 6;
                 if (t > 0 && t < th) {
                     th = t;
@@ -250,12 +258,24 @@ Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
     }
     cudaGetLastError();
     ctx->tuned.push_back({{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]}, B, prec,
-                          {best.bc, best.tpb_hi, best.tpb_lo, best.nr}, 0});
+                          {best.bc, best.tpb_hi, best.tpb_lo, best.nr, best.staged}, 0});
     if (!ctx->tune_cache.empty()) {
-        const int shape[4] = {best.bc, best.tpb_hi, best.tpb_lo, best.nr};
+        const int shape[5] = {best.bc, best.tpb_hi, best.tpb_lo, best.nr, best.staged};
         smpq_tune_cache_store(ctx->tune_cache.c_str(), dev.c_str(), ctx->dims, B, prec, shape, tbest);
     }
     return best;
+}
+
+// the tuned (or cached, or default) shape with the staging option applied
+Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
+    Shape s = tune_shape_raw(ctx, B, prec, cached);
+    if (tune_kind_lo(prec) != 1 || s.bc < 12 || ctx->opt.staging == 0) {
+        s.staged = 0;
+    } else if (ctx->opt.staging == 1) {
+        s.staged = 1;
+        s.nr = 1;
+    }
+    return s;
 }
 
 // device bytes one right-hand side costs in the solver (full-lattice vectors)
@@ -345,6 +365,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
     spec.tpb_hi = shape.tpb_hi;
     spec.tpb_lo = shape.tpb_lo;
     spec.nr = shape.nr;
+    spec.staged = shape.staged;
     ShiftParams cg; // kind 1: one unshifted system D_W^dag D_W x = D_W^dag b, y = x
     if (kind == 1) {
         cg.n = 1;
@@ -483,6 +504,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->tiles_per_block_lo = shape.tpb_lo;
         stats->cols_per_thread = shape.nr;
         stats->shape_from_cache = from_cache;
+        stats->staged = shape.staged && (prec == SMPQ_FP32 || prec == SMPQ_MIXED) && BC > 1;
         stats->solve_ms = solve_ms;
         stats->total_ms = tms;
         stats->kernel_launches = ctx->launches;
@@ -553,10 +575,11 @@ int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_d
     for (int l = 0; l < n; ++l) rounds = std::max(rounds, (N[l] + Bl[l] - 1) / Bl[l]);
     int Btot = 0;
     for (int l = 0; l < n; ++l) Btot += Bl[l];
-    // launch shape: the default tiles per block, one column per thread (timing
-    // candidates would need scratch the size of the round again)
+    // launch shape: the default tiles per block, one column per thread, FP32
+    // iterations with staged neighbours (timing candidates would need scratch
+    // the size of the round again)
     const int from_cache = 0;
-    const Shape shape{BC, TPB_DEFAULT, TPB_DEFAULT, 1};
+    const Shape shape{BC, TPB_DEFAULT, TPB_DEFAULT, 1, tune_kind_lo(prec) == 1 && c0->opt.staging != 0 ? 1 : 0};
     // global per-rhs tables (support class, source component, source class) in the first context
     if ((rc = ensure(c0, c0->ws[W_RHS], (size_t)3 * Btot * sizeof(int)))) return rc;
     int *d_rhs_class = (int *)c0->ws[W_RHS].p, *d_src_comp = d_rhs_class + Btot, *d_src_class = d_src_comp + Btot;
@@ -592,6 +615,7 @@ int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_d
             sp.tpb_hi = shape.tpb_hi;
             sp.tpb_lo = shape.tpb_lo;
             sp.nr = 1;
+            sp.staged = shape.staged;
             j0 += Bl[l];
         }
         cudaMemcpyAsync(d_rhs_class, h_rhs.data(), h_rhs.size() * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -668,6 +692,7 @@ int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_d
             sx.tiles_per_block_lo = shape.tpb_lo;
             sx.cols_per_thread = 1;
             sx.shape_from_cache = from_cache;
+            sx.staged = shape.staged;
         }
     }
     cudaEventRecord(c0->evB, st);
@@ -701,11 +726,12 @@ int smpq_options_default(smpq_options *o) {
     o->profile = 0;
     o->switch_residual = 7e-3;
     o->autotune = 1;
+    o->staging = -1;
     return SMPQ_OK;
 }
 
 int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[4], int B, int precision,
-                           int shape[4]) {
+                           int shape[5]) {
     if (!path || !device || !dims || !shape || B < 1) return SMPQ_EINVAL;
     FILE *f = std::fopen(path, "r");
     if (!f) return SMPQ_ESTATE;
@@ -714,12 +740,12 @@ int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[
     int rc = SMPQ_ESTATE;
     while (std::fgets(line, sizeof line, f)) {
         if (std::strncmp(line, key.c_str(), key.size()) != 0) continue;
-        int v[4];
+        int v[5];
         double ms;
-        if (std::sscanf(line + key.size(), "%d %d %d %d|%lf", &v[0], &v[1], &v[2], &v[3], &ms) == 5 &&
+        if (std::sscanf(line + key.size(), "%d %d %d %d %d|%lf", &v[0], &v[1], &v[2], &v[3], &v[4], &ms) == 6 &&
             (v[0] == 1 || v[0] == 12 || v[0] == 24 || v[0] == 48) && v[1] >= 1 && v[1] <= 64 && v[2] >= 1 &&
-            v[2] <= 64 && (v[3] == 1 || v[3] == 2)) {
-            std::copy(v, v + 4, shape); // the last matching line wins
+            v[2] <= 64 && (v[3] == 1 || v[3] == 2) && (v[4] == 0 || (v[4] == 1 && v[3] == 1))) {
+            std::copy(v, v + 5, shape); // the last matching line wins
             rc = SMPQ_OK;
         }
     }
@@ -728,13 +754,13 @@ int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[
 }
 
 int smpq_tune_cache_store(const char *path, const char *device, const int dims[4], int B, int precision,
-                          const int shape[4], double ms) {
+                          const int shape[5], double ms) {
     if (!path || !device || !dims || !shape || B < 1 || std::strchr(device, '|') || std::strchr(device, '\n'))
         return SMPQ_EINVAL;
     FILE *f = std::fopen(path, "a");
     if (!f) return SMPQ_EINVAL;
     const std::string key = cache_key(device, dims, B, precision);
-    std::fprintf(f, "%s%d %d %d %d|%.6g\n", key.c_str(), shape[0], shape[1], shape[2], shape[3], ms);
+    std::fprintf(f, "%s%d %d %d %d %d|%.6g\n", key.c_str(), shape[0], shape[1], shape[2], shape[3], shape[4], ms);
     std::fclose(f);
     return SMPQ_OK;
 }
@@ -785,6 +811,7 @@ int smpq_destroy(smpq_ctx *ctx) {
         release(ctx->U64);
         release(ctx->U32);
         release(ctx->Udf);
+        release(ctx->d_err);
         release(ctx->Uh16);
         release(ctx->Ub16);
         release(ctx->d_colour);
@@ -1086,9 +1113,20 @@ int smpq_time_dslash(smpq_ctx *ctx, int B, int dagger, int precision, int reps, 
     // the FP64 / FP32 tile: the widest of 48, 12 and 1 that divides B
     const int BC = B % 48 == 0 ? 48 : (B % 12 == 0 ? 12 : 1);
     const void *U = dslash_links(ctx, precision);
+    // FP32 on tiles of 12 or more columns: the neighbour sites staged in shared memory
+    const bool staged = precision == SMPQ_FP32 && BC >= 12 && ctx->opt.staging != 0;
+    if (staged) {
+        if ((rc = ensure(ctx, ctx->d_err, 16))) return rc;
+        cudaMemsetAsync(ctx->d_err.p, 0, 16, st);
+    }
+    cudaError_t le = cudaSuccess;
     auto launch = [&]() {
         if (precision == SMPQ_FP64) launch_dslash<double>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
-        else if (precision == SMPQ_FP32) launch_dslash<float>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
+        else if (staged) {
+            const cudaError_t e = launch_dslash_staged(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa,
+                                                       (int *)ctx->d_err.p, st);
+            if (e != cudaSuccess) le = e;
+        } else if (precision == SMPQ_FP32) launch_dslash<float>(ctx->geom, U, tin, tout, B, BC, dagger, ctx->opt.kappa, st);
         else launch_dslash_half(precision, ctx->geom, U, tin, tout, B, dagger, ctx->opt.kappa, st);
     };
     launch();
@@ -1098,7 +1136,13 @@ int smpq_time_dslash(smpq_ctx *ctx, int B, int dagger, int precision, int reps, 
     cudaEventRecord(ctx->ev2, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "time_dslash");
-    if ((rc = cuda_check(ctx, cudaGetLastError(), "time_dslash launch"))) return rc;
+    if ((rc = cuda_check(ctx, le != cudaSuccess ? le : cudaGetLastError(), "time_dslash launch"))) return rc;
+    if (staged) {
+        int h = 0;
+        if ((e = cudaMemcpy(&h, ctx->d_err.p, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_check(ctx, e, "time_dslash staging flag");
+        if (h) return set_err(ctx, SMPQ_ECUDA, "a shared-memory staging wait of the FP32 D_W timed out");
+    }
     float t = 0;
     if ((e = cudaEventElapsedTime(&t, ctx->ev1, ctx->ev2)) != cudaSuccess) return cuda_check(ctx, e, "time_dslash events");
     ctx->launches += reps + 2;

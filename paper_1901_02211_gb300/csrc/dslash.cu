@@ -3,6 +3,7 @@
 #include <string>
 
 #include "smpq_internal.cuh"
+#include "stage.cuh"
 #include "wilson.cuh"
 
 // ------------------------------------------------------------------ links
@@ -146,6 +147,72 @@ static void dslash_bc(const Geom &g, const void *U, const void *in, void *out, i
     else
         dslash_kernel<T, false, BC><<<grid, TileMap<BC>::THREADS, 0, st>>>(g, (const C *)U, (const C *)in, (C *)out,
                                                                             (T)kappa);
+}
+
+// The FP32 D_W with the neighbour sites staged in shared memory (stage.cuh):
+// out = in - kappa hop(in), tpb lattice tiles per block.
+template <bool DAG, int BC>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
+    dslash_staged_kernel(Geom g, const float2 *__restrict__ U, const float2 *__restrict__ in, float2 *__restrict__ out,
+                         float kappa, int tpb, int *err) {
+    typedef TileMap<BC> TM;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int jj = threadIdx.x % BC;
+    const size_t tb = (size_t)blockIdx.y * 12 * g.V * BC;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    stage::Runner<DAG, BC, stage::NSTAGE> run(dsm, g, U, in + tb, tile0, ntb, err);
+    for (int tl = 0; tl < ntb; ++tl) {
+        const int s = (tile0 + tl) * TM::SPB + threadIdx.x / BC;
+        const bool valid = s < g.V;
+        float2 acc[12][1];
+        run.hops(tl, s, valid, acc);
+        if (!valid) continue;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = tb + ((size_t)s * 12 + c) * BC + jj;
+            float2 v = in[o];
+            v.x -= kappa * acc[c][0].x;
+            v.y -= kappa * acc[c][0].y;
+            out[o] = v;
+        }
+    }
+}
+
+template <int BC>
+static cudaError_t dslash_staged_bc(const Geom &g, const void *U, const void *in, void *out, int B, int dagger,
+                                    double kappa, int *err, cudaStream_t st) {
+    constexpr int TPB_ST = 4; // lattice tiles per block
+    const int bytes = (int)stage::Dims<BC, stage::NSTAGE>::SMEM;
+    static bool attrs = false;
+    if (!attrs) {
+        cudaError_t e = cudaFuncSetAttribute(dslash_staged_kernel<false, BC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(dslash_staged_kernel<true, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     bytes);
+        if (e != cudaSuccess) return e;
+        attrs = true;
+    }
+    const int ntiles = (g.V + TileMap<BC>::SPB - 1) / TileMap<BC>::SPB;
+    const dim3 grid((ntiles + TPB_ST - 1) / TPB_ST, B / BC);
+    if (dagger)
+        dslash_staged_kernel<true, BC><<<grid, TileMap<BC>::THREADS, bytes, st>>>(
+            g, (const float2 *)U, (const float2 *)in, (float2 *)out, (float)kappa, TPB_ST, err);
+    else
+        dslash_staged_kernel<false, BC><<<grid, TileMap<BC>::THREADS, bytes, st>>>(
+            g, (const float2 *)U, (const float2 *)in, (float2 *)out, (float)kappa, TPB_ST, err);
+    return cudaSuccess;
+}
+
+cudaError_t launch_dslash_staged(const Geom &g, const void *U, const void *in, void *out, int B, int BC, int dagger,
+                                 double kappa, int *err, cudaStream_t st) {
+    switch (BC) {
+    case 12: return dslash_staged_bc<12>(g, U, in, out, B, dagger, kappa, err, st);
+    case 24: return dslash_staged_bc<24>(g, U, in, out, B, dagger, kappa, err, st);
+    case 48: return dslash_staged_bc<48>(g, U, in, out, B, dagger, kappa, err, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>

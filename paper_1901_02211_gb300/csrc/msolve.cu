@@ -31,6 +31,7 @@
 
 #include "half.cuh"
 #include "smpq_internal.cuh"
+#include "stage.cuh"
 #include "wilson.cuh"
 
 namespace {
@@ -85,13 +86,15 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return s;
 }
 
+constexpr int NFLAGS = 5; // the flags the host reads after each check interval
 struct Scal {
     double *rr, *bb, *alpha, *beta, *alpha_prev, *beta_prev, *rr_ref; // [B]
     int *act_rhs, *upd_rhs, *iters;                                  // [B]
     double *zeta, *zeta_prev, *zeta_new, *alpha_s, *beta_s;          // [n][B]
     int *act, *upd;                                                  // [n][B]
     int *flags; // [0] active rhs count, [1] residual replacement requested, [2] breakdown,
-                // [3] active rhs still above the precision-switch residual
+                // [3] active rhs still above the precision-switch residual,
+                // [4] a staging wait of the FP32 D_W ran out (stage.cuh)
     double *hist; // Lanczos: [2][hist_len] alpha_k, beta_k of rhs 0 (nullable)
     int hist_len;
     int *iter_counter; // [1] global iteration count (for the history index)
@@ -471,6 +474,118 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     double s1 = block_total<BC, NR>(ar, sm);
     if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
     fuse_step2<BC, TM::THREADS>(f, l, part_r, prow, G, sm);
+}
+
+// ------------------------------------------------------------------ FP32 D_W pair, neighbours staged
+// k_apply_a / k_apply_b for FP32 iterations (one column per thread) with the
+// neighbour sites brought into shared memory by bulk asynchronous copies
+// (stage.cuh): the same arithmetic in the same order, NS stages of SPB sites
+// in dynamic shared memory, *err set if a copy wait runs out.
+// three 240-thread blocks per SM (<= 91 registers a thread; 3 x 71 KB of shared memory)
+template <int BC, bool M>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
+    k_apply_a_st(Lats L, const float2 *__restrict__ p, float2 *__restrict__ t, float kappa, double *part_t,
+                 double *part_p, int tpb, Fuse f, int *err) {
+    typedef TileMap<BC> TM;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ double sm[SmemCols<BC, 1>::N];
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = threadIdx.x % BC;
+    const size_t tb = la.f0 + (size_t)cl * 12 * g.V * BC; // this RHS tile of the fields
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    stage::Runner<false, BC, stage::NSTAGE> run(dsm, g, (const float2 *)la.U, p + tb, tile0, ntb, err);
+    double at = 0, ap = 0;
+    for (int tl = 0; tl < ntb; ++tl) {
+        const int s = (tile0 + tl) * TM::SPB + threadIdx.x / BC;
+        const bool valid = s < g.V;
+        float2 acc[12][1];
+        run.hops(tl, s, valid, acc);
+        if (!valid) continue;
+        float st = 0, sp = 0;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = tb + ((size_t)s * 12 + c) * BC + jj;
+            float2 v = p[o];
+            sp += v.x * v.x + v.y * v.y;
+            v.x -= kappa * acc[c][0].x;
+            v.y -= kappa * acc[c][0].y;
+            st += v.x * v.x + v.y * v.y;
+            t[o] = v;
+        }
+        at += (double)st;
+        ap += (double)sp;
+    }
+    const double s1 = block_sum<BC>(at, sm);
+    const double s2 = block_sum<BC>(ap, sm);
+    if (threadIdx.x < BC) {
+        part_t[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[(prow + blockIdx.x) * BC + threadIdx.x] = s2;
+    }
+    fuse_step1<BC, TM::THREADS>(f, l, part_t, part_p, prow, G, sm);
+}
+
+template <int BC, bool M>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
+    k_apply_b_st(Lats L, const float2 *__restrict__ t, const float2 *__restrict__ p, float2 *__restrict__ r,
+                 const double *__restrict__ alpha, float kappa, double *part_r, int tpb, Fuse f, int *err) {
+    typedef TileMap<BC> TM;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ double sm[SmemCols<BC, 1>::N];
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = threadIdx.x % BC, j = blockIdx.y * BC + jj;
+    const size_t tb = la.f0 + (size_t)cl * 12 * g.V * BC;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    const float a = (float)alpha[j], sh = (float)la.s0;
+    stage::Runner<true, BC, stage::NSTAGE> run(dsm, g, (const float2 *)la.U, t + tb, tile0, ntb, err);
+    double ar = 0;
+    for (int tl = 0; tl < ntb; ++tl) {
+        const int s = (tile0 + tl) * TM::SPB + threadIdx.x / BC;
+        const bool valid = s < g.V;
+        float2 acc[12][1];
+        run.hops(tl, s, valid, acc);
+        if (!valid) continue;
+        float sr = 0;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = tb + ((size_t)s * 12 + c) * BC + jj;
+            const float2 tv = t[o], pv = p[o];
+            float2 rv = r[o];
+            const float apx = tv.x - kappa * acc[c][0].x + sh * pv.x;
+            const float apy = tv.y - kappa * acc[c][0].y + sh * pv.y;
+            rv.x -= a * apx;
+            rv.y -= a * apy;
+            sr += rv.x * rv.x + rv.y * rv.y;
+            r[o] = rv;
+        }
+        ar += (double)sr;
+    }
+    const double s1 = block_sum<BC>(ar, sm);
+    if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TM::THREADS>(f, l, part_r, prow, G, sm);
+}
+
+// the dynamic shared memory of the staged pair (above the 48 KB default)
+template <int BC, bool M> cudaError_t staged_attrs() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const int bytes = (int)stage::Dims<BC, stage::NSTAGE>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_a_st<BC, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_b_st<BC, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done = e == cudaSuccess;
+    return e;
 }
 
 // The base system's solution x accumulated by the p update: FP64 for the FP64
@@ -1198,6 +1313,7 @@ template <int BC> struct Solve {
     int chk;
     bool shifts;
     int tpb_hi = TPB, tpb_lo = TPB, nr = 1;
+    bool stg = false; // FP32 iterations: the D_W pair with staged neighbours (stage.cuh)
 
     explicit Solve(const std::vector<LatIn> &lats) : ctx(lats[0].ctx), in(lats), nl((int)lats.size()) {}
 
@@ -1246,12 +1362,14 @@ template <int BC> struct Solve {
         tpb_hi = std::max(1, in[0].spec->tpb_hi > 0 ? in[0].spec->tpb_hi : TPB);
         tpb_lo = std::max(1, in[0].spec->tpb_lo > 0 ? in[0].spec->tpb_lo : TPB);
         nr = in[0].spec->nr == 2 ? 2 : 1;
+        stg = in[0].spec->staged != 0 && BC >= 12; // (one-column tiles: plain loads)
+        if (stg && nr == 2) return set_err(ctx, SMPQ_EINVAL, "internal: the staged D_W has one column per thread");
         std::vector<Buf> &ws = ctx->ws;
         if (ws.size() < W_COUNT) ws.resize(W_COUNT);
         int rc;
         if ((rc = ensure(ctx, ws[W_PART], 3 * npart * sizeof(double)))) return rc;
         const size_t nscal = (size_t)B * 8 + (size_t)nshift * B * 5;
-        const size_t nint = (size_t)B * 3 + (size_t)nshift * B * 2 + 8 + (size_t)nchunk;
+        const size_t nint = (size_t)B * 3 + (size_t)nshift * B * 2 + 12 + (size_t)nchunk;
         const size_t spbytes = ((size_t)nl * sizeof(ShiftParams) + 255) / 256 * 256;
         if ((rc = ensure(ctx, ws[W_SCAL], spbytes + nscal * sizeof(double) + nint * sizeof(int)))) return rc;
         part0 = (double *)ws[W_PART].p;
@@ -1268,7 +1386,7 @@ template <int BC> struct Solve {
         int *ip = (int *)d;
         sc.act_rhs = ip; ip += B; sc.upd_rhs = ip; ip += B; sc.iters = ip; ip += B;
         sc.act = ip; ip += nshift * B; sc.upd = ip; ip += nshift * B;
-        sc.flags = ip; ip += 4; sc.iter_counter = ip; ip += 4;
+        sc.flags = ip; ip += 8; sc.iter_counter = ip; ip += 4;
         count = ip;
         sc.hist = hist;
         sc.hist_len = hist_len;
@@ -1289,11 +1407,11 @@ template <int BC> struct Solve {
                 ctx->prof_ev.push_back(ev);
             }
         }
-        if (cudaMallocHost(&hflags, 4 * sizeof(int)) != cudaSuccess) {
+        if (cudaMallocHost(&hflags, NFLAGS * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             return set_err(ctx, SMPQ_ENOMEM, "pinned host flags");
         }
-        cudaMemsetAsync(sc.flags, 0, (8 + (size_t)nchunk) * sizeof(int), st); // flags, counter, arrivals
+        cudaMemsetAsync(sc.flags, 0, (12 + (size_t)nchunk) * sizeof(int), st); // flags, counter, arrivals
         return SMPQ_OK;
     }
 
@@ -1407,6 +1525,14 @@ template <int BC> struct Solve {
         // block, per phase, and for the FP32 kernels one or two columns per thread
         const int tpb = hi ? tpb_hi : tpb_lo;
         const bool two_cols = std::is_same<T, float>::value && !half && nr == 2 && BC % 2 == 0 && !multi;
+        constexpr bool can_stage = std::is_same<T, float>::value && !half && BC >= 12;
+        const bool staged = can_stage && stg;
+        if constexpr (can_stage) {
+            if (staged) { // before any capture: the kernels' shared-memory limit
+                const cudaError_t e = multi ? staged_attrs<BC, true>() : staged_attrs<BC, false>();
+                if (e != cudaSuccess) return cuda_check(ctx, e, "staged D_W attributes");
+            }
+        }
         // Half-storage iterations replace the residual at least every 10x drop:
         // their iterated residual drifts from the true one by about the format's
         // rounding times the condition number per iteration, so a 1000x drop
@@ -1504,6 +1630,25 @@ template <int BC> struct Solve {
             auto launch = [&](auto nr_c, auto m) {
                 constexpr int NR = decltype(nr_c)::value;
                 constexpr bool M = decltype(m)::value;
+                if constexpr (can_stage && NR == 1) {
+                    if (staged) {
+                        int gx;
+                        const Lats Ld = lats_dw<T>(TileMap<BC>::SPB, tpb, &gx);
+                        const dim3 gridn(gx, nchunk);
+                        const size_t smem = stage::Dims<BC, stage::NSTAGE>::SMEM;
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
+                        k_apply_a_st<BC, M><<<gridn, TH, smem, st>>>(Ld, p, t, kappa, part0, part1, tpb, f1,
+                                                                      sc.flags + 4);
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
+                        k_apply_b_st<BC, M><<<gridn, TH, smem, st>>>(Ld, t, p, r, sc.alpha, kappa, part2, tpb, f2,
+                                                                      sc.flags + 4);
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+                        k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p,
+                                                                  xacc, xlo);
+                        return;
+                    }
+                }
                 if constexpr (NR == 1 || (std::is_same<T, float>::value && BC % 2 == 0 && !M)) {
                     typedef TileMap<BC, NR> TMN;
                     int gx;
@@ -1596,16 +1741,20 @@ template <int BC> struct Solve {
                 for (int k = 0; k < ck; ++k) iteration(k);
             ctx->launches += (long long)ck * per_iter;
             iters += ck;
-            cudaMemcpyAsync(hflags, sc.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(hflags, sc.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
             collect(ck, hi);
+            if (hflags[4]) {
+                status = set_err(ctx, SMPQ_ECUDA, "a shared-memory staging wait of the FP32 D_W timed out");
+                break;
+            }
             if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
             bool done = hflags[0] == 0;
             if (rel && (hflags[1] || done)) {
                 reliable();
                 ++nrel;
-                cudaMemcpyAsync(hflags, sc.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(hflags, sc.flags, NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, st);
                 e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) { status = cuda_check(ctx, e, "residual replacement"); break; }
                 done = hflags[0] == 0;
@@ -2023,6 +2172,38 @@ float time_pair(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part
     });
 }
 
+// the FP32 pair with staged neighbours (one column per thread); -1 if a
+// staging wait ran out (*err, zero on entry)
+template <int BC>
+float time_pair_staged(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part, double *alpha, int *err) {
+    typedef TileMap<BC> TM;
+    const int V = ctx->V, nchunk = B / BC;
+    const int GN = ((V + TM::SPB - 1) / TM::SPB + tpb - 1) / tpb;
+    const size_t nf = (size_t)B * 12 * V;
+    float2 *p = (float2 *)buf, *t = p + nf, *r = t + nf;
+    const Lats L = lats_single(ctx, Links<float>::get(ctx), GN);
+    const float kappa = (float)ctx->opt.kappa;
+    cudaStream_t st = ctx->stream;
+    const dim3 gridn(GN, nchunk);
+    const size_t smem = stage::Dims<BC, stage::NSTAGE>::SMEM;
+    if (staged_attrs<BC, false>() != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    Fuse none{};
+    const float ms = time_launches(ctx, reps, [&]() {
+        k_apply_a_st<BC, false><<<gridn, TM::THREADS, smem, st>>>(L, p, t, kappa, part,
+                                                                   part + (size_t)nchunk * GN * BC, tpb, none, err);
+        k_apply_b_st<BC, false><<<gridn, TM::THREADS, smem, st>>>(L, t, p, r, alpha, kappa, part, tpb, none, err);
+    });
+    int h = 0;
+    if (ms < 0 || cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || h) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    return ms;
+}
+
 // the half-storage pair (two columns per thread, r and x_lo in FP32)
 template <typename HT, int BC>
 float time_pair_half(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part, double *alpha) {
@@ -2047,7 +2228,7 @@ float time_pair_half(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double 
 }
 
 template <int BC> float time_kind(smpq_ctx *ctx, int kind, int B, int tpb, int nr, int reps, void *buf, double *part,
-                                  double *alpha) {
+                                  double *alpha, int *err) {
     switch (kind) {
     case 0: return time_pair<double, BC, 1>(ctx, B, tpb, reps, buf, part, alpha);
     case 1:
@@ -2056,18 +2237,19 @@ template <int BC> float time_kind(smpq_ctx *ctx, int kind, int B, int tpb, int n
     case 2: return time_pair<df64, BC, 1>(ctx, B, tpb, reps, buf, part, alpha);
     case 3: return time_pair_half<H16, BC>(ctx, B, tpb, reps, buf, part, alpha);
     case 4: return time_pair_half<B16, BC>(ctx, B, tpb, reps, buf, part, alpha);
+    case 5: return time_pair_staged<BC>(ctx, B, tpb, reps, buf, part, alpha, err);
     default: return -1.f;
     }
 }
 } // namespace
 
 float time_dslash_pair(smpq_ctx *ctx, int kind, int B, int BC, int tpb, int nr, int reps, void *buf, double *part,
-                       double *alpha) {
+                       double *alpha, int *err) {
     if (tpb < 1 || B % BC) return -1.f;
     switch (BC) {
-    case 12: return time_kind<12>(ctx, kind, B, tpb, nr, reps, buf, part, alpha);
-    case 24: return time_kind<24>(ctx, kind, B, tpb, nr, reps, buf, part, alpha);
-    case 48: return time_kind<48>(ctx, kind, B, tpb, nr, reps, buf, part, alpha);
+    case 12: return time_kind<12>(ctx, kind, B, tpb, nr, reps, buf, part, alpha, err);
+    case 24: return time_kind<24>(ctx, kind, B, tpb, nr, reps, buf, part, alpha, err);
+    case 48: return time_kind<48>(ctx, kind, B, tpb, nr, reps, buf, part, alpha, err);
     default: return -1.f;
     }
 }

@@ -39,6 +39,7 @@ struct smpq_ctx {
     int dims[4] = {0, 0, 0, 0};
     int V = 0;
     Buf U64, U32, Udf; // FP64, FP32 and float-float copies of the links
+    Buf d_err;         // int: set by a staged D_W whose staging wait ran out
     Buf Uh16, Ub16;    // rows 0 and 1 of the links in FP16 and BF16 (reconstruct-12)
 
     // spectrum / rational
@@ -63,7 +64,7 @@ struct smpq_ctx {
     struct Tuned {
         std::array<int, 4> dims;
         int B, prec;
-        std::array<int, 4> shape;
+        std::array<int, 5> shape; // bc, tpb_hi, tpb_lo, nr, staged
         int from_file;
     };
     std::vector<Tuned> tuned;
@@ -126,6 +127,10 @@ int half_tile(int B);
 size_t half_field_bytes(int V, int B);
 void launch_to_half(int prec, const double *in, void *out, int V, int B, cudaStream_t st);
 void launch_from_half(int prec, const void *in, double *out, int V, int B, cudaStream_t st);
+// the FP32 D_W with staged neighbour sites (stage.cuh), tiles of BC = 12, 24 or
+// 48 columns; *err (device int, zero on entry) is set if a staging wait ran out
+cudaError_t launch_dslash_staged(const Geom &g, const void *U, const void *in, void *out, int B, int BC, int dagger,
+                                 double kappa, int *err, cudaStream_t st);
 void launch_dslash_half(int prec, const Geom &g, const void *U, const void *in, void *out, int B, int dagger,
                         double kappa, cudaStream_t st);
 
@@ -146,6 +151,7 @@ struct SolveSpec {
     // block in the FP64-accurate and in the FP32 / half iterations, columns
     // per thread of the FP32 kernels (1 or 2)
     int tpb_hi, tpb_lo, nr;
+    int staged; // FP32 iterations: the D_W pair with neighbours staged in shared memory (nr = 1)
 };
 struct SolveOut {
     // y = R(H^2) b on the support, FP64, layout [j/BC][n_sup][12][BC] (the field
@@ -185,12 +191,13 @@ int lowmodes_dov_project(smpq_ctx *ctx, const double2 *b, double2 *bperp, int B,
 int lowmodes_dov_finish(smpq_ctx *ctx, double2 *out, int B, const std::vector<double> &wd, cudaStream_t st);
 // autotuner: average ms of one D_W + D_W^dag-update launch pair of the
 // iterations of `kind` (0 FP64, 1 FP32, 2 float-float, 3 FP16 + norms,
-// 4 BF16 + norms) for B columns in tiles of BC, tpb tiles per block and nr
-// columns per thread (FP32: 1 or 2).  Scratch in buf: 3 fields of B x 12 x V
-// float-float complex; part: 2 * B * V / 12 doubles of partials; alpha: B
-// doubles.  -1 on a bad shape or a CUDA error.
+// 4 BF16 + norms, 5 FP32 with staged neighbours) for B columns in tiles of BC,
+// tpb tiles per block and nr columns per thread (FP32: 1 or 2).  Scratch in
+// buf: 3 fields of B x 12 x V complex values of the kind; part: 2 * B * V / 12
+// doubles of partials; alpha: B doubles; err: one int, zero on entry (kind 5
+// sets it if a staging wait ran out).  -1 on a bad shape or a CUDA error.
 float time_dslash_pair(smpq_ctx *ctx, int kind, int B, int BC, int tpb, int nr, int reps, void *buf, double *part,
-                       double *alpha);
+                       double *alpha, int *err);
 
 // probing.cu : sources, star support, contraction, Q
 int build_star_support(smpq_ctx *ctx, Buf &supsite, int *n_sup);

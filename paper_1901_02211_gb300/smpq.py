@@ -57,6 +57,7 @@ class smpq_options(ctypes.Structure):
         ("full_support", ctypes.c_int),
         ("true_residual", ctypes.c_int),
         ("tune_cache", ctypes.c_char_p),
+        ("staging", ctypes.c_int),
     ]
 
 
@@ -89,6 +90,7 @@ class smpq_stats(ctypes.Structure):
         ("tiles_per_block_lo", ctypes.c_int),
         ("cols_per_thread", ctypes.c_int),
         ("shape_from_cache", ctypes.c_int),
+        ("staged", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -200,9 +202,9 @@ def smpq_alu_peak(device=0, kind=ALU_FP32X2):
 
 
 def smpq_tune_cache_lookup(path, device, dims, B, precision):
-    """The cached launch shape (bc, tpb_hi, tpb_lo, nr) or None."""
+    """The cached launch shape (bc, tpb_hi, tpb_lo, nr, staged) or None."""
     d = (ctypes.c_int * 4)(*dims)
-    sh = (ctypes.c_int * 4)()
+    sh = (ctypes.c_int * 5)()
     rc = load().smpq_tune_cache_lookup(os.fsencode(path), device.encode(), d, B, precision, sh)
     if rc == SMPQ_ESTATE:
         return None
@@ -212,7 +214,9 @@ def smpq_tune_cache_lookup(path, device, dims, B, precision):
 
 def smpq_tune_cache_store(path, device, dims, B, precision, shape, ms):
     d = (ctypes.c_int * 4)(*dims)
-    sh = (ctypes.c_int * 4)(*shape)
+    if len(shape) != 5:
+        raise ValueError("a launch shape has 5 entries (bc, tpb_hi, tpb_lo, nr, staged)")
+    sh = (ctypes.c_int * 5)(*shape)
     _check(load().smpq_tune_cache_store(os.fsencode(path), device.encode(), d, B, precision, sh, ms))
 
 

@@ -134,18 +134,20 @@ def test_tune_cache_round_trip(tmp_path):
     path = str(tmp_path / "tune.txt")
     dev, dims = "NVIDIA GB300/152sm", (8, 8, 8, 16)
     assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) is None
-    S.smpq_tune_cache_store(path, dev, dims, 3072, S.SMPQ_MIXED, (48, 4, 2, 1), 7.5)
-    S.smpq_tune_cache_store(path, dev, dims, 1536, S.SMPQ_MIXED, (24, 1, 8, 2), 3.0)
-    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (48, 4, 2, 1)
-    assert S.smpq_tune_cache_lookup(path, dev, dims, 1536, S.SMPQ_MIXED) == (24, 1, 8, 2)
+    S.smpq_tune_cache_store(path, dev, dims, 3072, S.SMPQ_MIXED, (48, 4, 2, 1, 1), 7.5)
+    S.smpq_tune_cache_store(path, dev, dims, 1536, S.SMPQ_MIXED, (24, 1, 8, 2, 0), 3.0)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (48, 4, 2, 1, 1)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 1536, S.SMPQ_MIXED) == (24, 1, 8, 2, 0)
     assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_FP32) is None
     assert S.smpq_tune_cache_lookup(path, dev, (8, 8, 16, 8), 3072, S.SMPQ_MIXED) is None
     assert S.smpq_tune_cache_lookup(path, "other/1sm", dims, 3072, S.SMPQ_MIXED) is None
     with open(path, "a") as f:
-        f.write("smpq-tune-1|NVIDIA GB300/152sm|8 8 8 16|3072|2|7 4 4 1|1.0\n")  # tile 7: rejected
+        f.write("smpq-tune-2|NVIDIA GB300/152sm|8 8 8 16|3072|2|7 4 4 1 0|1.0\n")  # tile 7: rejected
+        f.write("smpq-tune-2|NVIDIA GB300/152sm|8 8 8 16|3072|2|48 4 4 2 1|1.0\n")  # staged needs nr 1
+        f.write("smpq-tune-1|NVIDIA GB300/152sm|8 8 8 16|3072|2|48 8 8 1|1.0\n")  # old format: ignored
         f.write("garbage line\n")
-    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (48, 4, 2, 1)
-    S.smpq_tune_cache_store(path, dev, dims, 3072, S.SMPQ_MIXED, (12, 8, 8, 2), 6.0)
-    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (12, 8, 8, 2)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (48, 4, 2, 1, 1)
+    S.smpq_tune_cache_store(path, dev, dims, 3072, S.SMPQ_MIXED, (12, 8, 8, 2, 0), 6.0)
+    assert S.smpq_tune_cache_lookup(path, dev, dims, 3072, S.SMPQ_MIXED) == (12, 8, 8, 2, 0)
     with pytest.raises(S.SmpqError):
-        S.smpq_tune_cache_store(path, "bad|name", dims, 3072, S.SMPQ_MIXED, (48, 4, 4, 1), 1.0)
+        S.smpq_tune_cache_store(path, "bad|name", dims, 3072, S.SMPQ_MIXED, (48, 4, 4, 1, 0), 1.0)

@@ -343,6 +343,14 @@ def test_unit_links_give_zero(S):
 # ----------------------------------------------------------------------------- 8^3 x 16 against the oracle (sampled classes)
 
 
+def mixed_resid_bar(theta):
+    """Bar on the base system's true residual after a mixed solve that switched
+    to FP32 at ||r|| = theta ||b|| with no later replacement: 256 u_32 theta
+    (u_32 = 2^-24) above the 1e-10 tolerance."""
+    return 256 * 2.0 ** -24 * theta + 1e-10
+
+
+
 @pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed7e-3", "mixed1e-2", "mixed3e-2", "fp16n", "bf16n"])
 def test_qx_8x16_sampled(S, r, classes, prec):
@@ -369,9 +377,10 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     # the base system's residual recomputed with FP64 accuracy after the solve:
     # the FP64, FP32 and half paths stop at the 1e-10 tolerance (FP32 and half
     # through their residual replacements); the mixed path's FP32 phase has no
-    # replacement, and its base residual drifts to about u_32 theta times a
-    # growth factor (the price of the cancellation that keeps q(x) accurate)
-    assert 0 <= st["true_resid"] <= (1e-8 if prec.startswith("mixed") else 1.1e-10)
+    # replacement: it starts at ||r|| = theta ||b|| and its FP32 operator moves
+    # the iterated residual away from the true one by about u_32 theta times a
+    # growth factor (measured 50-70 on these lattices, bar 256)
+    assert 0 <= st["true_resid"] <= (mixed_resid_bar(switch) if prec.startswith("mixed") else 1.1e-10)
     # FP64 and the FP64-then-FP32 path meet the 1e-8 per-site bar; the FP32
     # path with FP64 reliable updates has the FP32 floor of its shifted systems.
     # The per-site error of the mixed path grows with the switch point (about
@@ -476,7 +485,10 @@ def test_bench_configuration_sampled(S):
         s.set_spectrum(a, b)
         s.build_sources(4, 0)
         q, Q, st = s.compute_qx()
+        # again, with the launch shape the first call tuned: the same bits
+        q2, Q2, st2 = s.compute_qx()
     assert st["n_rhs"] == 3072 and st["n_batches"] == 1
+    assert np.array_equal(q2, q) and Q2 == Q
     mask = np.isin(colour, sample)
     err = np.abs(q[mask] - ref[mask]).max()
     dQ = abs(q.real[mask].sum() - ref.real[mask].sum())
@@ -487,8 +499,9 @@ def test_bench_configuration_sampled(S):
     assert abs(Q - 2.0) < 0.05  # closed-form index k = 2, r_min = 4 probing bias
     # three launches per CG iteration (plus setup, phase switch, residual
     # replacement, contraction and the iterations of the last check interval
-    # after convergence)
-    assert st["kernel_launches"] <= 3 * (st["max_iterations"] + 20) + 60
+    # after convergence); the first call also ran the autotuner's timings
+    print("    second call: %d launches, staged FP32 D_W %d" % (st2["kernel_launches"], st2["staged"]))
+    assert st2["kernel_launches"] <= 3 * (st2["max_iterations"] + 20) + 60
 
 
 # ----------------------------------------------------------------------------- SMP trace of D_W^{-1}
@@ -559,7 +572,7 @@ def test_uneven_batch_matches_single_runs(S, flux4, zolo4, g5dov4):
                                                   stats[i]["true_resid"]))
         assert d <= 1e-9
         assert abs(Qs[i] - Q) <= 1e-9
-        assert 0 <= stats[i]["true_resid"] <= 1e-8  # the mixed path's measured base residual
+        assert 0 <= stats[i]["true_resid"] <= mixed_resid_bar(7e-3)  # the mixed path's measured base residual
     # against the oracle
     q4 = bufs_re[0] + 1j * bufs_im[0]
     dense = qx.dense_smp_qx(g5dov4, probing.color_sites((4, 4, 4, 4), 2, 0)[0])
@@ -606,10 +619,12 @@ def test_qx_16x32_sampled(S):
 
 def test_autotuner_shapes_and_cache_file(S, tmp_path):
     """The autotuner picks a D_W launch shape (RHS tile, tiles per block of each
-    phase, FP32 columns per thread), writes it to the cache file, and a second
-    context reads it back without timing.  A shape forced through the file
-    (two FP32 columns per thread, one and eight tiles per block) gives the same
-    q(x) to rounding, and both agree with the oracle."""
+    phase, FP32 columns per thread, staged FP32 neighbours), writes it to the
+    cache file, and a second context reads it back without timing.  Shapes
+    forced through the file (two FP32 columns per thread, one and eight tiles
+    per block; the staged FP32 D_W on 24-column tiles, three tiles per block,
+    so the last block holds one) give the same q(x) to rounding, and all agree
+    with the oracle."""
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
     a, b = _interval("flux8x16")
@@ -620,23 +635,26 @@ def test_autotuner_shapes_and_cache_file(S, tmp_path):
     mask = np.isin(colour, classes)
     path = str(tmp_path / "tune.txt")
     out = []
-    for forced in (None, None, (12, 1, 8, 2)):
+    for k, forced in enumerate((None, None, (12, 1, 8, 2, 0), (24, 2, 3, 1, 1))):
         if forced is not None:
-            path = str(tmp_path / "forced.txt")
+            path = str(tmp_path / ("forced%d.txt" % k))
             S.smpq_tune_cache_store(path, _device_key(S), dims, 48, S.SMPQ_MIXED, forced, 1.0)
         with _session(S, precision=S.SMPQ_MIXED, tune_cache=path) as s:
             s.load_gauge(dims, U)
             s.set_spectrum(a, b)
             s.build_sources(4, 0)
             q, Q, st = s.compute_qx(classes=classes)
-        shape = (st["rhs_tile"], st["tiles_per_block_hi"], st["tiles_per_block_lo"], st["cols_per_thread"])
+        shape = (st["rhs_tile"], st["tiles_per_block_hi"], st["tiles_per_block_lo"], st["cols_per_thread"],
+                 st["staged"])
         err = np.abs(q[mask] - ref[mask]).max()
         print("autotuner: shape %s from cache %d, max |dq| vs oracle %.3e" % (shape, st["shape_from_cache"], err))
         assert err <= 1e-8
         out.append((shape, st["shape_from_cache"], q))
     assert out[0][1] == 0 and out[1][1] == 1 and out[1][0] == out[0][0]
-    assert out[2][1] == 1 and out[2][0] == (12, 1, 8, 2)
+    assert out[2][1] == 1 and out[2][0] == (12, 1, 8, 2, 0)
+    assert out[3][1] == 1 and out[3][0] == (24, 2, 3, 1, 1)  # staged FP32 D_W, 3 tiles per block
     assert np.abs(out[2][2][mask] - out[0][2][mask]).max() <= 1e-10
+    assert np.abs(out[3][2][mask] - out[0][2][mask]).max() <= 1e-10
     assert len(open(str(tmp_path / "tune.txt")).read().splitlines()) == 1
 
 
