@@ -90,8 +90,9 @@ typedef struct {
     int profile;           /* time every D_W / D_W^dag launch of the solver with CUDA events */
     double switch_residual; /* SMPQ_MIXED: relative residual at which FP64 iterations hand over to FP32 */
     int autotune;           /* time the D_W launch shapes (RHS tile 12, 24, 48; tiles per block 1, 2,
-                               4, 8; FP32 columns per thread 1, 2) on the first solve of each batch
-                               shape, and use the fastest */
+                               4, 8; FP32 columns per thread 1, 2; neighbours staged in shared
+                               memory or not, per phase) on the first solve of each batch shape,
+                               and use the fastest */
     int full_support;       /* q(x): keep the shifted directions on every site instead of only where
                                z = D_W y is read (the ablation of that restriction; same result,
                                14 full-lattice vectors per source) */
@@ -108,11 +109,13 @@ typedef struct {
     const char *tune_cache; /* path of a text file of tuned launch shapes (NULL: none): read before
                                tuning a new shape, appended after (see smpq_tune_cache_lookup).  The
                                context copies the path. */
-    int staging;            /* FP32 D_W launches (SMPQ_FP32 and the second phase of SMPQ_MIXED) with
-                               the neighbour sites staged in shared memory by bulk asynchronous
-                               copies, one column per thread: -1 the autotuner chooses (staged when
-                               autotune is 0), 0 never, 1 always (RHS tiles of 12 columns or more).
-                               The stand-alone FP32 D_W of smpq_time_dslash stages unless this is 0. */
+    int staging;            /* D_W launches of the FP32 iterations (SMPQ_FP32, the second phase of
+                               SMPQ_MIXED) and of the float-float ones (the first phase of
+                               SMPQ_MIXED) with the neighbour sites staged in shared memory by bulk
+                               asynchronous copies, one column per thread: -1 the autotuner chooses
+                               per phase (plain loads when autotune is 0), 0 never, 1 always (RHS
+                               tiles of 12 columns or more).  The stand-alone FP32 D_W of
+                               smpq_time_dslash stages only when this is 1. */
 } smpq_options;
 
 typedef struct {
@@ -147,13 +150,14 @@ typedef struct {
     int tiles_per_block_lo; /*   FP64-accurate and of the FP32 / half-storage iterations, */
     int cols_per_thread;    /*   FP32 columns per thread (1 or 2), */
     int shape_from_cache;   /*   1 if the shape came from the tune_cache file, */
-    int staged;             /*   1 if the FP32 D_W launches staged the neighbour sites in shared
-                                 memory (bulk asynchronous copies; one column per thread) */
+    int staged;             /*   D_W launches that staged the neighbour sites in shared memory
+                                 (bulk asynchronous copies; one column per thread): bit 0 the FP32
+                                 iterations, bit 1 the float-float ones */
 } smpq_stats;
 
 /* Fill *opt with the paper's parameters: kappa 0.21, 14 poles, tol 1e-10,
  * max_iter 5000, FP64, reliable_delta 1e-3, periodic bc, automatic batching,
- * 10 iterations per check, graphs on, profiling off, switch_residual 7e-3,
+ * 10 iterations per check, graphs on, profiling off, switch_residual 1e-3,
  * autotuning on, no true-residual accumulation, no tuning cache file, staging
  * chosen by the autotuner (-1). */
 int smpq_options_default(smpq_options *opt);
@@ -320,10 +324,10 @@ int smpq_trace_dwinv(smpq_ctx *ctx, double *t_re, double *t_im, int on_device, d
 /* The autotuner's cache file (host only; not part of the paper's method).
  * A shape is {RHS tile width (1, 12, 24, 48), tiles per block of the
  * FP64-accurate D_W launches, tiles per block of the FP32 / half-storage ones,
- * FP32 columns per thread (1, 2), FP32 neighbours staged in shared memory (0,
- * 1; 1 only with one column)}, keyed by a device string (as the library writes
- * it: "<name>/<SMs>sm"), the lattice dims, the batch B and the precision.  One
- * line per entry:
+ * FP32 columns per thread (1, 2), neighbours staged in shared memory (bit 0
+ * the FP32 iterations, only with one column; bit 1 the float-float ones)},
+ * keyed by a device string (as the library writes it: "<name>/<SMs>sm"), the
+ * lattice dims, the batch B and the precision.  One line per entry:
  *   smpq-tune-2|<device>|<nx> <ny> <nz> <nt>|<B>|<precision>|<bc> <tpb_hi> <tpb_lo> <nr> <staged>|<ms>
  * lookup: SMPQ_OK and shape[5] filled from the last matching well-formed line,
  * SMPQ_ESTATE if the file is missing or has no such line, SMPQ_EINVAL for

@@ -178,7 +178,8 @@ Shape tune_shape_raw(smpq_ctx *ctx, int B, int prec, int *cached) {
     if (cand.empty()) return def;
     def.bc = cand.back();
     const int kind_lo = tune_kind_lo(prec);
-    def.staged = kind_lo == 1 && ctx->opt.staging != 0 ? 1 : 0; // FP32 iterations: staged neighbours
+    // staged neighbours (staging 1): bit 0 the FP32 iterations, bit 1 the float-float ones
+    def.staged = ctx->opt.staging == 1 ? (kind_lo == 1 ? 1 : 0) | (prec == SMPQ_MIXED ? 2 : 0) : 0;
     if (!ctx->opt.autotune) return def;
     for (auto &e : ctx->tuned)
         if (e.dims == std::array<int, 4>{ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3]} && e.B == B &&
@@ -235,22 +236,25 @@ Shape tune_shape_raw(smpq_ctx *ctx, int B, int prec, int *cached) {
                     if (fp64) s.tpb_hi = tpb;
                     else s.tpb_lo = tpb;
                     s.nr = nr;
-                    s.staged = v == 2 ? 1 : 0;
+                    s.staged = (s.staged & 2) | (v == 2 ? 1 : 0);
                 }
             }
-        if (mixed) { // the float-float iterations: about a fifth of the solve
+        if (mixed) { // the float-float iterations: about a quarter of the solve
             float th = 1e30f;
-            for (int tpb : {1, 2, 4, 8}) {
-                const float t = time_dslash_pair(ctx, 2, B, bc, tpb, 1, 2, buf, part, alpha, err);
-                ctx->launches += 6;
-                if (t > 0 && t < th) {
-                    th = t;
-                    s.tpb_hi = tpb;
+            for (int tpb : {1, 2, 4, 8})
+                for (int v : {0, 1}) { // plain loads, staged neighbours
+                    if ((v == 1 && ctx->opt.staging == 0) || (v == 0 && ctx->opt.staging == 1)) continue;
+                    const float t = time_dslash_pair(ctx, v ? 6 : 2, B, bc, tpb, 1, 2, buf, part, alpha, err);
+                    ctx->launches += 6;
+                    if (t > 0 && t < th) {
+                        th = t;
+                        s.tpb_hi = tpb;
+                        s.staged = (s.staged & 1) | (v ? 2 : 0);
+                    }
                 }
-            }
             thi = th;
         }
-        const float est = mixed ? 0.2f * thi + 0.8f * tlo : tlo;
+        const float est = mixed ? 0.25f * thi + 0.75f * tlo : tlo;
         if (est < tbest) {
             tbest = est;
             best = s;
@@ -269,11 +273,14 @@ Shape tune_shape_raw(smpq_ctx *ctx, int B, int prec, int *cached) {
 // the tuned (or cached, or default) shape with the staging option applied
 Shape tune_shape(smpq_ctx *ctx, int B, int prec, int *cached) {
     Shape s = tune_shape_raw(ctx, B, prec, cached);
-    if (tune_kind_lo(prec) != 1 || s.bc < 12 || ctx->opt.staging == 0) {
+    const int can = (tune_kind_lo(prec) == 1 ? 1 : 0) | (prec == SMPQ_MIXED ? 2 : 0); // stageable phases
+    if (s.bc < 12 || ctx->opt.staging == 0) {
         s.staged = 0;
     } else if (ctx->opt.staging == 1) {
-        s.staged = 1;
-        s.nr = 1;
+        s.staged = can;
+        if (can & 1) s.nr = 1;
+    } else {
+        s.staged &= can;
     }
     return s;
 }
@@ -504,7 +511,7 @@ int compute_classes(smpq_ctx *ctx, const std::vector<int> &classes, double *q_re
         stats->tiles_per_block_lo = shape.tpb_lo;
         stats->cols_per_thread = shape.nr;
         stats->shape_from_cache = from_cache;
-        stats->staged = shape.staged && (prec == SMPQ_FP32 || prec == SMPQ_MIXED) && BC > 1;
+        stats->staged = BC > 1 ? shape.staged : 0;
         stats->solve_ms = solve_ms;
         stats->total_ms = tms;
         stats->kernel_launches = ctx->launches;
@@ -575,11 +582,11 @@ int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_d
     for (int l = 0; l < n; ++l) rounds = std::max(rounds, (N[l] + Bl[l] - 1) / Bl[l]);
     int Btot = 0;
     for (int l = 0; l < n; ++l) Btot += Bl[l];
-    // launch shape: the default tiles per block, one column per thread, FP32
-    // iterations with staged neighbours (timing candidates would need scratch
-    // the size of the round again)
+    // launch shape: the default tiles per block, one column per thread (timing
+    // candidates would need scratch the size of the round again)
     const int from_cache = 0;
-    const Shape shape{BC, TPB_DEFAULT, TPB_DEFAULT, 1, tune_kind_lo(prec) == 1 && c0->opt.staging != 0 ? 1 : 0};
+    const Shape shape{BC, TPB_DEFAULT, TPB_DEFAULT, 1,
+                      c0->opt.staging == 1 ? (tune_kind_lo(prec) == 1 ? 1 : 0) | (prec == SMPQ_MIXED ? 2 : 0) : 0};
     // global per-rhs tables (support class, source component, source class) in the first context
     if ((rc = ensure(c0, c0->ws[W_RHS], (size_t)3 * Btot * sizeof(int)))) return rc;
     int *d_rhs_class = (int *)c0->ws[W_RHS].p, *d_src_comp = d_rhs_class + Btot, *d_src_class = d_src_comp + Btot;
@@ -724,7 +731,7 @@ int smpq_options_default(smpq_options *o) {
     o->iters_per_check = 10;
     o->use_graphs = 1;
     o->profile = 0;
-    o->switch_residual = 7e-3;
+    o->switch_residual = 1e-3;
     o->autotune = 1;
     o->staging = -1;
     return SMPQ_OK;
@@ -744,7 +751,7 @@ int smpq_tune_cache_lookup(const char *path, const char *device, const int dims[
         double ms;
         if (std::sscanf(line + key.size(), "%d %d %d %d %d|%lf", &v[0], &v[1], &v[2], &v[3], &v[4], &ms) == 6 &&
             (v[0] == 1 || v[0] == 12 || v[0] == 24 || v[0] == 48) && v[1] >= 1 && v[1] <= 64 && v[2] >= 1 &&
-            v[2] <= 64 && (v[3] == 1 || v[3] == 2) && (v[4] == 0 || (v[4] == 1 && v[3] == 1))) {
+            v[2] <= 64 && (v[3] == 1 || v[3] == 2) && v[4] >= 0 && v[4] <= 3 && (!(v[4] & 1) || v[3] == 1)) {
             std::copy(v, v + 5, shape); // the last matching line wins
             rc = SMPQ_OK;
         }
@@ -1113,8 +1120,8 @@ int smpq_time_dslash(smpq_ctx *ctx, int B, int dagger, int precision, int reps, 
     // the FP64 / FP32 tile: the widest of 48, 12 and 1 that divides B
     const int BC = B % 48 == 0 ? 48 : (B % 12 == 0 ? 12 : 1);
     const void *U = dslash_links(ctx, precision);
-    // FP32 on tiles of 12 or more columns: the neighbour sites staged in shared memory
-    const bool staged = precision == SMPQ_FP32 && BC >= 12 && ctx->opt.staging != 0;
+    // FP32 on tiles of 12 or more columns with staging 1: the neighbour sites staged in shared memory
+    const bool staged = precision == SMPQ_FP32 && BC >= 12 && ctx->opt.staging == 1;
     if (staged) {
         if ((rc = ensure(ctx, ctx->d_err, 16))) return rc;
         cudaMemsetAsync(ctx->d_err.p, 0, 16, st);

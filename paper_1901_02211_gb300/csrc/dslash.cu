@@ -154,13 +154,14 @@ static void dslash_bc(const Geom &g, const void *U, const void *in, void *out, i
 template <bool DAG, int BC>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     dslash_staged_kernel(Geom g, const float2 *__restrict__ U, const float2 *__restrict__ in, float2 *__restrict__ out,
-                         float kappa, int tpb, int *err) {
+                         double kd, int tpb, int *err) {
     typedef TileMap<BC> TM;
     extern __shared__ __align__(128) unsigned char dsm[];
     const int jj = threadIdx.x % BC;
     const size_t tb = (size_t)blockIdx.y * 12 * g.V * BC;
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    const float kappa = (float)kd;
     stage::Runner<DAG, BC, stage::NSTAGE> run(dsm, g, U, in + tb, tile0, ntb, err);
     for (int tl = 0; tl < ntb; ++tl) {
         const int s = (tile0 + tl) * TM::SPB + threadIdx.x / BC;
@@ -198,10 +199,10 @@ static cudaError_t dslash_staged_bc(const Geom &g, const void *U, const void *in
     const dim3 grid((ntiles + TPB_ST - 1) / TPB_ST, B / BC);
     if (dagger)
         dslash_staged_kernel<true, BC><<<grid, TileMap<BC>::THREADS, bytes, st>>>(
-            g, (const float2 *)U, (const float2 *)in, (float2 *)out, (float)kappa, TPB_ST, err);
+            g, (const float2 *)U, (const float2 *)in, (float2 *)out, kappa, TPB_ST, err);
     else
         dslash_staged_kernel<false, BC><<<grid, TileMap<BC>::THREADS, bytes, st>>>(
-            g, (const float2 *)U, (const float2 *)in, (float2 *)out, (float)kappa, TPB_ST, err);
+            g, (const float2 *)U, (const float2 *)in, (float2 *)out, kappa, TPB_ST, err);
     return cudaSuccess;
 }
 

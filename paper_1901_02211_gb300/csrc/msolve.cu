@@ -361,9 +361,10 @@ template <int BC, int NR> struct SmemCols {
 template <typename T, int BC, int NR, bool M>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_a(Lats L, const typename cplx_t<T>::type *__restrict__ p, typename cplx_t<T>::type *__restrict__ t,
-              T kappa, double *part_t, double *part_p, int tpb, Fuse f) {
+              double kd, double *part_t, double *part_p, int tpb, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
+    const T kappa = (T)kd;
     __shared__ double sm[SmemCols<BC, NR>::N];
     const int l = lat_index<M>(L);
     const Lat &la = L.l[l];
@@ -419,10 +420,11 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
 template <typename T, int BC, int NR, bool M>
 __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
     k_apply_b(Lats L, const typename cplx_t<T>::type *__restrict__ t, const typename cplx_t<T>::type *__restrict__ p,
-              typename cplx_t<T>::type *__restrict__ r, const double *__restrict__ alpha, T kappa, double *part_r,
+              typename cplx_t<T>::type *__restrict__ r, const double *__restrict__ alpha, double kd, double *part_r,
               int tpb, Fuse f) {
     typedef typename cplx_t<T>::type C;
     typedef TileMap<BC, NR> TM;
+    const T kappa = (T)kd;
     __shared__ double sm[SmemCols<BC, NR>::N];
     const int l = lat_index<M>(L);
     const Lat &la = L.l[l];
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(TileMap<BC, NR>::THREADS, MinBlocks<T>::value)
 // three 240-thread blocks per SM (<= 91 registers a thread; 3 x 71 KB of shared memory)
 template <int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
-    k_apply_a_st(Lats L, const float2 *__restrict__ p, float2 *__restrict__ t, float kappa, double *part_t,
+    k_apply_a_st(Lats L, const float2 *__restrict__ p, float2 *__restrict__ t, double kd, double *part_t,
                  double *part_p, int tpb, Fuse f, int *err) {
     typedef TileMap<BC> TM;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -499,6 +501,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     const size_t tb = la.f0 + (size_t)cl * 12 * g.V * BC; // this RHS tile of the fields
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    const float kappa = (float)kd;
     stage::Runner<false, BC, stage::NSTAGE> run(dsm, g, (const float2 *)la.U, p + tb, tile0, ntb, err);
     double at = 0, ap = 0;
     for (int tl = 0; tl < ntb; ++tl) {
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
 template <int BC, bool M>
 __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     k_apply_b_st(Lats L, const float2 *__restrict__ t, const float2 *__restrict__ p, float2 *__restrict__ r,
-                 const double *__restrict__ alpha, float kappa, double *part_r, int tpb, Fuse f, int *err) {
+                 const double *__restrict__ alpha, double kd, double *part_r, int tpb, Fuse f, int *err) {
     typedef TileMap<BC> TM;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ double sm[SmemCols<BC, 1>::N];
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     const size_t tb = la.f0 + (size_t)cl * 12 * g.V * BC;
     const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
     const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
-    const float a = (float)alpha[j], sh = (float)la.s0;
+    const float a = (float)alpha[j], sh = (float)la.s0, kappa = (float)kd;
     stage::Runner<true, BC, stage::NSTAGE> run(dsm, g, (const float2 *)la.U, t + tb, tile0, ntb, err);
     double ar = 0;
     for (int tl = 0; tl < ntb; ++tl) {
@@ -574,6 +577,114 @@ __global__ void __launch_bounds__(TileMap<BC>::THREADS, 3)
     const double s1 = block_sum<BC>(ar, sm);
     if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
     fuse_step2<BC, TM::THREADS>(f, l, part_r, prow, G, sm);
+}
+
+// The float-float pair (the first phase of SMPQ_MIXED) with staged neighbours
+// and links (stage.cuh, two stages): the epilogues of k_apply_a / k_apply_b.
+template <int BC, bool M>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<df64>::value)
+    k_apply_a_dfst(Lats L, const df64c *__restrict__ p, df64c *__restrict__ t, df64 kappa, double *part_t,
+                   double *part_p, int tpb, Fuse f, int *err) {
+    typedef TileMap<BC> TM;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ double sm[SmemCols<BC, 1>::N];
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = threadIdx.x % BC;
+    const size_t tb = la.f0 + (size_t)cl * 12 * g.V * BC;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    stage::RunnerDF<false, BC, stage::NSTAGE_DF> run(dsm, g, (const df64c *)la.U, p + tb, tile0, ntb, err);
+    double at = 0, ap = 0;
+    for (int tl = 0; tl < ntb; ++tl) {
+        const int s = (tile0 + tl) * TM::SPB + threadIdx.x / BC;
+        const bool valid = s < g.V;
+        df64c acc[12][1];
+        run.hops(tl, s, valid, acc);
+        if (!valid) continue;
+        df64 st = 0, sp = 0;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = tb + ((size_t)s * 12 + c) * BC + jj;
+            df64c v = p[o];
+            sp += v.x * v.x + v.y * v.y;
+            v.x -= kappa * acc[c][0].x;
+            v.y -= kappa * acc[c][0].y;
+            st += v.x * v.x + v.y * v.y;
+            t[o] = v;
+        }
+        at += (double)st;
+        ap += (double)sp;
+    }
+    const double s1 = block_sum<BC>(at, sm);
+    const double s2 = block_sum<BC>(ap, sm);
+    if (threadIdx.x < BC) {
+        part_t[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+        part_p[(prow + blockIdx.x) * BC + threadIdx.x] = s2;
+    }
+    fuse_step1<BC, TM::THREADS>(f, l, part_t, part_p, prow, G, sm);
+}
+
+template <int BC, bool M>
+__global__ void __launch_bounds__(TileMap<BC>::THREADS, MinBlocks<df64>::value)
+    k_apply_b_dfst(Lats L, const df64c *__restrict__ t, const df64c *__restrict__ p, df64c *__restrict__ r,
+                   const double *__restrict__ alpha, df64 kappa, double *part_r, int tpb, Fuse f, int *err) {
+    typedef TileMap<BC> TM;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ double sm[SmemCols<BC, 1>::N];
+    const int l = lat_index<M>(L);
+    const Lat &la = L.l[l];
+    if ((int)blockIdx.x >= la.G) return;
+    const Geom &g = la.g;
+    const int G = la.G, cl = blockIdx.y - la.chunk0;
+    const size_t prow = la.p0 + (size_t)cl * G;
+    const int jj = threadIdx.x % BC, j = blockIdx.y * BC + jj;
+    const size_t tb = la.f0 + (size_t)cl * 12 * g.V * BC;
+    const int ntiles = (g.V + TM::SPB - 1) / TM::SPB;
+    const int tile0 = blockIdx.x * tpb, ntb = min(ntiles, tile0 + tpb) - tile0;
+    const df64 a(alpha[j]), sh(la.s0);
+    stage::RunnerDF<true, BC, stage::NSTAGE_DF> run(dsm, g, (const df64c *)la.U, t + tb, tile0, ntb, err);
+    double ar = 0;
+    for (int tl = 0; tl < ntb; ++tl) {
+        const int s = (tile0 + tl) * TM::SPB + threadIdx.x / BC;
+        const bool valid = s < g.V;
+        df64c acc[12][1];
+        run.hops(tl, s, valid, acc);
+        if (!valid) continue;
+        df64 sr = 0;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t o = tb + ((size_t)s * 12 + c) * BC + jj;
+            const df64c tv = t[o], pv = p[o];
+            df64c rv = r[o];
+            df64c apv;
+            apv.x = tv.x - kappa * acc[c][0].x + sh * pv.x;
+            apv.y = tv.y - kappa * acc[c][0].y + sh * pv.y;
+            rv.x -= a * apv.x;
+            rv.y -= a * apv.y;
+            sr += rv.x * rv.x + rv.y * rv.y;
+            r[o] = rv;
+        }
+        ar += (double)sr;
+    }
+    const double s1 = block_sum<BC>(ar, sm);
+    if (threadIdx.x < BC) part_r[(prow + blockIdx.x) * BC + threadIdx.x] = s1;
+    fuse_step2<BC, TM::THREADS>(f, l, part_r, prow, G, sm);
+}
+
+template <int BC, bool M> cudaError_t staged_df_attrs() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const int bytes = (int)stage::DimsDF<BC, stage::NSTAGE_DF>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_a_dfst<BC, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_b_dfst<BC, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done = e == cudaSuccess;
+    return e;
 }
 
 // the dynamic shared memory of the staged pair (above the 48 KB default)
@@ -1313,7 +1424,8 @@ template <int BC> struct Solve {
     int chk;
     bool shifts;
     int tpb_hi = TPB, tpb_lo = TPB, nr = 1;
-    bool stg = false; // FP32 iterations: the D_W pair with staged neighbours (stage.cuh)
+    bool stg = false;    // FP32 iterations: the D_W pair with staged neighbours (stage.cuh)
+    bool stg_df = false; // float-float iterations: likewise
 
     explicit Solve(const std::vector<LatIn> &lats) : ctx(lats[0].ctx), in(lats), nl((int)lats.size()) {}
 
@@ -1362,7 +1474,8 @@ template <int BC> struct Solve {
         tpb_hi = std::max(1, in[0].spec->tpb_hi > 0 ? in[0].spec->tpb_hi : TPB);
         tpb_lo = std::max(1, in[0].spec->tpb_lo > 0 ? in[0].spec->tpb_lo : TPB);
         nr = in[0].spec->nr == 2 ? 2 : 1;
-        stg = in[0].spec->staged != 0 && BC >= 12; // (one-column tiles: plain loads)
+        stg = (in[0].spec->staged & 1) && BC >= 12; // (one-column tiles: plain loads)
+        stg_df = (in[0].spec->staged & 2) && BC >= 12;
         if (stg && nr == 2) return set_err(ctx, SMPQ_EINVAL, "internal: the staged D_W has one column per thread");
         std::vector<Buf> &ws = ctx->ws;
         if (ws.size() < W_COUNT) ws.resize(W_COUNT);
@@ -1526,10 +1639,18 @@ template <int BC> struct Solve {
         const int tpb = hi ? tpb_hi : tpb_lo;
         const bool two_cols = std::is_same<T, float>::value && !half && nr == 2 && BC % 2 == 0 && !multi;
         constexpr bool can_stage = std::is_same<T, float>::value && !half && BC >= 12;
+        constexpr bool can_stage_df = std::is_same<T, df64>::value && BC >= 12;
         const bool staged = can_stage && stg;
+        const bool staged_df = can_stage_df && stg_df;
         if constexpr (can_stage) {
             if (staged) { // before any capture: the kernels' shared-memory limit
                 const cudaError_t e = multi ? staged_attrs<BC, true>() : staged_attrs<BC, false>();
+                if (e != cudaSuccess) return cuda_check(ctx, e, "staged D_W attributes");
+            }
+        }
+        if constexpr (can_stage_df) {
+            if (staged_df) {
+                const cudaError_t e = multi ? staged_df_attrs<BC, true>() : staged_df_attrs<BC, false>();
                 if (e != cudaSuccess) return cuda_check(ctx, e, "staged D_W attributes");
             }
         }
@@ -1543,6 +1664,7 @@ template <int BC> struct Solve {
         // enters the shifted systems; the mixed solve's FP32 phase)
         const double delta2 = rel && replace_mid ? delta * delta : 0.0;
         const T kappa = (T)ctx->opt.kappa;
+        const double kd = ctx->opt.kappa;
         const int per_iter = 3;
         if constexpr (half) {
             if (!rel || !xlo || !xhi || !t64)
@@ -1637,12 +1759,31 @@ template <int BC> struct Solve {
                         const dim3 gridn(gx, nchunk);
                         const size_t smem = stage::Dims<BC, stage::NSTAGE>::SMEM;
                         if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-                        k_apply_a_st<BC, M><<<gridn, TH, smem, st>>>(Ld, p, t, kappa, part0, part1, tpb, f1,
+                        k_apply_a_st<BC, M><<<gridn, TH, smem, st>>>(Ld, p, t, kd, part0, part1, tpb, f1,
                                                                       sc.flags + 4);
                         if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
                         if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
-                        k_apply_b_st<BC, M><<<gridn, TH, smem, st>>>(Ld, t, p, r, sc.alpha, kappa, part2, tpb, f2,
+                        k_apply_b_st<BC, M><<<gridn, TH, smem, st>>>(Ld, t, p, r, sc.alpha, kd, part2, tpb, f2,
                                                                       sc.flags + 4);
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
+                        k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p,
+                                                                  xacc, xlo);
+                        return;
+                    }
+                }
+                if constexpr (can_stage_df && NR == 1) {
+                    if (staged_df) {
+                        int gx;
+                        const Lats Ld = lats_dw<T>(TileMap<BC>::SPB, tpb, &gx);
+                        const dim3 gridn(gx, nchunk);
+                        const size_t smem = stage::DimsDF<BC, stage::NSTAGE_DF>::SMEM;
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
+                        k_apply_a_dfst<BC, M><<<gridn, TH, smem, st>>>(Ld, p, t, kappa, part0, part1, tpb, f1,
+                                                                        sc.flags + 4);
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
+                        if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
+                        k_apply_b_dfst<BC, M><<<gridn, TH, smem, st>>>(Ld, t, p, r, sc.alpha, kappa, part2, tpb, f2,
+                                                                        sc.flags + 4);
                         if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
                         k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p,
                                                                   xacc, xlo);
@@ -1655,10 +1796,10 @@ template <int BC> struct Solve {
                     const Lats Ld = lats_dw<T>(TMN::SPB, tpb, &gx);
                     const dim3 gridn(gx, nchunk);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k], st);
-                    k_apply_a<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, p, t, kappa, part0, part1, tpb, f1);
+                    k_apply_a<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, p, t, kd, part0, part1, tpb, f1);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 1], st);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 2], st);
-                    k_apply_b<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, t, p, r, sc.alpha, kappa, part2, tpb,
+                    k_apply_b<T, BC, NR, M><<<gridn, TMN::THREADS, 0, st>>>(Ld, t, p, r, sc.alpha, kd, part2, tpb,
                                                                             f2);
                     if (prof) cudaEventRecord(ctx->prof_ev[4 * k + 3], st);
                     k_yp<T, TS, BC, M><<<gridyp, TH, 0, st>>>(Lyp, nshift, B, rhs_class, r, ps, y, sc, spd, p, xacc, xlo);
@@ -1678,8 +1819,8 @@ template <int BC> struct Solve {
                 const Geom &g = in[l].ctx->geom;
                 const df64c *Udf = (const df64c *)in[l].ctx->Udf.p;
                 k_rel_accum<T, BC><<<grid, TH, 0, st>>>(V[l], xhi + o, xlo + o, G1[l]);
-                k_apply_a<df64, BC, 1, false><<<grid, TH, 0, st>>>(lats_one<df64>(l), xhi, t64, kdf, part0, part1,
-                                                                   TPB, none);
+                k_apply_a<df64, BC, 1, false><<<grid, TH, 0, st>>>(lats_one<df64>(l), xhi, t64, ctx->opt.kappa, part0,
+                                                                   part1, TPB, none);
                 k_rel_resid_df<T, BC><<<grid, TH, 0, st>>>(g, Udf, t64 + o, xhi + o, srcl[l], r + o, sph[l].s0, kdf,
                                                            part2 + p0[l] * BC, G1[l]);
                 ctx->launches += 3;
@@ -1746,7 +1887,7 @@ template <int BC> struct Solve {
             if (e != cudaSuccess) { status = cuda_check(ctx, e, "multishift iteration"); break; }
             collect(ck, hi);
             if (hflags[4]) {
-                status = set_err(ctx, SMPQ_ECUDA, "a shared-memory staging wait of the FP32 D_W timed out");
+                status = set_err(ctx, SMPQ_ECUDA, "a shared-memory staging wait of the D_W timed out");
                 break;
             }
             if (hflags[2]) { status = set_err(ctx, SMPQ_EBREAKDOWN, "CG breakdown: <p,Ap> <= 0 or not finite"); break; }
@@ -1819,7 +1960,7 @@ template <int BC> struct Solve {
             const size_t o = f0[l];
             const df64c *Udf = (const df64c *)in[l].ctx->Udf.p;
             k_rel_accum<float, BC><<<grid, TH, 0, st>>>(V[l], xhi + o, xlo + o, G1[l]);
-            k_apply_a<df64, BC, 1, false><<<grid, TH, 0, st>>>(lats_one<df64>(l), xhi, t64, kdf, part0, part1, TPB,
+            k_apply_a<df64, BC, 1, false><<<grid, TH, 0, st>>>(lats_one<df64>(l), xhi, t64, ctx->opt.kappa, part0, part1, TPB,
                                                                none);
             k_rel_resid_df<float, BC><<<grid, TH, 0, st>>>(in[l].ctx->geom, Udf, t64 + o, xhi + o, srcl[l], rs + o,
                                                            sph[l].s0, kdf, part2 + p0[l] * BC, G1[l]);
@@ -1931,9 +2072,11 @@ template <int BC> struct Solve {
             // phase 2: FP32 vectors and D_W from the phase-1 state, without
             // residual replacement: the FP32 rounding of these iterations makes
             // the base residual drift from the true one by about u_32 theta
-            // times a growth factor (measured: 2e-9 at theta = 7e-3), and the
-            // shifted systems drift alike; their drifts largely cancel in
-            // y = sum_i c_i x_i.  With true_residual 2 the base system alone is
+            // times a growth factor (measured about 64 u_32 theta: 2.7e-8 at
+            // theta = 7e-3), and the shifted systems drift alike.  The drift
+            // is smooth over the lattice, so its share of Q = sum_x q(x) does
+            // not average out: at theta >= 2e-3 |dQ| over 8^3 x 16 reached
+            // 0.5-1.4e-9 for some switch points, at 1e-3 it stays below 3e-11.  With true_residual 2 the base system alone is
             // corrected once every shift has converged (one replacement, then
             // its CG restarts from the true residual): its residual meets tol,
             // but the correction no longer cancels against the other shifts'
@@ -2161,14 +2304,13 @@ float time_pair(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part
     const size_t nf = (size_t)B * 12 * V;
     C *p = (C *)buf, *t = p + nf, *r = t + nf;
     const Lats L = lats_single(ctx, Links<T>::get(ctx), GN);
-    const T kappa = (T)ctx->opt.kappa;
     cudaStream_t st = ctx->stream;
     const dim3 gridn(GN, nchunk);
     Fuse none{}; // timing only: no scalar step
     return time_launches(ctx, reps, [&]() {
-        k_apply_a<T, BC, NR, false><<<gridn, TM::THREADS, 0, st>>>(L, p, t, kappa, part,
+        k_apply_a<T, BC, NR, false><<<gridn, TM::THREADS, 0, st>>>(L, p, t, ctx->opt.kappa, part,
                                                                     part + (size_t)nchunk * GN * BC, tpb, none);
-        k_apply_b<T, BC, NR, false><<<gridn, TM::THREADS, 0, st>>>(L, t, p, r, alpha, kappa, part, tpb, none);
+        k_apply_b<T, BC, NR, false><<<gridn, TM::THREADS, 0, st>>>(L, t, p, r, alpha, ctx->opt.kappa, part, tpb, none);
     });
 }
 
@@ -2182,7 +2324,7 @@ float time_pair_staged(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, doubl
     const size_t nf = (size_t)B * 12 * V;
     float2 *p = (float2 *)buf, *t = p + nf, *r = t + nf;
     const Lats L = lats_single(ctx, Links<float>::get(ctx), GN);
-    const float kappa = (float)ctx->opt.kappa;
+    const double kappa = ctx->opt.kappa;
     cudaStream_t st = ctx->stream;
     const dim3 gridn(GN, nchunk);
     const size_t smem = stage::Dims<BC, stage::NSTAGE>::SMEM;
@@ -2195,6 +2337,37 @@ float time_pair_staged(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, doubl
         k_apply_a_st<BC, false><<<gridn, TM::THREADS, smem, st>>>(L, p, t, kappa, part,
                                                                    part + (size_t)nchunk * GN * BC, tpb, none, err);
         k_apply_b_st<BC, false><<<gridn, TM::THREADS, smem, st>>>(L, t, p, r, alpha, kappa, part, tpb, none, err);
+    });
+    int h = 0;
+    if (ms < 0 || cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || h) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    return ms;
+}
+
+// the float-float pair with staged neighbours; -1 if a staging wait ran out
+template <int BC>
+float time_pair_dfstaged(smpq_ctx *ctx, int B, int tpb, int reps, void *buf, double *part, double *alpha, int *err) {
+    typedef TileMap<BC> TM;
+    const int V = ctx->V, nchunk = B / BC;
+    const int GN = ((V + TM::SPB - 1) / TM::SPB + tpb - 1) / tpb;
+    const size_t nf = (size_t)B * 12 * V;
+    df64c *p = (df64c *)buf, *t = p + nf, *r = t + nf;
+    const Lats L = lats_single(ctx, Links<df64>::get(ctx), GN);
+    const df64 kappa(ctx->opt.kappa);
+    cudaStream_t st = ctx->stream;
+    const dim3 gridn(GN, nchunk);
+    const size_t smem = stage::DimsDF<BC, stage::NSTAGE_DF>::SMEM;
+    if (staged_df_attrs<BC, false>() != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    Fuse none{};
+    const float ms = time_launches(ctx, reps, [&]() {
+        k_apply_a_dfst<BC, false><<<gridn, TM::THREADS, smem, st>>>(L, p, t, kappa, part,
+                                                                     part + (size_t)nchunk * GN * BC, tpb, none, err);
+        k_apply_b_dfst<BC, false><<<gridn, TM::THREADS, smem, st>>>(L, t, p, r, alpha, kappa, part, tpb, none, err);
     });
     int h = 0;
     if (ms < 0 || cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || h) {
@@ -2238,6 +2411,7 @@ template <int BC> float time_kind(smpq_ctx *ctx, int kind, int B, int tpb, int n
     case 3: return time_pair_half<H16, BC>(ctx, B, tpb, reps, buf, part, alpha);
     case 4: return time_pair_half<B16, BC>(ctx, B, tpb, reps, buf, part, alpha);
     case 5: return time_pair_staged<BC>(ctx, B, tpb, reps, buf, part, alpha, err);
+    case 6: return time_pair_dfstaged<BC>(ctx, B, tpb, reps, buf, part, alpha, err);
     default: return -1.f;
     }
 }

@@ -64,7 +64,7 @@ struct smpq_ctx {
     struct Tuned {
         std::array<int, 4> dims;
         int B, prec;
-        std::array<int, 5> shape; // bc, tpb_hi, tpb_lo, nr, staged
+        std::array<int, 5> shape; // bc, tpb_hi, tpb_lo, nr, staged (bits: FP32, float-float)
         int from_file;
     };
     std::vector<Tuned> tuned;
@@ -151,7 +151,8 @@ struct SolveSpec {
     // block in the FP64-accurate and in the FP32 / half iterations, columns
     // per thread of the FP32 kernels (1 or 2)
     int tpb_hi, tpb_lo, nr;
-    int staged; // FP32 iterations: the D_W pair with neighbours staged in shared memory (nr = 1)
+    int staged; // D_W pair with neighbours staged in shared memory: bit 0 the FP32 iterations
+                // (nr = 1), bit 1 the float-float iterations
 };
 struct SolveOut {
     // y = R(H^2) b on the support, FP64, layout [j/BC][n_sup][12][BC] (the field
@@ -191,7 +192,8 @@ int lowmodes_dov_project(smpq_ctx *ctx, const double2 *b, double2 *bperp, int B,
 int lowmodes_dov_finish(smpq_ctx *ctx, double2 *out, int B, const std::vector<double> &wd, cudaStream_t st);
 // autotuner: average ms of one D_W + D_W^dag-update launch pair of the
 // iterations of `kind` (0 FP64, 1 FP32, 2 float-float, 3 FP16 + norms,
-// 4 BF16 + norms, 5 FP32 with staged neighbours) for B columns in tiles of BC,
+// 4 BF16 + norms, 5 FP32 with staged neighbours, 6 float-float with staged
+// neighbours) for B columns in tiles of BC,
 // tpb tiles per block and nr columns per thread (FP32: 1 or 2).  Scratch in
 // buf: 3 fields of B x 12 x V complex values of the kind; part: 2 * B * V / 12
 // doubles of partials; alpha: B doubles; err: one int, zero on entry (kind 5

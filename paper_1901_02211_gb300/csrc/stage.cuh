@@ -86,23 +86,47 @@ constexpr int NSTAGE = 3; // stage buffers: two steps of copies in flight during
 constexpr long long WAIT_LIMIT = 1LL << 31;   // about a second at 2 GHz
 constexpr long long CLEANUP_LIMIT = 1LL << 28; // per outstanding stage after a failure
 
-// Shared-memory footprint of the stages (bytes), without the barriers
+// 8-byte asynchronous copy global -> shared (the FP32 links: 72 bytes each, so
+// not aligned for the bulk engine), completed per thread by commit / wait groups
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float2 lds2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+
+
+// Shared-memory layout of the stages: NS field stages of SPB sites, NS link
+// stages of SPB links (9 complex values each), NS barriers
 template <int BC, int NS> struct Dims {
     typedef TileMap<BC, 1> TM;
     static constexpr int SITE = 12 * BC;           // complex values of one site (one RHS tile)
-    static constexpr int STAGE = TM::SPB * SITE;   // one stage: SPB neighbour sites
+    static constexpr int STAGE = TM::SPB * SITE;   // one field stage: SPB neighbour sites
+    static constexpr int LSTAGE = TM::SPB * 9;     // one link stage: the link of each site's hop
     static constexpr uint32_t SITE_BYTES = SITE * sizeof(float2);
-    static constexpr size_t SMEM = (size_t)NS * STAGE * sizeof(float2) + NS * sizeof(uint64_t);
+    static constexpr size_t LINK_OFF = (size_t)NS * STAGE * sizeof(float2);
+    static constexpr size_t BAR_OFF = LINK_OFF + (size_t)NS * LSTAGE * sizeof(float2);
+    static constexpr size_t SMEM = BAR_OFF + NS * sizeof(uint64_t);
 };
 
-// Issue the copies of step k (hop k % 8 of tile tile0 + k / 8) into stage k % NS.
-// Called by the 32 lanes of warp 0.
+// Issue the copies of step k (hop k % 8 of tile tile0 + k / 8) into stage
+// k % NS: lane i < SPB copies the neighbour site of block site i (bulk copy on
+// the stage's barrier) and the hop's link (nine 8-byte copies); every lane
+// then commits one copy group, so that group j of a lane is always step j.
+// Called by the 32 lanes of warp 0, with k < K.
 template <int BC, int NS>
-__device__ __forceinline__ void issue(const Geom &g, const float2 *__restrict__ in, int tile0, int k, float2 *stages,
-                                      uint64_t *bar) {
+__device__ __forceinline__ void issue(const Geom &g, const float2 *__restrict__ U, const float2 *__restrict__ in,
+                                      int tile0, int k, unsigned char *smem, uint64_t *bar) {
     typedef Dims<BC, NS> D;
     const int lane = threadIdx.x & 31;
     const int tile = tile0 + k / 8, h = k % 8, mu = h >> 1, st = k % NS;
+    const bool back = h & 1;
     const int s0 = tile * D::TM::SPB;
     const int nvalid = min(D::TM::SPB, g.V - s0);
     if (lane == 0) {
@@ -112,34 +136,68 @@ __device__ __forceinline__ void issue(const Geom &g, const float2 *__restrict__ 
     const int n = g.n[mu], sd = g.stride[mu];
     for (int i = lane; i < nvalid; i += 32) {
         const int s = s0 + i, c = (s / sd) % n;
-        const int nb = (h & 1) ? (c == 0 ? s + (n - 1) * sd : s - sd) : (c == n - 1 ? s - (n - 1) * sd : s + sd);
-        bulk_g2s(stages + (size_t)st * D::STAGE + (size_t)i * D::SITE, in + (size_t)nb * D::SITE, D::SITE_BYTES,
-                 &bar[st]);
+        const int nb = back ? (c == 0 ? s + (n - 1) * sd : s - sd) : (c == n - 1 ? s - (n - 1) * sd : s + sd);
+        bulk_g2s(smem + ((size_t)st * D::STAGE + (size_t)i * D::SITE) * sizeof(float2), in + (size_t)nb * D::SITE,
+                 D::SITE_BYTES, &bar[st]);
+        // the link of a forward hop sits on the site, of a backward hop on the neighbour
+        const float2 *u = U + ((size_t)mu * g.V + (back ? nb : s)) * 9;
+        const uint32_t dst = smem_u32(smem + D::LINK_OFF + ((size_t)st * D::LSTAGE + (size_t)i * 9) * sizeof(float2));
+#pragma unroll
+        for (int e = 0; e < 9; ++e) cp_async8(dst + e * sizeof(float2), u + e);
     }
+    cp_async_commit();
 }
 
-// The hop of step H (compile-time direction and orientation) for site s from
-// the staged neighbour q (shared memory, this thread's column).
-template <int H, bool DAG, int BC>
-__device__ __forceinline__ void hop_staged(const Geom &g, const SiteCoords &xc, const float2 *__restrict__ U,
-                                           const float2 *q, int s, float2 acc[12][1]) {
-    constexpr int MU = H >> 1;
-    constexpr bool BACK = H & 1;
-    const int n = g.n[MU], sd = g.stride[MU], c = xc.x[MU];
-    const bool edge = BACK ? c == 0 : c == n - 1;
-    const bool flip = edge && g.bcf[MU] < 0;
-    // the link of a backward hop sits on the neighbour site
-    const int ls = BACK ? (edge ? s + (n - 1) * sd : s - sd) : s;
-    // forward: (1 - g) U(x) psi(x+mu) [DAG: (1 + g)]; backward: (1 + g) U(x-mu)^dag psi(x-mu) [DAG: (1 - g)]
-    constexpr int SG = BACK ? (DAG ? -1 : +1) : (DAG ? +1 : -1);
-    hop_one<float, MU, SG, BACK, BC, 1>(U, q, g.V, g.V, 0, ls, flip, acc);
+// One hop for one column, neighbour spinor and link read from the stages
+// (shared addresses q: component 0 of this column, components BC apart; ul:
+// the 9 link elements).  The arithmetic and its order are those of hop_one.
+template <int MU, int SG, bool BACK, int BC>
+__device__ __forceinline__ void hop_smem(uint32_t q, uint32_t ul, bool flip, float2 acc[12][1]) {
+    constexpr uint32_t CS = BC * sizeof(float2); // bytes between components
+    float2 h[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 p0 = lds2(q + a * CS), p1 = lds2(q + (3 + a) * CS);
+        const float2 p2 = lds2(q + (6 + a) * CS), p3 = lds2(q + (9 + a) * CS);
+        float2 s0, s1;
+        s_apply<MU>(p2, p3, s0, s1);
+        if (SG > 0) { h[0][a] = cadd(p0, s0); h[1][a] = cadd(p1, s1); }
+        else { h[0][a] = csub(p0, s0); h[1][a] = csub(p1, s1); }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float2 ur[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ur[b] = lds2(ul + (BACK ? b * 3 + a : a * 3 + b) * sizeof(float2));
+        float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (BACK) {
+                w0 = cfmac(ur[b], h[0][b], w0);
+                w1 = cfmac(ur[b], h[1][b], w1);
+            } else {
+                w0 = cfma(ur[b], h[0][b], w0);
+                w1 = cfma(ur[b], h[1][b], w1);
+            }
+        }
+        if (flip) {
+            w0 = cneg(w0);
+            w1 = cneg(w1);
+        }
+        acc[a][0] = cadd(acc[a][0], w0);
+        acc[3 + a][0] = cadd(acc[3 + a][0], w1);
+        float2 l0, l1;
+        sdag_apply<MU>(w0, w1, l0, l1);
+        if (SG > 0) { acc[6 + a][0] = cadd(acc[6 + a][0], l0); acc[9 + a][0] = cadd(acc[9 + a][0], l1); }
+        else { acc[6 + a][0] = csub(acc[6 + a][0], l0); acc[9 + a][0] = csub(acc[9 + a][0], l1); }
+    }
 }
 
 // Block state of a staged D_W launch: the stage buffers and barriers in
 // dynamic shared memory, the block's lattice tiles, the step counter.
 template <bool DAG, int BC, int NS> struct Runner {
     typedef Dims<BC, NS> D;
-    float2 *stages;
+    unsigned char *smem;
     uint64_t *bar;
     const Geom &g;
     const float2 *__restrict__ U;
@@ -148,11 +206,10 @@ template <bool DAG, int BC, int NS> struct Runner {
     bool dead;
     int *err;
 
-    __device__ Runner(unsigned char *smem, const Geom &g_, const float2 *U_, const float2 *in_, int tile0_, int ntb_,
+    __device__ Runner(unsigned char *smem_, const Geom &g_, const float2 *U_, const float2 *in_, int tile0_, int ntb_,
                       int *err_)
-        : g(g_), U(U_), in(in_), tile0(tile0_), ntb(ntb_), dead(false), err(err_) {
-        stages = reinterpret_cast<float2 *>(smem);
-        bar = reinterpret_cast<uint64_t *>(smem + (size_t)NS * D::STAGE * sizeof(float2));
+        : smem(smem_), g(g_), U(U_), in(in_), tile0(tile0_), ntb(ntb_), dead(false), err(err_) {
+        bar = reinterpret_cast<uint64_t *>(smem + D::BAR_OFF);
         K = 8 * max(ntb, 0);
         bool failed = false;
         if (threadIdx.x == 0) {
@@ -163,28 +220,57 @@ template <bool DAG, int BC, int NS> struct Runner {
         // once any block of the launch (or an earlier one) has timed out, the
         // block issues and waits for nothing: a failure costs one round of blocks
         dead = __syncthreads_or(failed) != 0;
-        if (!dead && threadIdx.x < 32)
-            for (int k = 0; k < NS && k < K; ++k) issue<BC, NS>(g, in, tile0, k, stages, bar);
+        if (!dead && threadIdx.x < 32) {
+            for (int k = 0; k < NS; ++k) {
+                if (k < K) issue<BC, NS>(g, U, in, tile0, k, smem, bar);
+                else cp_async_commit();
+            }
+            cp_async_wait<NS - 1>(); // the links of step 0
+        }
+        __syncthreads();
     }
 
     // the 8 hops of lattice tile tl of the block for site s (valid: s < V) into acc
     __device__ __forceinline__ void hops(int tl, int s, bool valid, float2 acc[12][1]) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c][0] = make_float2(0.f, 0.f);
-        const SiteCoords xc(g, valid ? s : 0);
+        // boundary signs of the 8 hops of this site (antiperiodic directions)
+        unsigned flips = 0;
+        {
+            const SiteCoords xc(g, valid ? s : 0);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu)
+                if (g.bcf[mu] < 0) {
+                    if (xc.x[mu] == g.n[mu] - 1) flips |= 1u << (2 * mu);
+                    if (xc.x[mu] == 0) flips |= 1u << (2 * mu + 1);
+                }
+        }
         const int i = threadIdx.x / BC, jj = threadIdx.x % BC;
+        const uint32_t q0 = smem_u32(smem) + (uint32_t)((i * D::SITE + jj) * sizeof(float2));
+        const uint32_t u0 = smem_u32(smem + D::LINK_OFF) + (uint32_t)(i * 9 * sizeof(float2));
         auto step = [&](auto hc) {
             constexpr int H = decltype(hc)::value;
+            constexpr int MU = H >> 1;
+            constexpr bool BACK = H & 1;
+            // forward: (1 - g) U(x) psi(x+mu) [DAG: (1 + g)]; backward: (1 + g) U(x-mu)^dag psi(x-mu) [DAG: (1 - g)]
+            constexpr int SG = BACK ? (DAG ? -1 : +1) : (DAG ? +1 : -1);
             const int k = tl * 8 + H, st = k % NS;
             bool ok = true;
             if (!dead) ok = mbar_wait(&bar[st], (uint32_t)((k / NS) & 1), WAIT_LIMIT);
             if (!dead && valid)
-                hop_staged<H, DAG, BC>(g, xc, U, stages + (size_t)st * D::STAGE + (size_t)i * D::SITE + jj, s, acc);
+                hop_smem<MU, SG, BACK, BC>(q0 + (uint32_t)(st * D::STAGE * sizeof(float2)),
+                                           u0 + (uint32_t)(st * D::LSTAGE * sizeof(float2)), (flips >> H) & 1u, acc);
+            // warp 0: the links of step k + 1 have arrived (its group; the
+            // later NS - 2 may still be in flight) before the barrier
+            if (!dead && threadIdx.x < 32) cp_async_wait<NS - 2>();
             if (__syncthreads_or(!ok)) {
                 if (!dead) fail(k);
                 return;
             }
-            if (!dead && threadIdx.x < 32 && k + NS < K) issue<BC, NS>(g, in, tile0, k + NS, stages, bar);
+            if (!dead && threadIdx.x < 32) {
+                if (k + NS < K) issue<BC, NS>(g, U, in, tile0, k + NS, smem, bar);
+                else cp_async_commit(); // an empty group keeps group j = step j
+            }
         };
         step(std::integral_constant<int, 0>());
         step(std::integral_constant<int, 1>());
@@ -198,6 +284,134 @@ template <bool DAG, int BC, int NS> struct Runner {
 
     // a wait ran out at step k (block-uniform): report it, wait with a bound
     // for the copies still in flight (steps k .. k + NS - 1), stop computing
+    __device__ void fail(int k) {
+        dead = true;
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1);
+            for (int kk = k; kk < k + NS && kk < K; ++kk)
+                mbar_wait(&bar[kk % NS], (uint32_t)((kk / NS) & 1), CLEANUP_LIMIT);
+        }
+        if (threadIdx.x < 32) cp_async_wait<0>();
+        __syncthreads();
+    }
+};
+
+// ------------------------------------------------------------------ float-float
+// The float-float D_W (16-byte complex values) staged the same way, with two
+// stages (one step of copies in flight: a float-float hop is long enough to
+// cover it, and two 46 KB stages leave room for two blocks per SM).  The link
+// of a hop (9 x 16 bytes) is 16-byte aligned, so it travels by bulk copy on
+// the same barrier as the neighbour site.  The hop loop stays rolled (the
+// unrolled float-float hop overflows the instruction cache) and uses the
+// packed two-lane hop of wilson.cuh with shared-memory operands.
+template <int BC, int NS> struct DimsDF {
+    typedef TileMap<BC, 1> TM;
+    static constexpr int SITE = 12 * BC;
+    static constexpr int STAGE = TM::SPB * SITE;
+    static constexpr int LSTAGE = TM::SPB * 9;
+    static constexpr uint32_t SITE_BYTES = SITE * sizeof(df64c);
+    static constexpr uint32_t LINK_BYTES = 9 * sizeof(df64c);
+    static constexpr size_t LINK_OFF = (size_t)NS * STAGE * sizeof(df64c);
+    static constexpr size_t BAR_OFF = LINK_OFF + (size_t)NS * LSTAGE * sizeof(df64c);
+    static constexpr size_t SMEM = BAR_OFF + NS * sizeof(uint64_t);
+};
+constexpr int NSTAGE_DF = 2;
+
+template <int BC, int NS>
+__device__ __forceinline__ void issue_df(const Geom &g, const df64c *__restrict__ U, const df64c *__restrict__ in,
+                                         int tile0, int k, unsigned char *smem, uint64_t *bar) {
+    typedef DimsDF<BC, NS> D;
+    const int lane = threadIdx.x & 31;
+    const int tile = tile0 + k / 8, h = k % 8, mu = h >> 1, st = k % NS;
+    const bool back = h & 1;
+    const int s0 = tile * D::TM::SPB;
+    const int nvalid = min(D::TM::SPB, g.V - s0);
+    if (lane == 0) {
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[st], (uint32_t)nvalid * (D::SITE_BYTES + D::LINK_BYTES));
+    }
+    const int n = g.n[mu], sd = g.stride[mu];
+    for (int i = lane; i < nvalid; i += 32) {
+        const int s = s0 + i, c = (s / sd) % n;
+        const int nb = back ? (c == 0 ? s + (n - 1) * sd : s - sd) : (c == n - 1 ? s - (n - 1) * sd : s + sd);
+        bulk_g2s(smem + ((size_t)st * D::STAGE + (size_t)i * D::SITE) * sizeof(df64c), in + (size_t)nb * D::SITE,
+                 D::SITE_BYTES, &bar[st]);
+        bulk_g2s(smem + D::LINK_OFF + ((size_t)st * D::LSTAGE + (size_t)i * 9) * sizeof(df64c),
+                 U + ((size_t)mu * g.V + (back ? nb : s)) * 9, D::LINK_BYTES, &bar[st]);
+    }
+}
+
+template <bool DAG, int BC, int NS> struct RunnerDF {
+    typedef DimsDF<BC, NS> D;
+    unsigned char *smem;
+    uint64_t *bar;
+    const Geom &g;
+    const df64c *__restrict__ U;
+    const df64c *__restrict__ in;
+    int tile0, ntb, K;
+    bool dead;
+    int *err;
+
+    __device__ RunnerDF(unsigned char *smem_, const Geom &g_, const df64c *U_, const df64c *in_, int tile0_,
+                        int ntb_, int *err_)
+        : smem(smem_), g(g_), U(U_), in(in_), tile0(tile0_), ntb(ntb_), dead(false), err(err_) {
+        bar = reinterpret_cast<uint64_t *>(smem + D::BAR_OFF);
+        K = 8 * max(ntb, 0);
+        bool failed = false;
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+            fence_barrier_init();
+            failed = *(volatile int *)err != 0;
+        }
+        dead = __syncthreads_or(failed) != 0;
+        if (!dead && threadIdx.x < 32)
+            for (int k = 0; k < NS && k < K; ++k) issue_df<BC, NS>(g, U, in, tile0, k, smem, bar);
+    }
+
+    // the 8 hops of lattice tile tl for site s (valid: s < V): acc = hop(s)
+    __device__ __forceinline__ void hops(int tl, int s, bool valid, df64c acc[12][1]) {
+        f2c accU[3], accL[3];
+        const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) accU[a] = accL[a] = f2c{z, z, z, z};
+        const SiteCoords xc(g, valid ? s : 0);
+        const int i = threadIdx.x / BC, jj = threadIdx.x % BC;
+        const df64c *qs = reinterpret_cast<const df64c *>(smem) + (size_t)i * D::SITE + jj;
+        const df64c *us = reinterpret_cast<const df64c *>(smem + D::LINK_OFF) + (size_t)i * 9;
+#pragma unroll 1
+        for (int h = 0; h < 8; ++h) {
+            const int k = tl * 8 + h, st = k % NS;
+            bool ok = true;
+            if (!dead) ok = mbar_wait(&bar[st], (uint32_t)((k / NS) & 1), WAIT_LIMIT);
+            if (!dead && valid) {
+                const int mu = h >> 1;
+                const bool back = h & 1;
+                const bool edge = back ? xc.x[mu] == 0 : xc.x[mu] == g.n[mu] - 1;
+                const bool flip = edge && g.bcf[mu] < 0;
+                // forward: (1 - g) [DAG: (1 + g)], backward: (1 + g) [DAG: (1 - g)]
+                hop_one_pairs<BC>(mu, back != DAG, back, us + (size_t)st * D::LSTAGE, qs + (size_t)st * D::STAGE, 0,
+                                  0, 0, flip, accU, accL);
+            }
+            if (__syncthreads_or(!ok)) {
+                if (!dead) fail(k);
+                continue;
+            }
+            if (!dead && threadIdx.x < 32 && k + NS < K) issue_df<BC, NS>(g, U, in, tile0, k + NS, smem, bar);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float2 xh, xl, yh, yl;
+            two_sum2(accU[a].xh, accU[a].xl, xh, xl);
+            two_sum2(accU[a].yh, accU[a].yl, yh, yl);
+            acc[a][0] = {df64(xh.x, xl.x), df64(yh.x, yl.x)};
+            acc[3 + a][0] = {df64(xh.y, xl.y), df64(yh.y, yl.y)};
+            two_sum2(accL[a].xh, accL[a].xl, xh, xl);
+            two_sum2(accL[a].yh, accL[a].yl, yh, yl);
+            acc[6 + a][0] = {df64(xh.x, xl.x), df64(yh.x, yl.x)};
+            acc[9 + a][0] = {df64(xh.y, xl.y), df64(yh.y, yl.y)};
+        }
+    }
+
     __device__ void fail(int k) {
         dead = true;
         if (threadIdx.x == 0) {

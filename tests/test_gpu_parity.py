@@ -352,7 +352,8 @@ def mixed_resid_bar(theta):
 
 
 @pytest.mark.parametrize("r,classes", [(2, [0, 9]), (4, [0, 77, 255])])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed7e-3", "mixed1e-2", "mixed3e-2", "fp16n", "bf16n"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed1e-4", "mixed1e-3", "mixed7e-3", "mixed1e-2", "mixed3e-2", "fp16n",
+                                  "bf16n"])
 def test_qx_8x16_sampled(S, r, classes, prec):
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
@@ -362,7 +363,7 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     ref, _ = qx.smp_qx(U, dims, KAPPA, zolo, colour, n, colours=classes, batch_colours=len(classes))
     precision = S.SMPQ_MIXED if prec.startswith("mixed") else {
         "fp64": S.SMPQ_FP64, "fp32": S.SMPQ_FP32, "fp16n": S.SMPQ_FP16N, "bf16n": S.SMPQ_BF16N}[prec]
-    switch = float(prec[5:]) if prec.startswith("mixed") else 7e-3
+    switch = float(prec[5:]) if prec.startswith("mixed") else 1e-3
     with _session(S, precision=precision, switch_residual=switch, true_residual=1) as s:
         s.load_gauge(dims, U)
         s.set_spectrum(a, b)
@@ -384,9 +385,11 @@ def test_qx_8x16_sampled(S, r, classes, prec):
     # FP64 and the FP64-then-FP32 path meet the 1e-8 per-site bar; the FP32
     # path with FP64 reliable updates has the FP32 floor of its shifted systems.
     # The per-site error of the mixed path grows with the switch point (about
-    # 1e-8 theta); the sum over the 1024 sites of r = 2 meets the 1e-9 bar on Q
-    # at the default 7e-3 with a wide margin, but only at the edge at 1e-2 and
-    # not at 3e-2, so those two are informational here
+    # 1e-8 theta).  The 1e-9 bar on the sum over the sampled sites holds up to
+    # 7e-3 here; at 1e-2 and 3e-2 the bar is looser (informational).  Over the
+    # whole lattice the drift of the FP32 phase adds up coherently, which is
+    # why the default switch is 1e-3 (bench.py compares the whole-lattice Q
+    # with the FP64 path)
     # The half-storage paths (FP16 / BF16 D_W input and output with per-site
     # norms, FP64 reliable updates) have the same kind of floor at the format's
     # rounding u (2^-12, 2^-9): held to 2 u per site, Q not checked.
@@ -572,7 +575,7 @@ def test_uneven_batch_matches_single_runs(S, flux4, zolo4, g5dov4):
                                                   stats[i]["true_resid"]))
         assert d <= 1e-9
         assert abs(Qs[i] - Q) <= 1e-9
-        assert 0 <= stats[i]["true_resid"] <= mixed_resid_bar(7e-3)  # the mixed path's measured base residual
+        assert 0 <= stats[i]["true_resid"] <= mixed_resid_bar(1e-3)  # the mixed path's measured base residual
     # against the oracle
     q4 = bufs_re[0] + 1j * bufs_im[0]
     dense = qx.dense_smp_qx(g5dov4, probing.color_sites((4, 4, 4, 4), 2, 0)[0])
@@ -622,9 +625,9 @@ def test_autotuner_shapes_and_cache_file(S, tmp_path):
     phase, FP32 columns per thread, staged FP32 neighbours), writes it to the
     cache file, and a second context reads it back without timing.  Shapes
     forced through the file (two FP32 columns per thread, one and eight tiles
-    per block; the staged FP32 D_W on 24-column tiles, three tiles per block,
-    so the last block holds one) give the same q(x) to rounding, and all agree
-    with the oracle."""
+    per block; the staged FP32 and float-float D_W on 24-column tiles, three
+    tiles per block, so the last block holds one) give the same q(x) to
+    rounding, and all agree with the oracle."""
     cfg = make_config("flux8x16")
     U, dims = cfg["U"], cfg["dims"]
     a, b = _interval("flux8x16")
@@ -635,7 +638,7 @@ def test_autotuner_shapes_and_cache_file(S, tmp_path):
     mask = np.isin(colour, classes)
     path = str(tmp_path / "tune.txt")
     out = []
-    for k, forced in enumerate((None, None, (12, 1, 8, 2, 0), (24, 2, 3, 1, 1))):
+    for k, forced in enumerate((None, None, (12, 1, 8, 2, 0), (24, 3, 3, 1, 3))):
         if forced is not None:
             path = str(tmp_path / ("forced%d.txt" % k))
             S.smpq_tune_cache_store(path, _device_key(S), dims, 48, S.SMPQ_MIXED, forced, 1.0)
@@ -652,10 +655,40 @@ def test_autotuner_shapes_and_cache_file(S, tmp_path):
         out.append((shape, st["shape_from_cache"], q))
     assert out[0][1] == 0 and out[1][1] == 1 and out[1][0] == out[0][0]
     assert out[2][1] == 1 and out[2][0] == (12, 1, 8, 2, 0)
-    assert out[3][1] == 1 and out[3][0] == (24, 2, 3, 1, 1)  # staged FP32 D_W, 3 tiles per block
+    assert out[3][1] == 1 and out[3][0] == (24, 3, 3, 1, 3)  # staged FP32 and float-float D_W
     assert np.abs(out[2][2][mask] - out[0][2][mask]).max() <= 1e-10
     assert np.abs(out[3][2][mask] - out[0][2][mask]).max() <= 1e-10
     assert len(open(str(tmp_path / "tune.txt")).read().splitlines()) == 1
+
+
+def test_staged_batch_matches_plain(S, flux4, zolo4):
+    """Neighbour staging in both phases of the mixed solve (staging = 1), in the
+    one-solve batch of two lattices (the multi-lattice kernels), against single
+    runs with plain loads (staging = 0): the same arithmetic, so q(x) agrees to
+    rounding of the reductions."""
+    from paper_1901_02211_gb300 import Session, smpq
+    cases = [("flux4", 2), ("flux8x16", 2)]
+    singles, staged = [], []
+    for name, r in cases:
+        cfg = make_config(name)
+        a, b = (zolo4["a"], zolo4["b"]) if name == "flux4" else _interval(name)
+        for stg, out in ((0, singles), (1, staged)):
+            s = Session(precision=smpq.SMPQ_MIXED, staging=stg, autotune=0)
+            s.load_gauge(cfg["dims"], cfg["U"])
+            s.set_spectrum(a, b)
+            s.build_sources(r, 0)
+            out.append(s)
+    ref = [s.compute_qx()[0] for s in singles]
+    bufs_re = [np.zeros(s.V) for s in staged]
+    bufs_im = [np.zeros(s.V) for s in staged]
+    Qs, stats = smpq.smpq_compute_qx_batch([s.ctx for s in staged], bufs_re, bufs_im)
+    for i in range(len(cases)):
+        d = np.abs(bufs_re[i] + 1j * bufs_im[i] - ref[i]).max()
+        print("staged batch, lattice %d: max |q_staged - q_plain| = %.3e, staged bits %d" % (i, d, stats[i]["staged"]))
+        assert stats[i]["staged"] == 3
+        assert d <= 1e-10
+    for s in singles + staged:
+        s.close()
 
 
 def _device_key(S):
