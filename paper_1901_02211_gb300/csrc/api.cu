@@ -147,7 +147,8 @@ void set_geom(smpq_ctx *ctx) {
 struct Shape {
     int bc, tpb_hi, tpb_lo, nr, staged;
 };
-constexpr int TPB_DEFAULT = 4; // tiles per block of the lattice kernels (msolve.cu)
+constexpr int TPB_DEFAULT = 4;    // tiles per block of the FP32 / half / FP64 D_W launches (msolve.cu)
+constexpr int TPB_DEFAULT_HI = 2; // of the float-float ones (the tuner's usual choice on a GB300)
 
 std::string device_key(int dev) {
     cudaDeviceProp pr;
@@ -170,7 +171,7 @@ int tune_kind_lo(int prec) {
 
 Shape tune_shape_raw(smpq_ctx *ctx, int B, int prec, int *cached) {
     *cached = 0;
-    Shape def{1, TPB_DEFAULT, TPB_DEFAULT, 1, 0};
+    Shape def{1, prec == SMPQ_MIXED ? TPB_DEFAULT_HI : TPB_DEFAULT, TPB_DEFAULT, 1, 0};
     if (B == 1) return def;
     std::vector<int> cand;
     for (int bc : {12, 24, 48})
@@ -585,7 +586,7 @@ int compute_batch(smpq_ctx **ctxs, int n, double **q_re, double **q_im, int on_d
     // launch shape: the default tiles per block, one column per thread (timing
     // candidates would need scratch the size of the round again)
     const int from_cache = 0;
-    const Shape shape{BC, TPB_DEFAULT, TPB_DEFAULT, 1,
+    const Shape shape{BC, prec == SMPQ_MIXED ? TPB_DEFAULT_HI : TPB_DEFAULT, TPB_DEFAULT, 1,
                       c0->opt.staging == 1 ? (tune_kind_lo(prec) == 1 ? 1 : 0) | (prec == SMPQ_MIXED ? 2 : 0) : 0};
     // global per-rhs tables (support class, source component, source class) in the first context
     if ((rc = ensure(c0, c0->ws[W_RHS], (size_t)3 * Btot * sizeof(int)))) return rc;

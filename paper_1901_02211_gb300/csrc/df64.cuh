@@ -180,6 +180,26 @@ __device__ __forceinline__ void cdot3x2_pairs(const df64c a[3], const df64c v0[3
         ff_acc2(si, ei, ayh, ayl, vxh, vxl);
     }
 }
+// The same dot products with the right-hand vectors already in packed form:
+// (vxh[b], vxl[b], vyh[b], vyl[b]) hold component b of v0 in lane 0 and of v1
+// in lane 1.
+__device__ __forceinline__ void cdot3x2_packed(const df64c a[3], const float2 vxh[3], const float2 vxl[3],
+                                               const float2 vyh[3], const float2 vyl[3], float2 &sr, float2 &er,
+                                               float2 &si, float2 &ei) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const float2 axh = f2b(a[b].x.hi), axl = f2b(a[b].x.lo), ayh = f2b(a[b].y.hi), ayl = f2b(a[b].y.lo);
+        if (b == 0) {
+            ff_prod2(axh, axl, vxh[b], vxl[b], sr, er);
+            ff_prod2(axh, axl, vyh[b], vyl[b], si, ei);
+        } else {
+            ff_acc2(sr, er, axh, axl, vxh[b], vxl[b]);
+            ff_acc2(si, ei, axh, axl, vyh[b], vyl[b]);
+        }
+        ff_acc2(sr, er, f2neg(ayh), f2neg(ayl), vyh[b], vyl[b]);
+        ff_acc2(si, ei, ayh, ayl, vxh[b], vxl[b]);
+    }
+}
 // Two complex float-float values in packed form (lane 0, lane 1), unnormalised.
 struct f2c {
     float2 xh, xl, yh, yl;

@@ -323,11 +323,52 @@ __device__ __forceinline__ void wilson_hop_rolled(const Geom &g, const typename 
 // that form; S_mu^dag on the lower half is a lane swap (mu <= 1), a
 // multiplication by i (mu = 0, 2) and a lane-1 sign (mu = 1, 2), and the
 // projector sign and the boundary factor enter as sign pairs.
-template <int BC>
-__device__ __forceinline__ void hop_one_pairs(int mu, bool plus, bool back, const df64c *__restrict__ U,
+// MUC >= 0: the direction is that compile-time constant (the selects of S_mu
+// and S_mu^dag fold away); MUC < 0: the runtime mu_rt.
+// SMPQ_DF64_PACKED_PROJ=1: the projection in packed two-lane form as well.
+#ifndef SMPQ_DF64_PACKED_PROJ
+#define SMPQ_DF64_PACKED_PROJ 1
+#endif
+template <int BC, int MUC = -1>
+__device__ __forceinline__ void hop_one_pairs(int mu_rt, bool plus, bool back, const df64c *__restrict__ U,
                                               const df64c *__restrict__ in, int Vl, int nb, int ls, bool flip,
                                               f2c accU[3], f2c accL[3]) {
+    const int mu = MUC >= 0 ? MUC : mu_rt;
     const df64c *q = in + (size_t)nb * (12 * BC);
+#if SMPQ_DF64_PACKED_PROJ
+    // projection in packed form, lanes = the two spin rows: h = P + S_mu L with
+    // P = (psi_0, psi_1), L = (psi_2, psi_3); S_mu is a lane swap (mu <= 1), a
+    // re/im exchange (mu = 0, 2) and a pair of signs per component (times the
+    // projector sign), the same exact operations as s_apply_rt and cneg
+    float2 hxh[3], hxl[3], hyh[3], hyl[3];
+    {
+        const bool swp = mu <= 1, rot = mu == 0 || mu == 2;
+        const float pm = plus ? 1.f : -1.f;
+        const float2 sxp = mu == 1 ? make_float2(-pm, pm) : mu == 2 ? make_float2(pm, -pm) : make_float2(pm, pm);
+        const float2 syp = mu == 0   ? make_float2(-pm, -pm)
+                           : mu == 1 ? make_float2(-pm, pm)
+                           : mu == 2 ? make_float2(-pm, pm)
+                                     : make_float2(pm, pm);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const df64c p0 = q[a * BC], p1 = q[(3 + a) * BC], p2 = q[(6 + a) * BC], p3 = q[(9 + a) * BC];
+            const df64c l0 = swp ? p3 : p2, l1 = swp ? p2 : p3;
+            const df64 lx0 = rot ? l0.y : l0.x, ly0 = rot ? l0.x : l0.y, lx1 = rot ? l1.y : l1.x,
+                       ly1 = rot ? l1.x : l1.y;
+            const float2 lxh = __fmul2_rn(sxp, make_float2(lx0.hi, lx1.hi));
+            const float2 lxl = __fmul2_rn(sxp, make_float2(lx0.lo, lx1.lo));
+            const float2 lyh = __fmul2_rn(syp, make_float2(ly0.hi, ly1.hi));
+            const float2 lyl = __fmul2_rn(syp, make_float2(ly0.lo, ly1.lo));
+            float2 t, e;
+            two_sum2(make_float2(p0.x.hi, p1.x.hi), lxh, t, e);
+            hxh[a] = t;
+            hxl[a] = __fadd2_rn(e, __fadd2_rn(make_float2(p0.x.lo, p1.x.lo), lxl));
+            two_sum2(make_float2(p0.y.hi, p1.y.hi), lyh, t, e);
+            hyh[a] = t;
+            hyl[a] = __fadd2_rn(e, __fadd2_rn(make_float2(p0.y.lo, p1.y.lo), lyl));
+        }
+    }
+#else
     df64c h0[3], h1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -338,6 +379,7 @@ __device__ __forceinline__ void hop_one_pairs(int mu, bool plus, bool back, cons
         h0[a] = cadd_lazy(p0, s0);
         h1[a] = cadd_lazy(p1, s1);
     }
+#endif
     const df64c *ul = U + ((size_t)mu * Vl + ls) * 9;
     const int ra = back ? 1 : 3, rb = back ? 3 : 1; // element (a, b) of W at ul[a * ra + b * rb]
     const float f = flip ? -1.f : 1.f, g = plus ? f : -f, g1 = (mu == 1 || mu == 2) ? -g : g;
@@ -349,7 +391,11 @@ __device__ __forceinline__ void hop_one_pairs(int mu, bool plus, bool back, cons
 #pragma unroll
         for (int b = 0; b < 3; ++b) ur[b] = conj_if(ul[a * ra + b * rb], back);
         float2 sr, er, si, ei;
+#if SMPQ_DF64_PACKED_PROJ
+        cdot3x2_packed(ur, hxh, hxl, hyh, hyl, sr, er, si, ei);
+#else
         cdot3x2_pairs(ur, h0, h1, sr, er, si, ei);
+#endif
         f2c_add_lazy(accU[a], su, su, sr, er, si, ei);
         if (swp) {
             sr = make_float2(sr.y, sr.x);
@@ -362,6 +408,11 @@ __device__ __forceinline__ void hop_one_pairs(int mu, bool plus, bool back, cons
     }
 }
 
+// SMPQ_DF64_MU_UNROLL=1: the 8 hops as 4 direction copies x a 2-orientation
+// loop; 0: one rolled loop over all 8
+#ifndef SMPQ_DF64_MU_UNROLL
+#define SMPQ_DF64_MU_UNROLL 1
+#endif
 template <bool DAG, int BC>
 __device__ __forceinline__ void wilson_hop_pairs(const Geom &g, const df64c *__restrict__ U,
                                                  const df64c *__restrict__ in, int s, df64c acc[12][1]) {
@@ -370,6 +421,27 @@ __device__ __forceinline__ void wilson_hop_pairs(const Geom &g, const df64c *__r
 #pragma unroll
     for (int a = 0; a < 3; ++a) accU[a] = accL[a] = f2c{z, z, z, z};
     const SiteCoords xc(g, s);
+#if SMPQ_DF64_MU_UNROLL
+    // one copy of the hop per direction (the direction's selects fold away),
+    // the two orientations in a loop: half the code of the fully unrolled hop
+    auto dir = [&](auto mc) {
+        constexpr int MU = decltype(mc)::value;
+        const int n = g.n[MU], st = g.stride[MU], c = xc.x[MU];
+#pragma unroll 1
+        for (int bk = 0; bk < 2; ++bk) {
+            const bool back = bk != 0;
+            const bool edge = back ? c == 0 : c == n - 1;
+            const int nb = back ? (edge ? s + (n - 1) * st : s - st) : (edge ? s - (n - 1) * st : s + st);
+            const bool flip = edge && g.bcf[MU] < 0;
+            hop_one_pairs<BC, MU>(MU, back != DAG, back, U, in, g.V, nb, back ? nb : s, flip, accU, accL);
+        }
+        asm volatile("" ::: "memory"); // no loads hoisted across directions (bounds the live registers)
+    };
+    dir(std::integral_constant<int, 0>());
+    dir(std::integral_constant<int, 1>());
+    dir(std::integral_constant<int, 2>());
+    dir(std::integral_constant<int, 3>());
+#else
 #pragma unroll 1
     for (int k = 0; k < 8; ++k) {
         const int mu = k >> 1;
@@ -380,6 +452,7 @@ __device__ __forceinline__ void wilson_hop_pairs(const Geom &g, const df64c *__r
         const bool flip = edge && g.bcf[mu] < 0;
         hop_one_pairs<BC>(mu, back != DAG, back, U, in, g.V, nb, back ? nb : s, flip, accU, accL);
     }
+#endif
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float2 xh, xl, yh, yl;
